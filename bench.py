@@ -1,0 +1,285 @@
+"""Benchmark: PSE Brownian samples per second on one GB300 (replicas on N GPUs).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One step = one full PSE sample (cell list, neighbour list, device-side
+Lanczos loop, k-space noise, cuFFT, interpolation, combination) of the
+headline workload: N = 1e6 random hard spheres (a = 1, RSA seed 1) at volume
+fraction 0.1, tol 1e-3, xi a = 0.5 -- the paper's Table 1 setting at N ~ 1e6.
+L2 is flushed (a 256 MB write) before every timed step; each step is timed
+with CUDA events on the launching stream.  Prints one JSON line.
+
+The path has no data-parallel split: N > 1 GPUs run independent replicas
+(their own seeds), value = all ranks' particle-samples / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-samples/s at tol 1e-3 (N=1e6), learned+batched vs plain PSE"
+UNIT = "particle-samples/s"
+N_PART, PHI, XI, TOL, SEED_POS = 1_000_000, 0.1, 0.5, 1e-3, 1
+CPU_SAMPLE_N = 250_000  # bounded CPU sample: same density and parameters, smaller box
+
+
+def workload_config(plan=None):
+    cfg = {"workload": "random hard spheres, N=1e6, phi=0.1, a=1, tol=1e-3, xi*a=0.5 (RSA seed 1), "
+                       "one PSE sample per step",
+           "N": N_PART, "phi": PHI, "xi": XI, "tol": TOL, "precision": "fp32 grid/FFT/matvec, fp64 Lanczos scalars",
+           "l2": "flushed (256 MB write) before every timed step"}
+    if plan:
+        cfg.update({"L": round(plan["L"], 4), "M": plan["M"], "P": plan["P"], "r_cut": round(plan["r_cut"], 4),
+                    "ncell": plan["ncell"]})
+    return cfg
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def clocks_start():
+    f = open(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+             else os.devnull, "w")
+    try:
+        p = subprocess.Popen(["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                              "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                             stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        p = None
+    return p, f
+
+
+def clocks_stop(p, f, device_index=0):
+    if p is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    p.terminate()
+    try:
+        out, _ = p.communicate(timeout=5)
+    except subprocess.TimeoutExpired:
+        p.kill()
+        out, _ = p.communicate()
+    f.write(out)
+    f.close()
+    sm, smax, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in out.strip().splitlines():
+        cols = [c.strip() for c in line.split(",")]
+        if len(cols) < 9 or cols[0] != str(device_index):
+            continue
+        try:
+            sm.append(float(cols[1]))
+            smax = float(cols[2])
+        except ValueError:
+            continue
+        for n, v in zip(names, cols[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(n)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(budget_s=30.0):
+    """The FP64 oracle (as it stands) on a bounded sample: N=2.5e5 at the same phi/xi/tol."""
+    import numpy as np
+    from oracle import ewald, pse
+    from paper_1611_09322_gb300 import workloads
+    pos, L, _ = workloads.hard_spheres(CPU_SAMPLE_N, PHI, SEED_POS)
+    p = pos.astype(np.float64)
+    t0 = time.perf_counter()
+    plan = ewald.plan(L, 1.0, XI, TOL)
+    ur, j, _ = pse.real_sample(p, plan, 7, 0)
+    uw = pse.wave_sample_grid(p, plan, 7, 0)
+    dt = time.perf_counter() - t0
+    return {"value": CPU_SAMPLE_N / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"one FP64 oracle PSE sample of N={CPU_SAMPLE_N} hard spheres at phi={PHI}, tol={TOL}, "
+                      f"xi={XI} (M={plan.M}, Lanczos j={j}); numpy/scipy on the host cores; {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import ewald, pse
+    from paper_1611_09322_gb300 import workloads
+    pos, L, _ = workloads.hard_spheres(CPU_SAMPLE_N, PHI, SEED_POS)
+    p = pos.astype(np.float64)
+    plan = ewald.plan(L, 1.0, XI, TOL)
+    op = pse.RealOperator(p, plan)
+
+    def step(i):
+        ur, j, _ = pse.real_sample(p, plan, 7, i, op=op)
+        uw = pse.wave_sample_grid(p, plan, 7, i)
+        return j
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(1000 + i)
+    dt = time.perf_counter() - t0
+    value = CPU_SAMPLE_N * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"each step: one FP64 oracle PSE sample of N={CPU_SAMPLE_N} at phi={PHI} "
+                                       f"(same density and parameters as the N=1e6 workload; neighbour pairs "
+                                       f"built once outside the timed steps)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1611_09322_gb300 import Sampler, workloads
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    pos, L, _ = workloads.hard_spheres(N_PART, PHI, SEED_POS)
+    s = Sampler(L, 1.0, xi=XI, tol=TOL)
+    d_pos = torch.from_numpy(pos).to(dev)
+    out = torch.empty_like(d_pos)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    seed = 1000 + rank
+
+    for i in range(args.warmup):
+        s.sample(d_pos, seed, i, out=out)
+    torch.cuda.synchronize()
+    st = s.stats()
+    iters = [st["lanczos_iters"]]
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk, clkf = clocks_start()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        evs[i][0].record(stream)
+        s.sample(d_pos, seed, 100 + i, out=out)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = clocks_stop(clk, clkf, dev.index)
+    per = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(per)
+    iters.append(s.stats()["lanczos_iters"])
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * N_PART * args.steps / (total_ms / 1e3)
+
+    # live per-stage timing (CUDA events on the launching stream) for the roofline
+    stages = None
+    for i in range(3):
+        stages = s.profile_stages(d_pos, seed, 10_000 + i, out=out)
+    st = s.stats()
+    J = st["lanczos_iters"]
+    n_pairs = st["n_pairs"]
+    plan = s.plan
+    M = plan["M"]
+    # dominant kernel by share of the staged sample
+    dom = max(stages, key=lambda k: stages[k][0])
+    mv_ms, mv_n = stages["matvec"]
+    in_ms, in_n = stages["interp"]
+    # algorithmic bytes per launch: matvec reads cell-local
+    # positions, q and nbr_start per particle, the CSR list, writes u;
+    # interpolation reads positions and the 3 M^3 float grid once, writes u_w.
+    bytes_mv = 16 * N_PART * 3 + 4 * (N_PART + 1) + 4 * n_pairs
+    bytes_in = 16 * N_PART * 2 + 12 * M ** 3
+    bytes_fft = None
+    kernel_bytes = {"matvec": (bytes_mv, mv_ms / max(mv_n, 1)), "interp": (bytes_in, in_ms / max(in_n, 1))}
+    key = "matvec" if stages["matvec"][0] >= stages["interp"][0] else "interp"
+    kb, kms = kernel_bytes[key]
+    peak, peak_kind = measured_peak()
+    achieved = kb / (kms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": {"matvec": "k_lz_matvec", "interp": "k_interp"}[key],
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                "algorithmic_bytes_per_launch": kb, "ms_per_launch": round(kms, 5),
+                "dominant_stage": dom,
+                "stages_ms": {k: round(v[0], 4) for k, v in stages.items()},
+                "stages_launches": {k: v[1] for k, v in stages.items()}}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    hp = torch.from_numpy(pos).pin_memory()
+    ho = torch.empty_like(hp).pin_memory()
+    for i in range(2):
+        s.sample_host_ptr(N_PART, hp.data_ptr(), ho.data_ptr(), seed, 50_000 + i)
+    K2 = max(3, min(args.steps, 20))
+    t0 = time.perf_counter()
+    for i in range(K2):
+        s.sample_host_ptr(N_PART, hp.data_ptr(), ho.data_ptr(), seed, 60_000 + i)
+    e2e_s = (time.perf_counter() - t0) / K2
+    e2e = {"value": ws * N_PART / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 12 * N_PART,
+           "d2h_bytes_per_step": 12 * N_PART}
+
+    launches_per_step = 4 + 2 + 1 + 1 + 1 + 5 + 3 * (J + 1) + 1  # our kernels in the graph (cuFFT's excluded)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "ms_per_step_median": statistics.median(per), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(plan), "lanczos_iters": J, "n_pairs": n_pairs,
+                "variant": "plain PSE (single system, CUDA graph per sample)",
+                "roofline": roofline, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": launches_per_step * args.steps,
+                "parallelism": "replicas" if ws > 1 else "single GPU"}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    s.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,204 @@
+/*
+ * pse.h -- C ABI of the GB300 Positively Split Ewald (PSE) Brownian sampler.
+ *
+ * Method: A. M. Fiore, F. Balboa Usabiaga, A. Donev, J. W. Swan, "Rapid
+ * sampling of stochastic displacements in Brownian dynamics simulations",
+ * J. Chem. Phys. 146, 124116 (2017), arXiv:1611.09322.
+ *
+ * A sample is u = M_r^{1/2} z1 + M_w^{1/2} dW2 (Sec. II B, eq. split), whose
+ * covariance is the periodic Ewald-summed RPY mobility M = M_r + M_w
+ * (Sec. II A, eqs. pairmobility, Mwave, Mreal).  The caller multiplies u by
+ * sqrt(2 kT dt) (eq. langevin).  Units: viscosity eta = 1.
+ *
+ * Conventions for every entry point
+ *   - Positions are float32 (or float64 for the *_f64 calls), AoS x,y,z per
+ *     particle, 3N values, in a periodic cube of side L; values outside
+ *     [0, L) are wrapped.  Outputs are 3N values in the caller's order.
+ *   - Pointers named d_* are device pointers on the context's device; h_*
+ *     are host pointers.  The caller owns positions and outputs; the context
+ *     owns every internal buffer, cuFFT plan and CUDA graph.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous on it unless stated otherwise.
+ *   - (seed, sample_index) fully determine the noise: z1 and dW2 are drawn
+ *     from Philox4x32-10 (Salmon et al., SC'11), key = seed, counter =
+ *     (element, stream, sample_index), so a sample is reproducible.
+ *   - Errors are returned as pse_status, never by exit/abort.  A context is
+ *     not thread-safe; use one per host thread.
+ */
+#ifndef PSE_H
+#define PSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PSE_OK = 0,
+    PSE_EINVAL = 1,          /* invalid argument (box, radius, tol, N, pointer, sizes) */
+    PSE_ENOMEM = 2,          /* device or host allocation failed / capacity exceeded */
+    PSE_ECUDA = 3,           /* a CUDA runtime call failed */
+    PSE_ECUFFT = 4,          /* a cuFFT call failed */
+    PSE_ENOTCONVERGED = 5,   /* Lanczos hit max_iter; output holds the last iterate */
+    PSE_ENOTSUPPORTED = 6,   /* call not available for this context (e.g. precision) */
+    PSE_ENOTREADY = 7        /* required state missing (e.g. preconditioner weights) */
+} pse_status;
+
+enum { PSE_FP32 = 0, PSE_FP64 = 1 };
+
+/* Creation parameters.  Zero-initialise and set what you need. */
+typedef struct {
+    double tol;          /* relative tolerance of the Ewald truncations, the NUFFT
+                            quadrature and the Lanczos iteration, in (0, 0.1]   */
+    double xi;           /* splitting parameter; <= 0 selects 0.5 / a           */
+    int precision;       /* PSE_FP32: grid, FFT, matvec in float32 with float64
+                            Lanczos scalars; PSE_FP64: everything in float64    */
+    int max_iter;        /* Lanczos cap, 1..64; 0 selects 64                    */
+    int fixed_iter;      /* > 0: exactly this many Lanczos steps, no test        */
+    int grid_M;          /* > 0: override the FFT grid size (per side)          */
+    int support_P;       /* > 0: override the Gaussian support (points per side) */
+    int use_precond;     /* 1: block-diagonal learned preconditioner (weights
+                            set by pse_precond_set_weights), 0: none            */
+    double lanczos_tol;  /* <= 0: same as tol                                    */
+    int use_graph;       /* >= 0 (default): one CUDA graph per sample with a
+                            device-side Lanczos loop; -1: plain stream launches
+                            with a host-side loop (one sync per iteration)      */
+    int reserved[7];
+} pse_params;
+
+/* Parameters derived from (L, a, xi, tol) by Sec. II C of the paper:
+ *   r_cut:  exp(-xi^2 r_cut^2) = tol                        (real truncation)
+ *   k_cut:  smallest k with the eq. errbound bound <= tol    (wave truncation)
+ *   P, m:   smallest integer P with min_m exp(-pi^2 P^2/2m^2) + erfc(m/sqrt2) <= tol
+ *   M:      smallest 2,3,5,7-smooth grid with pi M / L >= k_cut and eta <= 1
+ *   eta:    Gaussian shape, sigma^2 = eta / (4 xi^2), eta = (P h xi / m)^2, h = L/M
+ *   ncell:  cells per side of the neighbour search, cell side >= r_cut          */
+typedef struct {
+    double L, a, xi, tol, r_cut, k_cut, m, eta, h, self_mobility;
+    int P, M, ncell, precision;
+} pse_plan_info;
+
+/* Statistics of the last completed pse_sample* call (read after the stream
+ * has been synchronised; pse_get_stats synchronises it). */
+typedef struct {
+    int lanczos_iters;   /* j at which the Lanczos test passed (or the cap)     */
+    int converged;       /* 1 if the test passed                               */
+    double lanczos_rel_change; /* ||x_j - x_{j-1}|| / ||x_j|| at exit          */
+    int64_t n_pairs;     /* directed near-field pairs within r_cut              */
+    int overflow;        /* 1 if the neighbour list exceeded its capacity       */
+    int reserved[5];
+} pse_stats;
+
+typedef struct pse_ctx pse_ctx;
+
+/* ---------------------------------------------------------------- setup */
+
+/* Host-only: derive the Sec. II C parameters without touching a GPU.
+ * L > 0 (box side), a > 0 (sphere radius), p->tol in (0, 0.1].
+ * Returns PSE_EINVAL on bad arguments or if r_cut >= L/2 (the near field
+ * would need more than the nearest periodic image). */
+pse_status pse_plan(double L, double a, const pse_params *p, pse_plan_info *out);
+
+/* Host-only: the dimensionless real-space scalars of Appendix A at n
+ * separations r[i] >= 0 (6 pi eta a M^(r) = F (I - rr) + G rr, eq. Mreal),
+ * in float64 -- the values the device table is built from.  r = 0 gives the
+ * self term of eq. self; 0 < r < 0.2a uses free-space RPY minus the
+ * Gaussian-damped wave integral (the closed form cancels there).
+ * xi > 0, a > 0; r, F, G: host arrays of n doubles (caller-owned). */
+pse_status pse_real_scalars(double xi, double a, int64_t n, const double *r, double *F, double *G);
+
+/* Create a sampler for a cube of side L and spheres of radius a with the
+ * default parameters (FP32, graph, max_iter 64) -- Sec. II.
+ * Allocates device memory on the current device lazily, at the first
+ * sample for a given N.  *out is NULL on failure. */
+pse_status pse_create(pse_ctx **out, double L, double a, double xi, double tol);
+
+/* As pse_create with explicit parameters. */
+pse_status pse_create_ex(pse_ctx **out, double L, double a, const pse_params *p);
+
+/* Release every device buffer, plan and graph of the context (synchronises
+ * the device first).  NULL is accepted. */
+void pse_destroy(pse_ctx *ctx);
+
+pse_status pse_get_plan(const pse_ctx *ctx, pse_plan_info *out);
+
+/* ---------------------------------------------------------------- sampling */
+
+/* One PSE Brownian sample (Sec. II B, eq. split), FP32 context.
+ *   N >= 1 particles; d_pos: 3N float32 (device); d_out: 3N float32
+ *   (device, caller-owned, may not alias d_pos).
+ * Real part: Lanczos on the sparse M_r (eq. Mreal, App. A) from a cell list,
+ * stopped when ||x_j - x_{j-1}|| / ||x_j|| < lanczos_tol (Chow & Saad).
+ * Wave part: Hermitian complex noise scaled per mode by eq. Mwave's
+ * B^{1/2} and the Gaussian deconvolution, inverse FFT (cuFFT), Gaussian
+ * interpolation at the particles (the Spectral-Ewald NUFFT of Sec. II B 2).
+ * Returns once the work is queued; whether the Lanczos test passed is
+ * reported by pse_get_stats (PSE_ENOTCONVERGED if the cap was hit, with the
+ * last iterate written).  Synchronises the device only when N changed since
+ * the previous call (buffers and the graph are then rebuilt). */
+pse_status pse_sample(pse_ctx *ctx, int64_t N, const float *d_pos, uint64_t seed,
+                      uint64_t sample_index, float *d_out, void *stream);
+
+/* As pse_sample, also writing the two independent parts of eq. split:
+ * d_real = M_r^{1/2} z1 and d_wave = M_w^{1/2} dW2 (each 3N float32, device;
+ * either may be NULL).  d_out may be NULL too. */
+pse_status pse_sample_parts(pse_ctx *ctx, int64_t N, const float *d_pos, uint64_t seed,
+                            uint64_t sample_index, float *d_out, float *d_real, float *d_wave,
+                            void *stream);
+
+/* As pse_sample with HOST buffers: copies h_pos (3N float32) to the device,
+ * samples, copies the result to h_out (3N float32) and synchronises `stream`.
+ * Pinned host memory makes the copies asynchronous-capable. */
+pse_status pse_sample_host(pse_ctx *ctx, int64_t N, const float *h_pos, uint64_t seed,
+                           uint64_t sample_index, float *h_out, void *stream);
+
+/* FP64 context (params.precision = PSE_FP64): positions, outputs and all
+ * arithmetic in float64.  Same semantics as pse_sample_parts. */
+pse_status pse_sample_f64(pse_ctx *ctx, int64_t N, const double *d_pos, uint64_t seed,
+                          uint64_t sample_index, double *d_out, double *d_real, double *d_wave,
+                          void *stream);
+
+/* Near-field product d_out = M_r d_v (eq. Mreal with the App. A scalars and
+ * the eq. self diagonal), FP32 context.  d_pos, d_v, d_out: 3N float32
+ * device arrays in the caller's order. */
+pse_status pse_real_matvec(pse_ctx *ctx, int64_t N, const float *d_pos, const float *d_v,
+                           float *d_out, void *stream);
+
+/* Stage indices of pse_profile_stages (the paper's Fig. gel split: real-space
+ * matvecs, other Lanczos work, FFT + scaling + RNG, spreading/interpolation). */
+enum {
+    PSE_STAGE_CELLS = 0,      /* binning + cell scan                         */
+    PSE_STAGE_SORT,           /* scatter into cell order + per-cell sort      */
+    PSE_STAGE_REAL_NOISE,     /* z1 and ||z1||                                */
+    PSE_STAGE_NEIGHBOURS,     /* neighbour count, scan, fill                  */
+    PSE_STAGE_MATVEC,         /* M_r q_j, all iterations                      */
+    PSE_STAGE_LANCZOS_UPDATE, /* three-term update + ||w||, all iterations    */
+    PSE_STAGE_EIGEN,          /* FP64 T_j^{1/2} e_1 + stop test, all iterations */
+    PSE_STAGE_FINAL,          /* x = V y, + wave part, caller order           */
+    PSE_STAGE_WAVE_NOISE,     /* k-space noise and B^{1/2} scaling            */
+    PSE_STAGE_FFT,            /* cuFFT C2R, three components                  */
+    PSE_STAGE_INTERP,         /* Gaussian interpolation at the particles      */
+    PSE_NSTAGES
+};
+
+/* One FP32 sample (as pse_sample) run stage by stage with plain launches and
+ * CUDA events between stages on `stream`; synchronises it.  ms[PSE_NSTAGES]
+ * receives each stage's device time in milliseconds and launches[PSE_NSTAGES]
+ * its number of kernel launches of this library (host arrays, caller-owned).
+ * The output equals pse_sample's for the same arguments. */
+pse_status pse_profile_stages(pse_ctx *ctx, int64_t N, const float *d_pos, uint64_t seed,
+                              uint64_t sample_index, float *d_out, double *ms, int *launches,
+                              void *stream);
+
+/* Statistics of the last sample (synchronises the context's last stream). */
+pse_status pse_get_stats(pse_ctx *ctx, pse_stats *out);
+
+/* Static description of a status code. */
+const char *pse_strerror(pse_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSE_H */

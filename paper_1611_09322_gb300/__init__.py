@@ -1,0 +1,162 @@
+"""GB300-native Positively Split Ewald (PSE) Brownian displacement sampler.
+
+Python side of the C ABI in ``include/pse.h`` (arXiv:1611.09322).  The
+functions ``pse_*`` below carry the names of the C entry points and only
+marshal arguments; all arithmetic runs in the CUDA kernels of libpse.so.
+PyTorch supplies device memory and the current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import PSE_FP32, PSE_FP64, PseError, pse_params, pse_plan_info, pse_stats
+
+__all__ = ["Sampler", "pse_plan", "pse_real_scalars", "PseError", "PSE_FP32", "PSE_FP64", "make_params"]
+
+
+def make_params(tol=1e-3, xi=0.5, precision=PSE_FP32, max_iter=0, fixed_iter=0, grid_M=0, support_P=0,
+                use_precond=0, lanczos_tol=0.0, use_graph=True):
+    p = pse_params()
+    p.tol = tol
+    p.xi = xi
+    p.precision = precision
+    p.max_iter = max_iter
+    p.fixed_iter = fixed_iter
+    p.grid_M = grid_M
+    p.support_P = support_P
+    p.use_precond = use_precond
+    p.lanczos_tol = lanczos_tol
+    p.use_graph = 0 if use_graph else -1
+    return p
+
+
+def pse_plan(L, a=1.0, **kw):
+    """Host-only Sec. II C parameter planning (no GPU needed); returns a dict."""
+    lib = _lib.load()
+    p = make_params(**kw)
+    out = pse_plan_info()
+    _lib.check(lib.pse_plan(L, a, ctypes.byref(p), ctypes.byref(out)), "pse_plan")
+    return out.as_dict()
+
+
+def pse_real_scalars(r, xi, a=1.0):
+    """Host-only Appendix A scalars F(r), G(r) (float64 numpy arrays)."""
+    lib = _lib.load()
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    F = np.empty_like(r)
+    G = np.empty_like(r)
+    vp = lambda x: x.ctypes.data_as(ctypes.c_void_p)
+    _lib.check(lib.pse_real_scalars(xi, a, r.size, vp(r), vp(F), vp(G)), "pse_real_scalars")
+    return F, G
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+class Sampler:
+    """One PSE sampler for a periodic cube of side L (a context of libpse)."""
+
+    def __init__(self, L, a=1.0, **kw):
+        self.lib = _lib.load()
+        self.params = make_params(**kw)
+        self.L, self.a = L, a
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.pse_create_ex(ctypes.byref(h), L, a, ctypes.byref(self.params)), "pse_create_ex")
+        self.ctx = h
+        info = pse_plan_info()
+        _lib.check(self.lib.pse_get_plan(self.ctx, ctypes.byref(info)), "pse_get_plan")
+        self.plan = info.as_dict()
+        self.fp64 = self.params.precision == PSE_FP64
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.pse_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check_pos(self, pos):
+        import torch
+        want = torch.float64 if self.fp64 else torch.float32
+        if not (pos.is_cuda and pos.dtype == want and pos.is_contiguous() and pos.dim() == 2 and pos.shape[1] == 3):
+            raise ValueError(f"positions must be a contiguous (N, 3) {want} CUDA tensor")
+
+    def sample(self, pos, seed, sample_index=0, out=None, parts=False):
+        """u = M_r^{1/2} z1 + M_w^{1/2} dW2 at `pos`; with parts=True returns (u, u_real, u_wave)."""
+        import torch
+        self._check_pos(pos)
+        N = pos.shape[0]
+        if out is None:
+            out = torch.empty_like(pos)
+        real = torch.empty_like(pos) if parts else None
+        wave = torch.empty_like(pos) if parts else None
+        if self.fp64:
+            st = self.lib.pse_sample_f64(self.ctx, N, _ptr(pos), seed, sample_index, _ptr(out), _ptr(real),
+                                         _ptr(wave), _stream())
+        elif parts:
+            st = self.lib.pse_sample_parts(self.ctx, N, _ptr(pos), seed, sample_index, _ptr(out), _ptr(real),
+                                           _ptr(wave), _stream())
+        else:
+            st = self.lib.pse_sample(self.ctx, N, _ptr(pos), seed, sample_index, _ptr(out), _stream())
+        _lib.check(st, "pse_sample")
+        return (out, real, wave) if parts else out
+
+    def sample_host(self, pos_host, seed, sample_index=0, out_host=None):
+        """Host buffers in and out (the copies happen inside libpse); numpy float32 (N, 3)."""
+        pos_host = np.ascontiguousarray(pos_host, dtype=np.float32)
+        if out_host is None:
+            out_host = np.empty_like(pos_host)
+        st = self.lib.pse_sample_host(self.ctx, pos_host.shape[0], pos_host.ctypes.data_as(ctypes.c_void_p), seed,
+                                      sample_index, out_host.ctypes.data_as(ctypes.c_void_p), _stream())
+        _lib.check(st, "pse_sample_host")
+        return out_host
+
+    def sample_host_ptr(self, N, h_pos_ptr, h_out_ptr, seed, sample_index=0):
+        """As sample_host with raw host pointers (e.g. pinned torch tensors)."""
+        _lib.check(self.lib.pse_sample_host(self.ctx, N, ctypes.c_void_p(h_pos_ptr), seed, sample_index,
+                                            ctypes.c_void_p(h_out_ptr), _stream()), "pse_sample_host")
+
+    def real_matvec(self, pos, v, out=None):
+        """M_r v (near-field product, eq. Mreal) for (N, 3) CUDA float32 tensors."""
+        import torch
+        self._check_pos(pos)
+        if out is None:
+            out = torch.empty_like(v)
+        _lib.check(self.lib.pse_real_matvec(self.ctx, pos.shape[0], _ptr(pos), _ptr(v), _ptr(out), _stream()),
+                   "pse_real_matvec")
+        return out
+
+    def profile_stages(self, pos, seed, sample_index=0, out=None):
+        """Per-stage device times (ms) and launch counts of one sample (pse_profile_stages)."""
+        import torch
+        self._check_pos(pos)
+        if out is None:
+            out = torch.empty_like(pos)
+        n = len(_lib.STAGES)
+        ms = (ctypes.c_double * n)()
+        nl = (ctypes.c_int * n)()
+        _lib.check(self.lib.pse_profile_stages(self.ctx, pos.shape[0], _ptr(pos), seed, sample_index, _ptr(out),
+                                               ms, nl, _stream()), "pse_profile_stages")
+        return {name: (ms[i], nl[i]) for i, name in enumerate(_lib.STAGES)}
+
+    def stats(self, strict=False):
+        s = pse_stats()
+        st = self.lib.pse_get_stats(self.ctx, ctypes.byref(s))
+        if strict:
+            _lib.check(st, "pse_get_stats")
+        d = s.as_dict()
+        d["status"] = _lib.STATUS.get(st, st)
+        return d

@@ -1,0 +1,99 @@
+"""ctypes binding of libpse (include/pse.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Device
+arrays are torch CUDA tensors passed as raw pointers with the current torch
+stream; there is no CPU fallback: if the library cannot be loaded every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libpse.so")
+
+PSE_FP32, PSE_FP64 = 0, 1
+STAGES = ["cells", "sort", "real_noise", "neighbours", "matvec", "lanczos_update", "eigen", "final",
+          "wave_noise", "fft", "interp"]
+STATUS = {0: "PSE_OK", 1: "PSE_EINVAL", 2: "PSE_ENOMEM", 3: "PSE_ECUDA", 4: "PSE_ECUFFT",
+          5: "PSE_ENOTCONVERGED", 6: "PSE_ENOTSUPPORTED", 7: "PSE_ENOTREADY"}
+
+
+class PseError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+
+
+class pse_params(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("xi", ctypes.c_double), ("precision", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("fixed_iter", ctypes.c_int), ("grid_M", ctypes.c_int),
+                ("support_P", ctypes.c_int), ("use_precond", ctypes.c_int), ("lanczos_tol", ctypes.c_double),
+                ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+
+
+class pse_plan_info(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_double), ("a", ctypes.c_double), ("xi", ctypes.c_double), ("tol", ctypes.c_double),
+                ("r_cut", ctypes.c_double), ("k_cut", ctypes.c_double), ("m", ctypes.c_double),
+                ("eta", ctypes.c_double), ("h", ctypes.c_double), ("self_mobility", ctypes.c_double),
+                ("P", ctypes.c_int), ("M", ctypes.c_int), ("ncell", ctypes.c_int), ("precision", ctypes.c_int)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class pse_stats(ctypes.Structure):
+    _fields_ = [("lanczos_iters", ctypes.c_int), ("converged", ctypes.c_int),
+                ("lanczos_rel_change", ctypes.c_double), ("n_pairs", ctypes.c_int64),
+                ("overflow", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
+# name -> (restype, argtypes); the exported surface of include/pse.h
+_VP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_U64 = ctypes.c_uint64
+_ST = ctypes.c_int
+SIGNATURES = {
+    "pse_plan": (_ST, [ctypes.c_double, ctypes.c_double, ctypes.POINTER(pse_params), ctypes.POINTER(pse_plan_info)]),
+    "pse_create": (_ST, [ctypes.POINTER(_VP), ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+    "pse_create_ex": (_ST, [ctypes.POINTER(_VP), ctypes.c_double, ctypes.c_double, ctypes.POINTER(pse_params)]),
+    "pse_destroy": (None, [_VP]),
+    "pse_get_plan": (_ST, [_VP, ctypes.POINTER(pse_plan_info)]),
+    "pse_sample": (_ST, [_VP, _I64, _VP, _U64, _U64, _VP, _VP]),
+    "pse_sample_parts": (_ST, [_VP, _I64, _VP, _U64, _U64, _VP, _VP, _VP, _VP]),
+    "pse_sample_host": (_ST, [_VP, _I64, _VP, _U64, _U64, _VP, _VP]),
+    "pse_sample_f64": (_ST, [_VP, _I64, _VP, _U64, _U64, _VP, _VP, _VP, _VP]),
+    "pse_real_matvec": (_ST, [_VP, _I64, _VP, _VP, _VP, _VP]),
+    "pse_get_stats": (_ST, [_VP, ctypes.POINTER(pse_stats)]),
+    "pse_strerror": (ctypes.c_char_p, [_ST]),
+    "pse_profile_stages": (_ST, [_VP, _I64, _VP, _U64, _U64, _VP, _VP, _VP, _VP]),
+    "pse_real_scalars": (_ST, [ctypes.c_double, ctypes.c_double, _I64, _VP, _VP, _VP]),
+}
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libpse.so (built by paper_1611_09322_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"libpse.so not built at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status, where):
+    if status != 0:
+        raise PseError(status, where)
+    return status

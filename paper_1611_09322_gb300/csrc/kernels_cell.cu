@@ -1,0 +1,249 @@
+// Cell list, device scan and near-field neighbour list (the linked-cell
+// search the paper's real-space sum uses, Sec. III), sm_103a.
+//
+// Particles are binned into ncell^3 cells of side >= r_cut, counting-sorted
+// into cell order (deterministic: ties in a cell are ordered by caller
+// index), and every sorted particle gets a CSR list of the particles within
+// r_cut.  Each entry packs the neighbour's sorted index with the 3x3x3
+// stencil offset of its cell, so pair vectors are formed from cell-local
+// offsets: d = (l_i - l_t) - dc * cs, accurate to a few float ulps of the
+// cell side whatever the box size, with no wrap logic in the matvec.
+#include "pse_internal.cuh"
+
+namespace pse {
+
+template <typename T> __device__ __forceinline__ T wrap_box(T x, T L) {
+    if (x < T(0) || x >= L) {
+        x -= L * floor(x / L);
+        if (x >= L || x < T(0)) x = T(0);
+    }
+    return x;
+}
+
+template <typename T> __device__ __forceinline__ int cell_coord(T x, T inv_cs, int nc) {
+    int c = (int)(x * inv_cs);
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+// offset of x from its cell corner c*cs, compensated: fma gives x - c*cs_hi
+// with one rounding, then the low part of cs is removed.
+__device__ __forceinline__ float cell_offset(float x, int c, float cs, float cs_lo) {
+    return fmaf(-(float)c, cs, x) - (float)c * cs_lo;
+}
+__device__ __forceinline__ double cell_offset(double x, int c, double cs, double) { return x - c * cs; }
+
+template <typename T>
+__global__ void k_bin(int64_t N, const SampleArgs<T> *args, Geom<T> g, int *cell_of, int *slot, int *count) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const T *p = args->pos + 3 * i;
+    const T x = wrap_box(p[0], g.L), y = wrap_box(p[1], g.L), z = wrap_box(p[2], g.L);
+    const int cx = cell_coord(x, g.inv_cs, g.nc), cy = cell_coord(y, g.inv_cs, g.nc),
+              cz = cell_coord(z, g.inv_cs, g.nc);
+    const int c = (cx * g.nc + cy) * g.nc + cz;
+    cell_of[i] = c;
+    slot[i] = atomicAdd(count + c, 1);
+}
+
+template <typename T>
+__global__ void k_scatter(int64_t N, const SampleArgs<T> *args, Geom<T> g, const int *cell_of, const int *slot,
+                          const int *start, V4<T> *pos_sorted, V4<T> *loc_sorted) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const T *p = args->pos + 3 * i;
+    const T x = wrap_box(p[0], g.L), y = wrap_box(p[1], g.L), z = wrap_box(p[2], g.L);
+    const int c = cell_of[i];
+    const int cz = c % g.nc, cy = (c / g.nc) % g.nc, cx = c / (g.nc * g.nc);
+    const int dst = start[c] + slot[i];
+    V4<T> a;
+    a.x = x; a.y = y; a.z = z;
+    if constexpr (sizeof(T) == 4) a.w = __int_as_float((int)i);
+    else a.w = __longlong_as_double((long long)i);
+    pos_sorted[dst] = a;
+    V4<T> l;
+    l.x = cell_offset(x, cx, g.cs, g.cs_lo);
+    l.y = cell_offset(y, cy, g.cs, g.cs_lo);
+    l.z = cell_offset(z, cz, g.cs, g.cs_lo);
+    if constexpr (sizeof(T) == 4) l.w = __int_as_float(c);
+    else l.w = __longlong_as_double((long long)c);
+    loc_sorted[dst] = l;
+}
+
+template <typename T> __device__ __forceinline__ long long w_bits(T w) {
+    if constexpr (sizeof(T) == 4) return (long long)__float_as_int(w);
+    else return __double_as_longlong(w);
+}
+
+// Insertion sort of each cell's entries by caller index: makes the sorted
+// order, and every summation order downstream, independent of atomics.
+template <typename T>
+__global__ void k_cellsort(int ncell3, const int *start, V4<T> *pos_sorted, V4<T> *loc_sorted) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell3) return;
+    const int b = start[c], e = start[c + 1];
+    for (int i = b + 1; i < e; ++i) {
+        const V4<T> pa = pos_sorted[i], la = loc_sorted[i];
+        const long long key = w_bits(pa.w);
+        int j = i - 1;
+        while (j >= b && w_bits(pos_sorted[j].w) > key) {
+            pos_sorted[j + 1] = pos_sorted[j];
+            loc_sorted[j + 1] = loc_sorted[j];
+            --j;
+        }
+        pos_sorted[j + 1] = pa;
+        loc_sorted[j + 1] = la;
+    }
+}
+
+// One thread per sorted particle: count (fill = false) or write (fill = true)
+// the neighbours within r_cut over the 27 stencil cells.  With ncell = 2 the
+// same cell appears under two offsets; r_cut < L/2 leaves at most one image
+// of each pair inside r_cut, so the distance test keeps the right one.
+template <typename T, bool FILL>
+__global__ void k_nbr(int64_t N, Geom<T> g, const V4<T> *loc, const int *cell_start, int *count,
+                      const int *nbr_start, int *nbr, int64_t cap, int *overflow) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const V4<T> li = loc[s];
+    const int c = (int)w_bits(li.w);
+    const int nc = g.nc;
+    const int cz = c % nc, cy = (c / nc) % nc, cx = c / (nc * nc);
+    int cnt = 0;
+    int64_t base = FILL ? nbr_start[s] : 0;
+    for (int ox = -1; ox <= 1; ++ox) {
+        const int ax = (cx + ox + nc) % nc;
+        for (int oy = -1; oy <= 1; ++oy) {
+            const int ay = (cy + oy + nc) % nc;
+            for (int oz = -1; oz <= 1; ++oz) {
+                const int az = (cz + oz + nc) % nc;
+                const int code = (ox + 1) * 9 + (oy + 1) * 3 + (oz + 1);
+                const int c2 = (ax * nc + ay) * nc + az;
+                const int b = cell_start[c2], e = cell_start[c2 + 1];
+                for (int t = b; t < e; ++t) {
+                    if (t == s && code == 13) continue;
+                    const V4<T> lt = loc[t];
+                    const T dx = (li.x - lt.x) - T(ox) * g.cs;
+                    const T dy = (li.y - lt.y) - T(oy) * g.cs;
+                    const T dz = (li.z - lt.z) - T(oz) * g.cs;
+                    const T r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 < g.rc2) {
+                        if (FILL) {
+                            const int64_t pos = base + cnt;
+                            if (pos < cap) nbr[pos] = (t << 5) | code;
+                            else atomicExch(overflow, 1);
+                        }
+                        ++cnt;
+                    }
+                }
+            }
+        }
+    }
+    if (!FILL) count[s] = cnt;
+}
+
+// ------------------------------------------------------------------ exclusive scan
+// Three passes: per-block scan of PSE_SCAN_ITEMS ints (1024 threads x 4),
+// a one-block scan of the block totals, then the carry-in add.
+__global__ void k_scan_block(const int *in, int *out, int64_t n, int *sums) {
+    __shared__ int sh[1024];
+    const int64_t base = (int64_t)blockIdx.x * PSE_SCAN_ITEMS + threadIdx.x * 4;
+    int v[4];
+    int tot = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0;
+        tot += v[k];
+    }
+    sh[threadIdx.x] = tot;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {  // Hillis-Steele inclusive scan
+        const int t = threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += t;
+        __syncthreads();
+    }
+    int run = sh[threadIdx.x] - tot;  // exclusive prefix of this thread
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 1023) sums[blockIdx.x] = sh[1023];
+}
+
+__global__ void k_scan_sums(int *sums, int nb, int *total_out) {
+    __shared__ int sh[1024];
+    int carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += 1024) {
+        const int i = b0 + threadIdx.x;
+        const int v = i < nb ? sums[i] : 0;
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            const int t = threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < nb) sums[i] = carry + sh[threadIdx.x] - v;
+        const int chunk = sh[1023];
+        __syncthreads();
+        carry += chunk;
+    }
+    if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void k_scan_add(int *out, int64_t n, const int *sums) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] += sums[i / PSE_SCAN_ITEMS];
+}
+
+void launch_scan(const int *in, int *out, int64_t n, int *sums, cudaStream_t s) {
+    const int nb = (int)((n + PSE_SCAN_ITEMS - 1) / PSE_SCAN_ITEMS);
+    if (nb > 0) k_scan_block<<<nb, 1024, 0, s>>>(in, out, n, sums);
+    k_scan_sums<<<1, 1024, 0, s>>>(sums, nb, out + n);
+    if (n > 0) k_scan_add<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n, sums);
+}
+
+// ------------------------------------------------------------------ launchers
+static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+template <typename T>
+void launch_bin(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
+    const int64_t nc3 = (int64_t)g.nc * g.nc * g.nc;
+    cudaMemsetAsync(d.cell_count, 0, sizeof(int) * nc3, s);
+    k_bin<T><<<nblk(N, 256), 256, 0, s>>>(N, args, g, d.cell_of, d.slot, d.cell_count);
+    launch_scan(d.cell_count, d.cell_start, nc3, d.scan_sums, s);
+}
+
+template <typename T>
+void launch_scatter(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
+    k_scatter<T><<<nblk(N, 256), 256, 0, s>>>(N, args, g, d.cell_of, d.slot, d.cell_start, d.pos_sorted,
+                                              d.loc_sorted);
+}
+
+template <typename T> void launch_cellsort(int ncell3, const Dev<T> &d, cudaStream_t s) {
+    k_cellsort<T><<<nblk(ncell3, 256), 256, 0, s>>>(ncell3, d.cell_start, d.pos_sorted, d.loc_sorted);
+}
+
+template <typename T> void launch_nbr(int64_t N, Geom<T> g, const Dev<T> &d, bool fill, cudaStream_t s) {
+    if (!fill) {
+        k_nbr<T, false><<<nblk(N, 128), 128, 0, s>>>(N, g, d.loc_sorted, d.cell_start, d.nbr_count, nullptr,
+                                                     nullptr, 0, nullptr);
+        launch_scan(d.nbr_count, d.nbr_start, N, d.scan_sums, s);
+    } else {
+        k_nbr<T, true><<<nblk(N, 128), 128, 0, s>>>(N, g, d.loc_sorted, d.cell_start, nullptr, d.nbr_start,
+                                                    d.nbr, d.nbr_cap, &d.lz->overflow);
+    }
+}
+
+#define PSE_INST(T)                                                                                       \
+    template void launch_bin<T>(int64_t, const SampleArgs<T> *, Geom<T>, const Dev<T> &, cudaStream_t);     \
+    template void launch_scatter<T>(int64_t, const SampleArgs<T> *, Geom<T>, const Dev<T> &, cudaStream_t); \
+    template void launch_cellsort<T>(int, const Dev<T> &, cudaStream_t);                                  \
+    template void launch_nbr<T>(int64_t, Geom<T>, const Dev<T> &, bool, cudaStream_t);
+PSE_INST(float)
+PSE_INST(double)
+#undef PSE_INST
+
+}  // namespace pse

@@ -1,0 +1,401 @@
+// Real-space sample M_r^{1/2} z1 by Lanczos (Sec. II B 1; Chow & Saad),
+// sm_103a.
+//
+// Vectors live in cell-sorted order as 16-byte (x, y, z, pad) records.  The
+// basis is kept unnormalised: q_1 = z1 and q_{j+1} = w_j, with
+// beta_j = ||q_{j+1}||, v_j = q_j / beta_{j-1}.  Per iteration j:
+//   matvec  u = M_r q_j                       (+ deterministic q_j . u)
+//   update  alpha_j = q_j.u / beta_{j-1}^2,
+//           q_{j+1} = u/beta_{j-1} - alpha_j q_j/beta_{j-1} - beta_{j-1} q_{j-1}/beta_{j-2}
+//                                               (+ deterministic ||q_{j+1}||^2)
+//   eigen   y_j = T_j^{1/2} e_1 in FP64 (one warp), stop test
+//           ||y_j - [y_{j-1}; 0]|| / ||y_j|| < tol  (= ||x_j - x_{j-1}|| / ||x_j||
+//           for an orthonormal basis)
+// and finally x = beta_0 sum_i y_i q_i / beta_{i-1}.  Scalars are FP64; the
+// per-block partial sums are reduced in block order by the last block to
+// arrive, so results do not depend on scheduling.
+#include "pse_internal.cuh"
+
+namespace pse {
+
+template <typename T> __device__ __forceinline__ long long w_bits_r(T w) {
+    if constexpr (sizeof(T) == 4) return (long long)__float_as_int(w);
+    else return __double_as_longlong(w);
+}
+
+// ------------------------------------------------------------------ init: q_1 = z1, beta_0
+template <typename T>
+__global__ void k_lz_init(int64_t N, const SampleArgs<T> *args, int system, const V4<T> *pos_sorted, V4<T> *q1,
+                          double *partials, LzState *lz) {
+    __shared__ double sh[32];
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double part = 0.0;
+    if (s < N) {
+        const uint32_t orig = (uint32_t)w_bits_r(pos_sorted[s].w);
+        const Normals4<T> z = normals4<T>(orig, 2u * system, args->seed, args->sample);
+        V4<T> v;
+        v.x = z.v[0]; v.y = z.v[1]; v.z = z.v[2]; v.w = T(0);
+        q1[s] = v;
+        part = (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z;
+    }
+    part = block_sum(part, sh);
+    double total;
+    if (grid_sum_last(part, partials, &lz->counter_init, sh, &total) && threadIdx.x == 0) {
+        lz->beta[0] = sqrt(total);
+        lz->iter = 1;
+        lz->jeig = 0;
+        lz->J = 0;
+        lz->converged = 0;
+        lz->cont = 1;
+        lz->rel = 0.0;
+    }
+}
+
+// ------------------------------------------------------------------ near-field matvec
+// One thread per sorted particle: u_s = self q_s + sum_t [F (I - rr) + G rr] q_t,
+// F, G linearly interpolated from the FP64-built table (stored / 6 pi a).
+template <typename T>
+__device__ __forceinline__ V4<T> mr_row(int64_t s, Geom<T> g, const V4<T> *__restrict__ loc,
+                                        const int *__restrict__ nbr_start, const int *__restrict__ nbr,
+                                        const V4<T> *__restrict__ table, const V4<T> *__restrict__ q) {
+    const V4<T> li = loc[s];
+    const V4<T> qi = q[s];
+    T ax = g.self_m * qi.x, ay = g.self_m * qi.y, az = g.self_m * qi.z;
+    const int e0 = nbr_start[s], e1 = nbr_start[s + 1];
+    for (int e = e0; e < e1; ++e) {
+        const int ent = __ldg(nbr + e);
+        const int t = ent >> 5, code = ent & 31;
+        const int ox = code / 9 - 1, oy = (code / 3) % 3 - 1, oz = code % 3 - 1;
+        const V4<T> lt = loc[t];
+        const V4<T> qt = q[t];
+        const T dx = (li.x - lt.x) - (T(ox) * g.cs + T(ox) * g.cs_lo);
+        const T dy = (li.y - lt.y) - (T(oy) * g.cs + T(oy) * g.cs_lo);
+        const T dz = (li.z - lt.z) - (T(oz) * g.cs + T(oz) * g.cs_lo);
+        const T r2 = dx * dx + dy * dy + dz * dz;
+        T rinv, r;
+        if constexpr (sizeof(T) == 4) {
+            rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+        } else {
+            rinv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
+        }
+        r = r2 * rinv;
+        T F, GmF;
+        if (sizeof(T) == 8 && r >= T(0.2) * g.a) {
+            // FP64 context: Appendix A evaluated exactly instead of interpolated
+            double Fd, Gd;
+            fg_closed_hd((double)r, (double)g.xi, (double)g.a, &Fd, &Gd);
+            const double sc = 1.0 / (6.0 * 3.14159265358979323846 * (double)g.a);
+            F = (T)(Fd * sc);
+            GmF = (T)((Gd - Fd) * sc);
+        } else {
+            const T uu = r * g.tab_inv_dr;
+            int it = (int)uu;
+            it = it > PSE_TABLE_N - 2 ? PSE_TABLE_N - 2 : it;
+            const T f = uu - T(it);
+            const V4<T> tb = table[it];
+            F = tb.x + f * tb.z;
+            GmF = tb.y + f * tb.w;
+        }
+        const T hx = dx * rinv, hy = dy * rinv, hz = dz * rinv;
+        const T dot = GmF * (hx * qt.x + hy * qt.y + hz * qt.z);
+        ax += F * qt.x + dot * hx;
+        ay += F * qt.y + dot * hy;
+        az += F * qt.z + dot * hz;
+    }
+    V4<T> o;
+    o.x = ax; o.y = ay; o.z = az; o.w = T(0);
+    return o;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_lz_matvec(int64_t N, Geom<T> g, const V4<T> *__restrict__ loc,
+                                                   const int *__restrict__ nbr_start, const int *__restrict__ nbr,
+                                                   const V4<T> *__restrict__ table, const V4<T> *basis, V4<T> *u,
+                                                   double *partials, LzState *lz) {
+    __shared__ double sh[32];
+    const int j = lz->iter;
+    if (j > PSE_MAXIT) return;  // uniform across the grid
+    const V4<T> *q = basis + (int64_t)(j - 1) * N;
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double part = 0.0;
+    if (s < N) {
+        const V4<T> o = mr_row<T>(s, g, loc, nbr_start, nbr, table, q);
+        u[s] = o;
+        const V4<T> qs = q[s];
+        part = (double)(qs.x * o.x + qs.y * o.y + qs.z * o.z);
+    }
+    part = block_sum(part, sh);
+    double total;
+    if (grid_sum_last(part, partials, &lz->counter_mv, sh, &total) && threadIdx.x == 0) {
+        const double b1 = lz->beta[j - 1];
+        const bool ok = b1 > 0.0;  // beta_{j-1} = 0: invariant subspace, the eigen kernel stops the loop
+        const double alpha = ok ? total / (b1 * b1) : 0.0;
+        lz->alpha[j] = alpha;
+        lz->c_u = ok ? (float)(1.0 / b1) : 0.f;
+        lz->c_q = ok ? (float)(alpha / b1) : 0.f;
+        lz->c_p = (ok && j >= 2) ? (float)(b1 / lz->beta[j - 2]) : 0.f;
+    }
+}
+
+template <typename T>
+__global__ void k_lz_update(int64_t N, V4<T> *basis, const V4<T> *u, double *partials, LzState *lz) {
+    __shared__ double sh[32];
+    const int j = lz->iter;
+    if (j > PSE_MAXIT) return;
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double part = 0.0;
+    if (s < N) {
+        // coefficients in the working precision; the FP64 path recomputes them exactly
+        T cu, cq, cp;
+        if constexpr (sizeof(T) == 4) {
+            cu = lz->c_u; cq = lz->c_q; cp = lz->c_p;
+        } else {
+            const double b1 = lz->beta[j - 1];
+            const bool ok = b1 > 0.0;
+            cu = ok ? 1.0 / b1 : 0.0;
+            cq = ok ? lz->alpha[j] / b1 : 0.0;
+            cp = (ok && j >= 2) ? b1 / lz->beta[j - 2] : 0.0;
+        }
+        const V4<T> us = u[s];
+        const V4<T> qj = basis[(int64_t)(j - 1) * N + s];
+        V4<T> w;
+        w.x = cu * us.x - cq * qj.x;
+        w.y = cu * us.y - cq * qj.y;
+        w.z = cu * us.z - cq * qj.z;
+        w.w = T(0);
+        if (j >= 2) {
+            const V4<T> qp = basis[(int64_t)(j - 2) * N + s];
+            w.x -= cp * qp.x;
+            w.y -= cp * qp.y;
+            w.z -= cp * qp.z;
+        }
+        basis[(int64_t)j * N + s] = w;
+        part = (double)w.x * w.x + (double)w.y * w.y + (double)w.z * w.z;
+    }
+    part = block_sum(part, sh);
+    double total;
+    if (grid_sum_last(part, partials, &lz->counter_up, sh, &total) && threadIdx.x == 0) {
+        lz->beta[j] = sqrt(total);
+        lz->iter = j + 1;
+    }
+}
+
+// ------------------------------------------------------------------ FP64 tridiagonal eigen-solve
+// One warp.  T_k (diag alpha_1..alpha_k, off-diag beta_1..beta_{k-1}) is
+// diagonalised by implicit QL sweeps with Wilkinson-type shifts (Golub & Van
+// Loan, Sec. 8.3); every lane runs the scalar recurrences redundantly and
+// applies each plane rotation to its own rows of the eigenvector matrix.
+// Then y = Q diag(sqrt(lambda)) Q^T e_1.
+__global__ void __launch_bounds__(32) k_lz_eig(LzState *lz, int max_iter, int fixed_iter, double tol,
+                                               cudaGraphConditionalHandle handle) {
+    __shared__ double Q[PSE_MAXIT][PSE_MAXIT + 1];
+    __shared__ double d[PSE_MAXIT + 1], e[PSE_MAXIT + 1], y[PSE_MAXIT + 1];
+    const int lane = threadIdx.x;
+    const int k = lz->jeig;
+    __syncwarp();
+    if (lane == 0) lz->jeig = k + 1;
+    if (k == 0) {
+        if (lane == 0 && handle) cudaGraphSetConditional(handle, 1u);
+        return;
+    }
+    for (int i = lane; i < k; i += 32) {
+        d[i] = lz->alpha[i + 1];
+        e[i] = (i + 1 < k) ? lz->beta[i + 1] : 0.0;
+        for (int c = 0; c < k; ++c) Q[i][c] = (i == c) ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    const double eps = 2.220446049250313e-16;
+    for (int l = 0; l < k; ++l) {
+        for (int sweep = 0; sweep < 60; ++sweep) {
+            int m = l;
+            for (; m < k - 1; ++m) {
+                const double dd = fabs(d[m]) + fabs(d[m + 1]);
+                if (fabs(e[m]) <= eps * dd) break;
+            }
+            if (m == l) break;
+            // shift from the leading 2x2 block
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = hypot(g, 1.0);
+            g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
+            double s = 1.0, c = 1.0, p = 0.0;
+            int i = m - 1;
+            bool deflated = false;
+            for (; i >= l; --i) {
+                const double f = s * e[i], b = c * e[i];
+                r = hypot(f, g);
+                __syncwarp();
+                if (lane == 0) e[i + 1] = r;
+                __syncwarp();
+                if (r == 0.0) {
+                    if (lane == 0) { d[i + 1] -= p; e[m] = 0.0; }
+                    __syncwarp();
+                    deflated = true;
+                    break;
+                }
+                s = f / r;
+                c = g / r;
+                g = d[i + 1] - p;
+                r = (d[i] - g) * s + 2.0 * c * b;
+                p = s * r;
+                __syncwarp();
+                if (lane == 0) d[i + 1] = g + p;
+                __syncwarp();
+                g = c * r - b;
+                for (int row = lane; row < k; row += 32) {
+                    const double qa = Q[row][i], qb = Q[row][i + 1];
+                    Q[row][i + 1] = s * qa + c * qb;
+                    Q[row][i] = c * qa - s * qb;
+                }
+                __syncwarp();
+            }
+            if (deflated && i >= l) continue;
+            __syncwarp();
+            if (lane == 0) { d[l] -= p; e[l] = g; e[m] = 0.0; }
+            __syncwarp();
+        }
+    }
+    __syncwarp();
+    // y = Q diag(sqrt(max(lambda, 0))) Q^T e_1
+    for (int row = lane; row < k; row += 32) {
+        double acc = 0.0;
+        for (int c = 0; c < k; ++c) acc += Q[row][c] * sqrt(fmax(d[c], 0.0)) * Q[0][c];
+        y[row] = acc;
+    }
+    __syncwarp();
+    double num = 0.0, den = 0.0;
+    for (int row = lane; row < k; row += 32) {
+        const double prev = (row < k - 1) ? lz->y[row] : 0.0;
+        num += (y[row] - prev) * (y[row] - prev);
+        den += y[row] * y[row];
+    }
+    num = warp_sum(num);
+    den = warp_sum(den);
+    const double rel = (k >= 2 && den > 0) ? sqrt(num / den) : 1.0;
+    bool stop;
+    int conv = 0;
+    if (fixed_iter > 0) {
+        stop = (k >= fixed_iter);
+        conv = stop;
+    } else {
+        // beta_k = 0: the Krylov space is invariant and T_k^{1/2} e_1 is exact
+        const bool breakdown = !(lz->beta[k] > 0.0);
+        conv = breakdown || (k >= 2 && rel < tol);
+        stop = conv || (k >= max_iter);
+    }
+    const double b0 = lz->beta[0];
+    __syncwarp();
+    for (int row = lane; row < k; row += 32) {
+        lz->y[row] = y[row];
+        lz->coef[row] = (float)(b0 * y[row] / lz->beta[row]);
+    }
+    if (lane == 0) {
+        lz->rel = rel;
+        if (stop) {
+            lz->J = k;
+            lz->converged = conv;
+        }
+        lz->cont = stop ? 0 : 1;
+        if (handle) cudaGraphSetConditional(handle, stop ? 0u : 1u);
+    }
+}
+
+// ------------------------------------------------------------------ final combination
+// x_s = sum_{i=1..J} coef_i q_i[s]  (+ wave part), written in caller order.
+template <typename T>
+__global__ void k_lz_final(int64_t N, const SampleArgs<T> *args, const V4<T> *pos_sorted, const V4<T> *basis,
+                           const V4<T> *uwave, const LzState *lz, bool with_wave) {
+    __shared__ T cf[PSE_MAXIT + 2];
+    __shared__ double cfd[PSE_MAXIT + 2];
+    const int J = lz->J;
+    for (int i = threadIdx.x; i < J; i += blockDim.x) {
+        if constexpr (sizeof(T) == 4) cf[i] = lz->coef[i];
+        else cfd[i] = lz->beta[0] * lz->y[i] / lz->beta[i];
+    }
+    __syncthreads();
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    T x = 0, y = 0, z = 0;
+    for (int i = 0; i < J; ++i) {
+        T c;
+        if constexpr (sizeof(T) == 4) c = cf[i];
+        else c = cfd[i];
+        const V4<T> q = basis[(int64_t)i * N + s];
+        x += c * q.x;
+        y += c * q.y;
+        z += c * q.z;
+    }
+    const int64_t o = 3 * w_bits_r(pos_sorted[s].w);
+    T wx = 0, wy = 0, wz = 0;
+    if (with_wave) {
+        const V4<T> w = uwave[s];
+        wx = w.x; wy = w.y; wz = w.z;
+    }
+    if (args->real) { args->real[o] = x; args->real[o + 1] = y; args->real[o + 2] = z; }
+    if (args->wave && with_wave) { args->wave[o] = wx; args->wave[o + 1] = wy; args->wave[o + 2] = wz; }
+    if (args->out) { args->out[o] = x + wx; args->out[o + 1] = y + wy; args->out[o + 2] = z + wz; }
+}
+
+// ------------------------------------------------------------------ caller-vector matvec
+template <typename T>
+__global__ void k_gather_vec(int64_t N, const SampleArgs<T> *args, const V4<T> *pos_sorted, V4<T> *q) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const int64_t o = 3 * w_bits_r(pos_sorted[s].w);
+    V4<T> v;
+    v.x = args->vin[o]; v.y = args->vin[o + 1]; v.z = args->vin[o + 2]; v.w = T(0);
+    q[s] = v;
+}
+
+template <typename T>
+__global__ void k_matvec_scatter(int64_t N, const SampleArgs<T> *args, Geom<T> g, const V4<T> *loc,
+                                 const int *nbr_start, const int *nbr, const V4<T> *table, const V4<T> *q,
+                                 const V4<T> *pos_sorted) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const V4<T> o = mr_row<T>(s, g, loc, nbr_start, nbr, table, q);
+    const int64_t i = 3 * w_bits_r(pos_sorted[s].w);
+    args->out[i] = o.x;
+    args->out[i + 1] = o.y;
+    args->out[i + 2] = o.z;
+}
+
+// ------------------------------------------------------------------ launchers
+static inline unsigned nb(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+template <typename T>
+void launch_lz_init(int64_t N, const SampleArgs<T> *args, int system, const Dev<T> &d, cudaStream_t s) {
+    k_lz_init<T><<<nb(N, 256), 256, 0, s>>>(N, args, system, d.pos_sorted, d.basis, d.partials, d.lz);
+}
+template <typename T> void launch_lz_matvec(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
+    k_lz_matvec<T><<<nb(N, 128), 128, 0, s>>>(N, g, d.loc_sorted, d.nbr_start, d.nbr, d.table, d.basis, d.u,
+                                              d.partials, d.lz);
+}
+template <typename T> void launch_lz_update(int64_t N, int, const Dev<T> &d, cudaStream_t s) {
+    k_lz_update<T><<<nb(N, 256), 256, 0, s>>>(N, d.basis, d.u, d.partials + (N + 127) / 128 + 8, d.lz);
+}
+void launch_lz_eig(LzState *lz, int max_iter, int fixed_iter, double tol, cudaGraphConditionalHandle h,
+                   cudaStream_t s) {
+    k_lz_eig<<<1, 32, 0, s>>>(lz, max_iter, fixed_iter, tol, h);
+}
+template <typename T>
+void launch_lz_final(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, bool with_wave, cudaStream_t s) {
+    k_lz_final<T><<<nb(N, 256), 256, 0, s>>>(N, args, d.pos_sorted, d.basis, d.uwave, d.lz, with_wave);
+}
+template <typename T>
+void launch_matvec_caller(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
+    k_gather_vec<T><<<nb(N, 256), 256, 0, s>>>(N, args, d.pos_sorted, d.u);
+    k_matvec_scatter<T><<<nb(N, 128), 128, 0, s>>>(N, args, g, d.loc_sorted, d.nbr_start, d.nbr, d.table, d.u,
+                                                   d.pos_sorted);
+}
+
+#define PSE_INST(T)                                                                                          \
+    template void launch_lz_init<T>(int64_t, const SampleArgs<T> *, int, const Dev<T> &, cudaStream_t);        \
+    template void launch_lz_matvec<T>(int64_t, Geom<T>, const Dev<T> &, cudaStream_t);                       \
+    template void launch_lz_update<T>(int64_t, int, const Dev<T> &, cudaStream_t);                           \
+    template void launch_lz_final<T>(int64_t, const SampleArgs<T> *, const Dev<T> &, bool, cudaStream_t);    \
+    template void launch_matvec_caller<T>(int64_t, const SampleArgs<T> *, Geom<T>, const Dev<T> &, cudaStream_t);
+PSE_INST(float)
+PSE_INST(double)
+#undef PSE_INST
+
+}  // namespace pse

@@ -1,0 +1,581 @@
+// C ABI of libpse (include/pse.h): context, buffers, the per-sample CUDA
+// graph and the entry points.
+//
+// One sample is one graph launch.  The graph forks after the cell sort:
+//   real branch:  neighbour list -> WHILE { matvec -> update  ||  eig(T_{j-1}) }
+//   wave branch:  k-space noise -> cuFFT C2R (x3) -> interpolation
+// and joins in the final combination kernel.  The Lanczos loop runs on the
+// device: the eigen kernel of iteration j-1 (FP64, one warp) runs beside the
+// matvec of iteration j and sets the WHILE node's condition, so the host
+// never waits inside a sample.  Per-call arguments (pointers, seed, sample
+// index) live in a small device struct refreshed by one copy before launch.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "pse_internal.cuh"
+
+using namespace pse;
+
+struct pse_ctx {
+    pse_params params;
+    pse_plan_info plan;
+    int device = 0;
+    int max_iter = PSE_MAXIT;
+    int64_t N = 0;       // size the per-N buffers and the graph were built for
+    Dev<float> df{};
+    Dev<double> dd{};
+    Geom<float> gf{};
+    Geom<double> gd{};
+    WaveGeom<float> wf{};
+    WaveGeom<double> wd{};
+    int ncell3 = 0;
+    cufftHandle fft = 0;
+    bool fft_made = false;
+    cudaStream_t s_main = nullptr, s_wave = nullptr, s_body = nullptr, s_body2 = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle cond = 0;
+    cudaStream_t last_stream = nullptr;
+    void *stage_pos = nullptr, *stage_out = nullptr;  // device staging for the host-buffer call
+    std::vector<void *> per_n;                          // buffers freed when N changes
+    std::vector<void *> per_ctx;                        // buffers freed at destroy
+};
+
+#define CK(call)                                            \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) { return PSE_ECUDA; }        \
+    } while (0)
+#define CKF(call)                                           \
+    do {                                                    \
+        cufftResult r_ = (call);                            \
+        if (r_ != CUFFT_SUCCESS) { return PSE_ECUFFT; }     \
+    } while (0)
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <typename T> Dev<T> &dev(pse_ctx *c);
+template <> Dev<float> &dev<float>(pse_ctx *c) { return c->df; }
+template <> Dev<double> &dev<double>(pse_ctx *c) { return c->dd; }
+template <typename T> Geom<T> &geom(pse_ctx *c);
+template <> Geom<float> &geom<float>(pse_ctx *c) { return c->gf; }
+template <> Geom<double> &geom<double>(pse_ctx *c) { return c->gd; }
+template <typename T> WaveGeom<T> &wgeom(pse_ctx *c);
+template <> WaveGeom<float> &wgeom<float>(pse_ctx *c) { return c->wf; }
+template <> WaveGeom<double> &wgeom<double>(pse_ctx *c) { return c->wd; }
+
+pse_status alloc(std::vector<void *> &list, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return PSE_ENOMEM;
+    }
+    list.push_back(*p);
+    return PSE_OK;
+}
+
+void free_list(std::vector<void *> &list) {
+    for (void *p : list) cudaFree(p);
+    list.clear();
+}
+
+void drop_graph(pse_ctx *c) {
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->exec = nullptr;
+    c->graph = nullptr;
+}
+
+template <typename T> void fill_geom(pse_ctx *c) {
+    const pse_plan_info &p = c->plan;
+    Geom<T> g{};
+    g.L = (T)p.L;
+    const double cs = p.L / p.ncell;
+    g.cs = (T)cs;
+    g.cs_lo = (T)(cs - (double)(T)cs);
+    g.inv_cs = (T)(p.ncell / p.L);
+    g.rc2 = (T)(p.r_cut * p.r_cut);
+    g.tab_inv_dr = (T)((PSE_TABLE_N - 1) / p.r_cut);
+    g.self_m = (T)p.self_mobility;
+    g.a = (T)p.a;
+    g.xi = (T)p.xi;
+    g.nc = p.ncell;
+    geom<T>(c) = g;
+    WaveGeom<T> w{};
+    w.M = p.M;
+    w.P = p.P;
+    w.Mh1 = p.M / 2 + 1;
+    w.kscale = (T)(2 * M_PI / p.L);
+    w.a = (T)p.a;
+    w.inv4xi2 = (T)(1.0 / (4 * p.xi * p.xi));
+    w.decay = (T)((1 - p.eta) / (8 * p.xi * p.xi));
+    w.inv_sqrtV = (T)(1.0 / sqrt(p.L * p.L * p.L));
+    const double gl = p.M / p.L;
+    w.gl_hi = (T)gl;
+    w.gl_lo = (T)(gl - (double)(T)gl);
+    w.ch2 = (T)(2 * p.xi * p.xi * p.h * p.h / p.eta);
+    w.norm = (T)(pow(2 * p.xi * p.xi / (M_PI * p.eta), 1.5) * p.h * p.h * p.h);
+    wgeom<T>(c) = w;
+}
+
+// Per-context buffers: table, spectrum, grid, FFT plan, streams, events.
+template <typename T> pse_status init_ctx(pse_ctx *c) {
+    fill_geom<T>(c);
+    Dev<T> &d = dev<T>(c);
+    const pse_plan_info &p = c->plan;
+    // F, G table in FP64, stored (F, G-F, dF, d(G-F)) / (6 pi a) in T
+    std::vector<double> F(PSE_TABLE_N), G(PSE_TABLE_N);
+    build_fg_table(p.r_cut, p.xi, p.a, PSE_TABLE_N, F.data(), G.data());
+    std::vector<V4<T>> tab(PSE_TABLE_N);
+    const double s = 1.0 / (6 * M_PI * p.a);
+    for (int i = 0; i < PSE_TABLE_N; ++i) {
+        const double f0 = F[i] * s, g0 = (G[i] - F[i]) * s;
+        const double f1 = (i + 1 < PSE_TABLE_N) ? F[i + 1] * s : f0;
+        const double g1 = (i + 1 < PSE_TABLE_N) ? (G[i + 1] - F[i + 1]) * s : g0;
+        tab[i].x = (T)f0;
+        tab[i].y = (T)g0;
+        tab[i].z = (T)(f1 - f0);
+        tab[i].w = (T)(g1 - g0);
+    }
+    pse_status st;
+    if ((st = alloc(c->per_ctx, (void **)&d.table, sizeof(V4<T>) * PSE_TABLE_N)) != PSE_OK) return st;
+    CK(cudaMemcpy(d.table, tab.data(), sizeof(V4<T>) * PSE_TABLE_N, cudaMemcpyHostToDevice));
+    const int64_t M = p.M, plane = M * M * (M / 2 + 1);
+    const size_t csize = sizeof(T) * 2;
+    if ((st = alloc(c->per_ctx, &d.spec, csize * 3 * plane)) != PSE_OK) return st;
+    if ((st = alloc(c->per_ctx, (void **)&d.grid, sizeof(T) * 3 * M * M * M)) != PSE_OK) return st;
+    if ((st = alloc(c->per_ctx, (void **)&d.lz, sizeof(LzState))) != PSE_OK) return st;
+    CK(cudaMemset(d.lz, 0, sizeof(LzState)));
+    if ((st = alloc(c->per_ctx, (void **)&d.args, sizeof(SampleArgs<T>))) != PSE_OK) return st;
+    if ((st = alloc(c->per_ctx, (void **)&d.scan_sums, sizeof(int) * PSE_SCAN_ITEMS)) != PSE_OK) return st;
+    int n[3] = {(int)M, (int)M, (int)M};
+    CKF(cufftPlanMany(&c->fft, 3, n, nullptr, 1, (int)plane, nullptr, 1, (int)(M * M * M),
+                      sizeof(T) == 4 ? CUFFT_C2R : CUFFT_Z2D, 3));
+    c->fft_made = true;
+    CK(cudaStreamCreateWithFlags(&c->s_main, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&c->s_wave, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&c->s_body, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&c->s_body2, cudaStreamNonBlocking));
+    for (int i = 0; i < 4; ++i) CK(cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming));
+    return PSE_OK;
+}
+
+// Per-N buffers.
+template <typename T> pse_status ensure(pse_ctx *c, int64_t N) {
+    if (N == c->N) return PSE_OK;
+    if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+    cudaDeviceSynchronize();
+    drop_graph(c);
+    free_list(c->per_n);
+    c->N = 0;
+    Dev<T> &d = dev<T>(c);
+    const pse_plan_info &p = c->plan;
+    const int64_t nc3 = (int64_t)p.ncell * p.ncell * p.ncell;
+    c->ncell3 = (int)nc3;
+    if (nc3 + 1 > PSE_MAX_SCAN || N + 1 > PSE_MAX_SCAN || N >= (1 << 26)) return PSE_EINVAL;
+    // neighbour capacity: spheres of radius a within r_cut + a, at most a
+    // close-packed fraction of that ball, plus slack for small overlaps
+    const double rr = p.r_cut / p.a + 1.0;
+    int64_t per = (int64_t)ceil(0.8 * rr * rr * rr) + 32;
+    int64_t cap = N * per;
+    if (cap > 0x7fffffffLL) cap = 0x7fffffffLL;
+    d.nbr_cap = cap;
+    pse_status st;
+#define A(ptr, bytes) \
+    if ((st = alloc(c->per_n, (void **)&(ptr), (bytes))) != PSE_OK) return st
+    A(d.pos_sorted, sizeof(V4<T>) * N);
+    A(d.loc_sorted, sizeof(V4<T>) * N);
+    A(d.cell_of, sizeof(int) * N);
+    A(d.slot, sizeof(int) * N);
+    A(d.cell_count, sizeof(int) * nc3);
+    A(d.cell_start, sizeof(int) * (nc3 + 1));
+    A(d.nbr_count, sizeof(int) * N);
+    A(d.nbr_start, sizeof(int) * (N + 1));
+    A(d.nbr, sizeof(int) * cap);
+    A(d.basis, sizeof(V4<T>) * N * (c->max_iter + 2));
+    A(d.u, sizeof(V4<T>) * N);
+    A(d.uwave, sizeof(V4<T>) * N);
+    A(d.partials, sizeof(double) * (2 * ((N + 127) / 128 + 16) + 64));
+    A(c->stage_pos, sizeof(T) * 3 * N);
+    A(c->stage_out, sizeof(T) * 3 * N);
+#undef A
+    c->N = N;
+    return PSE_OK;
+}
+
+// Kernels before the fork: bin, scan, scatter, per-cell sort, q_1 = z1.
+template <typename T> void pre(pse_ctx *c, int64_t N, cudaStream_t s) {
+    Dev<T> &d = dev<T>(c);
+    launch_bin<T>(N, d.args, geom<T>(c), d, s);
+    launch_scatter<T>(N, d.args, geom<T>(c), d, s);
+    launch_cellsort<T>(c->ncell3, d, s);
+    cudaMemsetAsync(&d.lz->overflow, 0, sizeof(int), s);
+}
+
+template <typename T> pse_status wave_branch(pse_ctx *c, int64_t N, cudaStream_t s) {
+    Dev<T> &d = dev<T>(c);
+    launch_wave_noise<T>(wgeom<T>(c), d.args, 0, d.spec, s);
+    CKF(cufftSetStream(c->fft, s));
+    if constexpr (sizeof(T) == 4) {
+        CKF(cufftExecC2R(c->fft, (cufftComplex *)d.spec, (cufftReal *)d.grid));
+    } else {
+        CKF(cufftExecZ2D(c->fft, (cufftDoubleComplex *)d.spec, (cufftDoubleReal *)d.grid));
+    }
+    launch_interp<T>(N, wgeom<T>(c), d, s);
+    return PSE_OK;
+}
+
+template <typename T> pse_status build_graph(pse_ctx *c) {
+    const int64_t N = c->N;
+    Dev<T> &d = dev<T>(c);
+    cudaStream_t s = c->s_main;
+    const double ltol = c->params.lanczos_tol > 0 ? c->params.lanczos_tol : c->plan.tol;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    pre<T>(c, N, s);
+    launch_lz_init<T>(N, d.args, 0, d, s);
+    cudaEventRecord(c->ev[0], s);
+    cudaStreamWaitEvent(c->s_wave, c->ev[0], 0);
+    pse_status wst = wave_branch<T>(c, N, c->s_wave);
+    cudaEventRecord(c->ev[1], c->s_wave);
+    launch_nbr<T>(N, geom<T>(c), d, false, s);
+    launch_nbr<T>(N, geom<T>(c), d, true, s);
+    // WHILE node for the Lanczos loop
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &ndeps);
+    cudaGraphNode_t node = nullptr;
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    if (e == cudaSuccess && cs == cudaStreamCaptureStatusActive) {
+        e = cudaGraphConditionalHandleCreate(&c->cond, g, 1, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess) {
+            cp.conditional.handle = c->cond;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            e = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp);
+        }
+        if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    }
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(c->s_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaEventRecord(c->ev[2], c->s_body);
+            cudaStreamWaitEvent(c->s_body2, c->ev[2], 0);
+            launch_lz_matvec<T>(N, geom<T>(c), d, c->s_body);
+            launch_lz_update<T>(N, c->max_iter, d, c->s_body);
+            launch_lz_eig(d.lz, c->max_iter, c->params.fixed_iter, ltol, c->cond, c->s_body2);
+            cudaEventRecord(c->ev[3], c->s_body2);
+            cudaStreamWaitEvent(c->s_body, c->ev[3], 0);
+            cudaGraph_t body_out = nullptr;
+            e = cudaStreamEndCapture(c->s_body, &body_out);
+        }
+    }
+    cudaStreamWaitEvent(s, c->ev[1], 0);
+    launch_lz_final<T>(N, d.args, d, true, s);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess || wst != PSE_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return wst != PSE_OK ? wst : PSE_ECUDA;
+    }
+    c->graph = graph;
+    if (cudaGraphInstantiate(&c->exec, graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        drop_graph(c);
+        return PSE_ECUDA;
+    }
+    return PSE_OK;
+}
+
+// Same kernels, launched directly with a host-side Lanczos loop (one
+// synchronisation per iteration).  Used when use_graph = -1.
+template <typename T> pse_status run_plain(pse_ctx *c, cudaStream_t s) {
+    const int64_t N = c->N;
+    Dev<T> &d = dev<T>(c);
+    const double ltol = c->params.lanczos_tol > 0 ? c->params.lanczos_tol : c->plan.tol;
+    pre<T>(c, N, s);
+    launch_lz_init<T>(N, d.args, 0, d, s);
+    pse_status st = wave_branch<T>(c, N, s);
+    if (st != PSE_OK) return st;
+    launch_nbr<T>(N, geom<T>(c), d, false, s);
+    launch_nbr<T>(N, geom<T>(c), d, true, s);
+    for (int it = 0; it < c->max_iter + 2; ++it) {
+        launch_lz_matvec<T>(N, geom<T>(c), d, s);
+        launch_lz_update<T>(N, c->max_iter, d, s);
+        launch_lz_eig(d.lz, c->max_iter, c->params.fixed_iter, ltol, 0, s);
+        int cont = 0;
+        CK(cudaMemcpyAsync(&cont, &d.lz->cont, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (!cont) break;
+    }
+    launch_lz_final<T>(N, d.args, d, true, s);
+    return PSE_OK;
+}
+
+template <typename T>
+pse_status sample_impl(pse_ctx *c, int64_t N, const T *pos, uint64_t seed, uint64_t sample, T *out, T *real,
+                       T *wave, cudaStream_t s) {
+    if (!pos || N < 1) return PSE_EINVAL;
+    if (!out && !real && !wave) return PSE_EINVAL;
+    DeviceGuard guard(c->device);
+    pse_status st = ensure<T>(c, N);
+    if (st != PSE_OK) return st;
+    const bool use_graph = c->params.use_graph >= 0;
+    if (use_graph && !c->exec) {
+        st = build_graph<T>(c);
+        if (st != PSE_OK) return st;
+    }
+    SampleArgs<T> a{};
+    a.pos = pos;
+    a.out = out;
+    a.real = real;
+    a.wave = wave;
+    a.vin = nullptr;
+    a.seed = seed;
+    a.sample = sample;
+    CK(cudaMemcpyAsync(dev<T>(c).args, &a, sizeof(a), cudaMemcpyHostToDevice, s));
+    if (use_graph) {
+        CK(cudaGraphLaunch(c->exec, s));
+    } else {
+        st = run_plain<T>(c, s);
+        if (st != PSE_OK) return st;
+    }
+    c->last_stream = s;
+    CK(cudaGetLastError());
+    return PSE_OK;
+}
+
+pse_status create_impl(pse_ctx **out, double L, double a, const pse_params *p) {
+    if (!out) return PSE_EINVAL;
+    *out = nullptr;
+    if (!p) return PSE_EINVAL;
+    pse_ctx *c = new (std::nothrow) pse_ctx();
+    if (!c) return PSE_ENOMEM;
+    c->params = *p;
+    pse_status st = pse_plan(L, a, p, &c->plan);
+    if (st != PSE_OK) { delete c; return st; }
+    if (p->max_iter < 0 || p->max_iter > PSE_MAXIT || p->fixed_iter < 0 || p->fixed_iter > PSE_MAXIT) {
+        delete c;
+        return PSE_EINVAL;
+    }
+    c->max_iter = p->max_iter > 0 ? p->max_iter : PSE_MAXIT;
+    if (c->params.fixed_iter > c->max_iter) c->max_iter = c->params.fixed_iter;
+    if (cudaGetDevice(&c->device) != cudaSuccess) { cudaGetLastError(); delete c; return PSE_ECUDA; }
+    st = (p->precision == PSE_FP64) ? init_ctx<double>(c) : init_ctx<float>(c);
+    if (st != PSE_OK) { pse_destroy(c); return st; }
+    *out = c;
+    return PSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pse_status pse_create_ex(pse_ctx **out, double L, double a, const pse_params *p) {
+    return create_impl(out, L, a, p);
+}
+
+pse_status pse_create(pse_ctx **out, double L, double a, double xi, double tol) {
+    pse_params p;
+    memset(&p, 0, sizeof(p));
+    p.tol = tol;
+    p.xi = xi;
+    p.precision = PSE_FP32;
+    return create_impl(out, L, a, &p);
+}
+
+void pse_destroy(pse_ctx *c) {
+    if (!c) return;
+    DeviceGuard guard(c->device);
+    cudaDeviceSynchronize();
+    drop_graph(c);
+    if (c->fft_made) cufftDestroy(c->fft);
+    free_list(c->per_n);
+    free_list(c->per_ctx);
+    cudaStream_t ss[4] = {c->s_main, c->s_wave, c->s_body, c->s_body2};
+    for (cudaStream_t s : ss) if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : c->ev) if (e) cudaEventDestroy(e);
+    delete c;
+}
+
+pse_status pse_get_plan(const pse_ctx *c, pse_plan_info *out) {
+    if (!c || !out) return PSE_EINVAL;
+    *out = c->plan;
+    return PSE_OK;
+}
+
+pse_status pse_sample(pse_ctx *c, int64_t N, const float *d_pos, uint64_t seed, uint64_t sample_index, float *d_out,
+                      void *stream) {
+    if (!c || c->plan.precision != PSE_FP32) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
+    if (!d_out) return PSE_EINVAL;
+    return sample_impl<float>(c, N, d_pos, seed, sample_index, d_out, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+pse_status pse_sample_parts(pse_ctx *c, int64_t N, const float *d_pos, uint64_t seed, uint64_t sample_index,
+                            float *d_out, float *d_real, float *d_wave, void *stream) {
+    if (!c || c->plan.precision != PSE_FP32) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
+    return sample_impl<float>(c, N, d_pos, seed, sample_index, d_out, d_real, d_wave, (cudaStream_t)stream);
+}
+
+pse_status pse_sample_f64(pse_ctx *c, int64_t N, const double *d_pos, uint64_t seed, uint64_t sample_index,
+                          double *d_out, double *d_real, double *d_wave, void *stream) {
+    if (!c || c->plan.precision != PSE_FP64) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
+    return sample_impl<double>(c, N, d_pos, seed, sample_index, d_out, d_real, d_wave, (cudaStream_t)stream);
+}
+
+pse_status pse_sample_host(pse_ctx *c, int64_t N, const float *h_pos, uint64_t seed, uint64_t sample_index,
+                           float *h_out, void *stream) {
+    if (!c || c->plan.precision != PSE_FP32) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
+    if (!h_pos || !h_out || N < 1) return PSE_EINVAL;
+    DeviceGuard guard(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    pse_status st = ensure<float>(c, N);
+    if (st != PSE_OK) return st;
+    CK(cudaMemcpyAsync(c->stage_pos, h_pos, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, s));
+    st = sample_impl<float>(c, N, (const float *)c->stage_pos, seed, sample_index, (float *)c->stage_out, nullptr,
+                            nullptr, s);
+    if (st != PSE_OK) return st;
+    CK(cudaMemcpyAsync(h_out, c->stage_out, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return PSE_OK;
+}
+
+pse_status pse_real_matvec(pse_ctx *c, int64_t N, const float *d_pos, const float *d_v, float *d_out,
+                           void *stream) {
+    if (!c) return PSE_EINVAL;
+    if (c->plan.precision != PSE_FP32) return PSE_ENOTSUPPORTED;
+    if (!d_pos || !d_v || !d_out || N < 1) return PSE_EINVAL;
+    DeviceGuard guard(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    pse_status st = ensure<float>(c, N);
+    if (st != PSE_OK) return st;
+    SampleArgs<float> a{};
+    a.pos = d_pos;
+    a.out = d_out;
+    a.vin = d_v;
+    CK(cudaMemcpyAsync(c->df.args, &a, sizeof(a), cudaMemcpyHostToDevice, s));
+    pre<float>(c, N, s);
+    launch_nbr<float>(N, c->gf, c->df, false, s);
+    launch_nbr<float>(N, c->gf, c->df, true, s);
+    launch_matvec_caller<float>(N, c->df.args, c->gf, c->df, s);
+    c->last_stream = s;
+    CK(cudaGetLastError());
+    return PSE_OK;
+}
+
+pse_status pse_profile_stages(pse_ctx *c, int64_t N, const float *d_pos, uint64_t seed, uint64_t sample_index,
+                              float *d_out, double *ms, int *launches, void *stream) {
+    if (!c) return PSE_EINVAL;
+    if (c->plan.precision != PSE_FP32) return PSE_ENOTSUPPORTED;
+    if (!d_pos || !d_out || !ms || !launches || N < 1) return PSE_EINVAL;
+    DeviceGuard guard(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    pse_status st = ensure<float>(c, N);
+    if (st != PSE_OK) return st;
+    Dev<float> &d = c->df;
+    SampleArgs<float> a{};
+    a.pos = d_pos;
+    a.out = d_out;
+    a.seed = seed;
+    a.sample = sample_index;
+    CK(cudaMemcpyAsync(d.args, &a, sizeof(a), cudaMemcpyHostToDevice, s));
+    const double ltol = c->params.lanczos_tol > 0 ? c->params.lanczos_tol : c->plan.tol;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int i = 0; i < PSE_NSTAGES; ++i) { ms[i] = 0.0; launches[i] = 0; }
+    auto timed = [&](int stage, int nl, auto &&fn) -> pse_status {
+        if (cudaEventRecord(e0, s) != cudaSuccess) return PSE_ECUDA;
+        pse_status r = fn();
+        if (r != PSE_OK) return r;
+        if (cudaEventRecord(e1, s) != cudaSuccess) return PSE_ECUDA;
+        if (cudaEventSynchronize(e1) != cudaSuccess) return PSE_ECUDA;
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms[stage] += t;
+        launches[stage] += nl;
+        return PSE_OK;
+    };
+    const int nscan = 3;
+    pse_status r = PSE_OK;
+    if (r == PSE_OK) r = timed(PSE_STAGE_CELLS, 1 + nscan, [&] { launch_bin<float>(N, d.args, c->gf, d, s); return PSE_OK; });
+    if (r == PSE_OK) r = timed(PSE_STAGE_SORT, 2, [&] {
+        launch_scatter<float>(N, d.args, c->gf, d, s);
+        launch_cellsort<float>(c->ncell3, d, s);
+        cudaMemsetAsync(&d.lz->overflow, 0, sizeof(int), s);
+        return PSE_OK; });
+    if (r == PSE_OK) r = timed(PSE_STAGE_REAL_NOISE, 1, [&] { launch_lz_init<float>(N, d.args, 0, d, s); return PSE_OK; });
+    if (r == PSE_OK) r = timed(PSE_STAGE_WAVE_NOISE, 1, [&] { launch_wave_noise<float>(c->wf, d.args, 0, d.spec, s); return PSE_OK; });
+    if (r == PSE_OK) r = timed(PSE_STAGE_FFT, 0, [&] {
+        CKF(cufftSetStream(c->fft, s));
+        CKF(cufftExecC2R(c->fft, (cufftComplex *)d.spec, (cufftReal *)d.grid));
+        return PSE_OK; });
+    if (r == PSE_OK) r = timed(PSE_STAGE_INTERP, 1, [&] { launch_interp<float>(N, c->wf, d, s); return PSE_OK; });
+    if (r == PSE_OK) r = timed(PSE_STAGE_NEIGHBOURS, 2 + nscan, [&] {
+        launch_nbr<float>(N, c->gf, d, false, s);
+        launch_nbr<float>(N, c->gf, d, true, s);
+        return PSE_OK; });
+    for (int it = 0; r == PSE_OK && it < c->max_iter + 2; ++it) {
+        r = timed(PSE_STAGE_MATVEC, 1, [&] { launch_lz_matvec<float>(N, c->gf, d, s); return PSE_OK; });
+        if (r == PSE_OK) r = timed(PSE_STAGE_LANCZOS_UPDATE, 1, [&] { launch_lz_update<float>(N, c->max_iter, d, s); return PSE_OK; });
+        if (r == PSE_OK) r = timed(PSE_STAGE_EIGEN, 1, [&] {
+            launch_lz_eig(d.lz, c->max_iter, c->params.fixed_iter, ltol, 0, s);
+            return PSE_OK; });
+        int cont = 0;
+        if (r == PSE_OK && cudaMemcpy(&cont, &d.lz->cont, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) r = PSE_ECUDA;
+        if (!cont) break;
+    }
+    if (r == PSE_OK) r = timed(PSE_STAGE_FINAL, 1, [&] { launch_lz_final<float>(N, d.args, d, true, s); return PSE_OK; });
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->last_stream = s;
+    if (r != PSE_OK) return r;
+    CK(cudaGetLastError());
+    return PSE_OK;
+}
+
+pse_status pse_get_stats(pse_ctx *c, pse_stats *out) {
+    if (!c || !out) return PSE_EINVAL;
+    memset(out, 0, sizeof(*out));
+    if (c->N == 0) return PSE_OK;
+    DeviceGuard guard(c->device);
+    if (c->last_stream) CK(cudaStreamSynchronize(c->last_stream));
+    CK(cudaDeviceSynchronize());
+    LzState lz;
+    const LzState *src = c->plan.precision == PSE_FP64 ? c->dd.lz : c->df.lz;
+    const int *ns = c->plan.precision == PSE_FP64 ? c->dd.nbr_start : c->df.nbr_start;
+    CK(cudaMemcpy(&lz, src, sizeof(lz), cudaMemcpyDeviceToHost));
+    int np = 0;
+    CK(cudaMemcpy(&np, ns + c->N, sizeof(int), cudaMemcpyDeviceToHost));
+    out->lanczos_iters = lz.J;
+    out->converged = lz.converged;
+    out->lanczos_rel_change = lz.rel;
+    out->n_pairs = np;
+    out->overflow = lz.overflow;
+    if (lz.overflow) return PSE_ENOMEM;
+    if (!lz.converged && lz.J > 0) return PSE_ENOTCONVERGED;
+    return PSE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,263 @@
+// Internal declarations shared by the CUDA translation units of libpse.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "pse.h"
+
+#define PSE_MAXIT 64          // Lanczos cap (basis holds PSE_MAXIT + 2 vectors)
+#define PSE_TABLE_N 4096      // entries of the F, G table on [0, r_cut]
+#define PSE_SCAN_ITEMS 4096   // elements per block of the device scan
+#define PSE_MAX_SCAN (PSE_SCAN_ITEMS * PSE_SCAN_ITEMS)
+
+namespace pse {
+
+// 16-byte (float) / 32-byte (double) aligned 4-vector.
+template <typename T> struct alignas(4 * sizeof(T)) V4 { T x, y, z, w; };
+
+// Geometry of one periodic system, by value into kernels.
+template <typename T> struct Geom {
+    T L;          // box side
+    T cs;         // cell side (>= r_cut)
+    T cs_lo;      // cs - (T)cs in the next precision (compensation; 0 for double)
+    T inv_cs;
+    T rc2;        // r_cut^2
+    T tab_inv_dr; // (PSE_TABLE_N - 1) / r_cut
+    T self_m;     // self mobility of eq. self, divided by 6 pi a
+    T a;          // sphere radius (FP64 path: closed-form F, G for r >= 0.2 a)
+    T xi;         // splitting parameter
+    int nc;       // cells per side
+};
+
+// Wave-space parameters of one system.
+template <typename T> struct WaveGeom {
+    int M, P, Mh1;       // grid side, support, M/2 + 1
+    T kscale;            // 2 pi / L
+    T a;                 // sphere radius
+    T inv4xi2;           // 1 / (4 xi^2)
+    T decay;             // (1 - eta) / (8 xi^2)
+    T inv_sqrtV;         // V^{-1/2}
+    T gl_hi, gl_lo;      // M / L split in two (compensated product x * M / L)
+    T ch2;               // 2 xi^2 h^2 / eta: Gaussian exponent per squared grid unit
+    T norm;              // (2 xi^2 / (pi eta))^{3/2} h^3
+};
+
+// Per-sample arguments, read by the kernels from device memory so that one
+// instantiated graph serves every call.
+template <typename T> struct SampleArgs {
+    const T *pos;   // 3N caller positions
+    T *out;         // 3N or null
+    T *real;        // 3N or null
+    T *wave;        // 3N or null
+    const T *vin;   // 3N caller vector for the matvec path, or null
+    uint64_t seed;
+    uint64_t sample;
+};
+
+// Device-side state of the Lanczos iteration (one system).
+struct LzState {
+    double alpha[PSE_MAXIT + 2];
+    double beta[PSE_MAXIT + 2];     // beta[0] = ||z1||
+    double y[PSE_MAXIT + 2];        // T_j^{1/2} e_1 of the last checked j
+    float coef[PSE_MAXIT + 2];      // beta0 * y_i / beta_{i-1}, i = 1..J (float for the final pass)
+    float c_u, c_q, c_p;            // update coefficients of the current iteration
+    int iter;                       // iteration the matvec/update kernels run next
+    int jeig;                       // T_j the eigen kernel processes next
+    int J;                          // accepted iteration count
+    int converged;
+    int cont;                       // loop continues (host-loop mode reads this)
+    double rel;                     // last ||y_j - y_{j-1}|| / ||y_j||
+    unsigned int counter_mv, counter_up, counter_init;
+    int overflow;                   // neighbour list capacity exceeded
+};
+
+// Appendix A, cases 1 and 2 (FP64): 6 pi eta a M^(r) = F (I - rr) + G rr.
+// Used by the host table builder and by the FP64 device matvec.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline void fg_closed_hd(double r, double xi, double a, double *F, double *G) {
+    const double sp = 1.7724538509055160273;  // sqrt(pi)
+    const double x2 = xi * xi, x3 = x2 * xi, x4 = x2 * x2;
+    const double r2 = r * r, r3 = r2 * r;
+    const double rm = r - 2 * a, rp = r + 2 * a, am = 2 * a - r;
+    const double e1 = exp(-r2 * x2), e2 = exp(-rm * rm * x2), e3 = exp(-rp * rp * x2);
+    const double c4 = erfc(r * xi), c5 = erfc(rm * xi), c6 = erfc(rp * xi);
+    const double A4 = 4 * a * a;
+    const double f1 = (18 * r2 * x2 + 3) / (64 * sp * a * r2 * x3);
+    const double f2 = (2 * x2 * am * (A4 + 4 * a * r + 9 * r2) - 2 * a - 3 * r) / (128 * sp * a * r3 * x3);
+    const double f3 = (-2 * x2 * rp * (A4 - 4 * a * r + 9 * r2) + 2 * a - 3 * r) / (128 * sp * a * r3 * x3);
+    const double f4 = (3 - 36 * r2 * r2 * x4) / (128 * a * r3 * x4);
+    const double f5 = (4 * x4 * rm * rm * (A4 + 4 * a * r + 9 * r2) - 3) / (256 * a * r3 * x4);
+    const double f6 = (4 * x4 * rp * rp * (A4 - 4 * a * r + 9 * r2) - 3) / (256 * a * r3 * x4);
+    const double g1 = (6 * r2 * x2 - 3) / (32 * sp * a * r2 * x3);
+    const double g2 = (-2 * x2 * rm * rm * (2 * a + 3 * r) + 2 * a + 3 * r) / (64 * sp * a * r3 * x3);
+    const double g3 = (2 * x2 * rp * rp * (2 * a - 3 * r) - 2 * a + 3 * r) / (64 * sp * a * r3 * x3);
+    const double g4 = -3 * (4 * r2 * r2 * x4 + 1) / (64 * a * r3 * x4);
+    const double g5 = (3 - 4 * x4 * am * am * am * (2 * a + 3 * r)) / (128 * a * r3 * x4);
+    const double g6 = (3 - 4 * x4 * (2 * a - 3 * r) * rp * rp * rp) / (128 * a * r3 * x4);
+    double f0 = 0.0, g0 = 0.0;
+    if (r <= 2 * a) {
+        f0 = -rm * rm * (A4 + 4 * a * r + 9 * r2) / (32 * a * r3);
+        g0 = am * am * am * (2 * a + 3 * r) / (16 * a * r3);
+    }
+    *F = f0 + f1 * e1 + f2 * e2 + f3 * e3 + f4 * c4 + f5 * c5 + f6 * c6;
+    *G = g0 + g1 * e1 + g2 * e2 + g3 * e3 + g4 * c4 + g5 * c5 + g6 * c6;
+}
+
+// ------------------------------------------------------------------ device helpers
+#ifdef __CUDACC__
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 multiplies,
+// Weyl-bumped key between rounds.
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Four N(0,1) from one Philox block: uniforms (2k+1) 2^-24 from the top 23
+// bits (exact in float), Box-Muller with sincospi.
+template <typename T> struct Normals4 { T v[4]; };
+
+__device__ __forceinline__ void bm_pair(uint32_t xa, uint32_t xb, float &z0, float &z1) {
+    const float ua = ((float)(xa >> 9) + 0.5f) * 1.1920928955078125e-07f;  // 2^-23
+    const float ub = ((float)(xb >> 9) + 0.5f) * 1.1920928955078125e-07f;
+    const float r = sqrtf(-2.0f * logf(ua));
+    float s, c;
+    sincospif(2.0f * ub, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+__device__ __forceinline__ void bm_pair(uint32_t xa, uint32_t xb, double &z0, double &z1) {
+    const double ua = ((double)(xa >> 9) + 0.5) * 1.1920928955078125e-07;
+    const double ub = ((double)(xb >> 9) + 0.5) * 1.1920928955078125e-07;
+    const double r = sqrt(-2.0 * log(ua));
+    double s, c;
+    sincospi(2.0 * ub, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
+template <typename T>
+__device__ __forceinline__ Normals4<T> normals4(uint32_t element, uint32_t stream, uint64_t seed,
+                                                 uint64_t sample) {
+    const uint4 x = philox(make_uint4(element, stream, (uint32_t)sample, (uint32_t)(sample >> 32)),
+                           make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    Normals4<T> n;
+    bm_pair(x.x, x.y, n.v[0], n.v[1]);
+    bm_pair(x.z, x.w, n.v[2], n.v[3]);
+    return n;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum (blockDim.x a multiple of 32, <= 1024); result valid in all threads.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (wid == 0) t = warp_sum(t);
+    if (threadIdx.x == 0) sh[0] = t;
+    __syncthreads();
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// Deterministic grid-wide sum: every block stores its partial, the last block
+// to arrive (atomic ticket, no waiting) adds the partials in block order.
+// Returns true in the last block, with *total valid in all its threads.
+__device__ __forceinline__ bool grid_sum_last(double partial, double *partials, unsigned int *counter,
+                                              double *sh, double *total) {
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = partial;
+        __threadfence();
+        const unsigned int t = atomicAdd(counter, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double acc = 0.0;
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) acc += __ldcg(partials + b);
+    *total = block_sum(acc, sh);
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+#endif
+
+// ------------------------------------------------------------------ host launchers
+struct Buffers;  // defined in pse_api.cu
+
+template <typename T> struct Dev {
+    // sorted particle data
+    V4<T> *pos_sorted;   // wrapped caller positions, w = original index (int bits)
+    V4<T> *loc_sorted;   // offsets from the cell corner, w = cell id (int bits)
+    int *cell_of;        // per caller particle
+    int *slot;           // per caller particle
+    int *cell_count;     // ncell^3
+    int *cell_start;     // ncell^3 + 1
+    int *nbr_count;      // N
+    int *nbr_start;      // N + 1
+    int *nbr;            // capacity entries: (t << 5) | stencil code
+    int64_t nbr_cap;
+    int *scan_sums;      // PSE_SCAN_ITEMS
+    V4<T> *basis;        // (PSE_MAXIT + 2) * N, q_1 .. q_{J+1}
+    V4<T> *u;            // matvec output
+    V4<T> *uwave;        // wave part at sorted particles
+    double *partials;    // per-block partial sums
+    LzState *lz;
+    V4<T> *table;        // PSE_TABLE_N: (F, G - F, dF, d(G-F)) / (6 pi a)
+    void *spec;          // 3 * M * M * Mh1 complex
+    T *grid;             // 3 * M^3 real
+    SampleArgs<T> *args;
+};
+
+// cells / scan / neighbour list
+template <typename T> void launch_bin(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d,
+                                      cudaStream_t s);
+void launch_scan(const int *in, int *out, int64_t n, int *sums, cudaStream_t s);
+template <typename T> void launch_scatter(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d,
+                                          cudaStream_t s);
+template <typename T> void launch_cellsort(int ncell3, const Dev<T> &d, cudaStream_t s);
+template <typename T> void launch_nbr(int64_t N, Geom<T> g, const Dev<T> &d, bool fill, cudaStream_t s);
+
+// Lanczos
+template <typename T> void launch_lz_init(int64_t N, const SampleArgs<T> *args, int system, const Dev<T> &d,
+                                          cudaStream_t s);
+template <typename T> void launch_lz_matvec(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s);
+template <typename T> void launch_lz_update(int64_t N, int max_iter, const Dev<T> &d, cudaStream_t s);
+void launch_lz_eig(LzState *lz, int max_iter, int fixed_iter, double tol, cudaGraphConditionalHandle h,
+                   cudaStream_t s);
+template <typename T> void launch_lz_final(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, bool with_wave,
+                                           cudaStream_t s);
+// plain matvec of a caller vector (sorted gather -> M_r -> scatter back)
+template <typename T> void launch_matvec_caller(int64_t N, const SampleArgs<T> *args, Geom<T> g,
+                                                const Dev<T> &d, cudaStream_t s);
+
+// wave space
+template <typename T> void launch_wave_noise(WaveGeom<T> w, const SampleArgs<T> *args, int system, void *spec,
+                                             cudaStream_t s);
+template <typename T> void launch_interp(int64_t N, WaveGeom<T> w, const Dev<T> &d, cudaStream_t s);
+
+// host-side setup (FP64 arithmetic)
+void build_fg_table(double r_cut, double xi, double a, int n, double *F, double *G);
+double self_real(double xi, double a);
+
+}  // namespace pse

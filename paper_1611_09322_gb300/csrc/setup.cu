@@ -1,0 +1,189 @@
+// Host-side FP64 setup: Sec. II C parameter planning and the tabulated
+// real-space scalars F(r), G(r) of Appendix A.
+#include <math.h>
+#include <string.h>
+
+#include "pse_internal.cuh"
+
+namespace pse {
+
+static const double kPi = 3.14159265358979323846;
+
+static void fg_closed(double r, double xi, double a, double *F, double *G) { fg_closed_hd(r, xi, a, F, G); }
+
+// Appendix A, case 3 (eq. self), dimensionless.
+double self_real(double xi, double a) {
+    return (1.0 - exp(-4 * a * a * xi * xi) + 4 * sqrt(kPi) * a * xi * erfc(2 * a * xi)) / (4 * sqrt(kPi) * xi * a);
+}
+
+// Near r = 0 the closed form cancels catastrophically (terms ~ 1/(r^3 xi^4)).
+// There F = F_RPY - F_w: the free-space RPY tensor (overlap branch of
+// eq. RPY_free_space) minus the k-integral of eqs. int1/int2 taken with the
+// weight H instead of 1 - H.  H decays like a Gaussian, so composite Simpson
+// on [0, 16 xi] converges to rounding.
+static void fg_small(double r, double xi, double a, double *F, double *G) {
+    const int n = 8192;  // even
+    const double kmax = 16.0 * xi, hk = kmax / n;
+    double sF = 0.0, sG = 0.0;
+    for (int i = 0; i <= n; ++i) {
+        const double k = i * hk;
+        const double q = k * k / (4 * xi * xi);
+        const double Hk = (1 + q) * exp(-q);
+        const double ka = k * a;
+        const double s2 = (ka > 0) ? (sin(ka) / ka) * (sin(ka) / ka) : 1.0;
+        const double x = k * r;
+        double kF, kG;
+        if (x < 1e-2) {
+            const double x2 = x * x;
+            kF = 2.0 / 3.0 - 2.0 * x2 / 15.0 + x2 * x2 / 140.0;
+            kG = 1.0 / 3.0 - x2 / 30.0 + x2 * x2 / 840.0;
+        } else {
+            kF = (x * cos(x) + (x * x - 1) * sin(x)) / (x * x * x);
+            kG = (sin(x) - x * cos(x)) / (x * x * x);
+        }
+        const double wgt = (i == 0 || i == n) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+        sF += wgt * Hk * s2 * kF;
+        sG += wgt * Hk * s2 * kG;
+    }
+    sF *= hk / 3.0;
+    sG *= hk / 3.0;
+    const double Fw = sF / (2 * kPi * kPi) * 6 * kPi * a;
+    const double Gw = sG / (kPi * kPi) * 6 * kPi * a;
+    const double A = 1.0 - 9.0 * r / (32.0 * a), B = 3.0 * r / (32.0 * a);
+    *F = A - Fw;
+    *G = A + B - Gw;
+}
+
+void build_fg_table(double r_cut, double xi, double a, int n, double *F, double *G) {
+    const double dr = r_cut / (n - 1);
+    for (int i = 0; i < n; ++i) {
+        const double r = i * dr;
+        if (i == 0) {
+            F[i] = G[i] = self_real(xi, a);
+        } else if (r < 0.2 * a) {
+            fg_small(r, xi, a, &F[i], &G[i]);
+        } else {
+            fg_closed(r, xi, a, &F[i], &G[i]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ Sec. II C parameters
+static double kcut_bound(double k, double xi, double a) {
+    return (4.0 / k * exp(-k * k / (4 * xi * xi)) - sqrt(kPi) / xi * erfc(k / (2 * xi))) / (2 * kPi * a);
+}
+
+static double quad_err(int P, double m) {
+    return exp(-kPi * kPi * P * P / (2 * m * m)) + erfc(m / sqrt(2.0));
+}
+
+// Minimiser over m of quad_err(P, m): bisection on the sign of its derivative.
+static double best_m(int P) {
+    const double c = kPi * kPi * P * P / 2.0;
+    double lo = 0.5, hi = 2.0 * P;
+    for (int it = 0; it < 200; ++it) {
+        const double m = 0.5 * (lo + hi);
+        const double d = exp(-c / (m * m)) * 2 * c / (m * m * m) - sqrt(2 / kPi) * exp(-m * m / 2);
+        if (d < 0) lo = m; else hi = m;
+    }
+    return 0.5 * (lo + hi);
+}
+
+static int smooth2357(int n) {
+    const int p[4] = {2, 3, 5, 7};
+    for (int i = 0; i < 4; ++i) while (n % p[i] == 0) n /= p[i];
+    return n == 1;
+}
+
+}  // namespace pse
+
+using namespace pse;
+
+extern "C" pse_status pse_plan(double L, double a, const pse_params *p, pse_plan_info *out) {
+    if (!p || !out) return PSE_EINVAL;
+    if (!(L > 0) || !(a > 0) || !isfinite(L) || !isfinite(a)) return PSE_EINVAL;
+    const double tol = p->tol;
+    if (!(tol > 0) || tol > 0.1) return PSE_EINVAL;
+    const double xi = (p->xi > 0) ? p->xi : 0.5 / a;
+    if (!isfinite(xi)) return PSE_EINVAL;
+    if (p->precision != PSE_FP32 && p->precision != PSE_FP64) return PSE_EINVAL;
+    memset(out, 0, sizeof(*out));
+    out->L = L;
+    out->a = a;
+    out->xi = xi;
+    out->tol = tol;
+    out->precision = p->precision;
+    out->r_cut = sqrt(log(1.0 / tol)) / xi;
+    if (out->r_cut >= 0.5 * L) return PSE_EINVAL;
+    // k_cut: bisection on the decreasing eq. errbound bound
+    double lo = 1e-6, hi = 1.0;
+    while (kcut_bound(hi, xi, a) > tol) hi *= 2.0;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (kcut_bound(mid, xi, a) > tol) lo = mid; else hi = mid;
+    }
+    out->k_cut = hi;
+    int P;
+    if (p->support_P > 0) {
+        P = p->support_P;
+    } else {
+        P = 3;
+        while (quad_err(P, best_m(P)) > tol) ++P;
+    }
+    out->P = P;
+    out->m = best_m(P);
+    int M;
+    if (p->grid_M > 0) {
+        M = p->grid_M;
+    } else {
+        M = (int)ceil(out->k_cut * L / kPi - 1e-9);
+        if (M < P + 1) M = P + 1;
+        if (M < 4) M = 4;
+        while (!smooth2357(M)) ++M;
+        while (pow(P * (L / M) * xi / out->m, 2) > 1.0) {
+            ++M;
+            while (!smooth2357(M)) ++M;
+        }
+    }
+    if (M < P + 1 || M > 2048) return PSE_EINVAL;
+    out->M = M;
+    out->h = L / M;
+    out->eta = pow(P * out->h * xi / out->m, 2);
+    if (out->eta > 1.0 + 1e-12 && p->grid_M > 0) return PSE_EINVAL;
+    // neighbour-search cells: side >= r_cut with a 1e-4 margin for float binning
+    int nc = (int)floor(L / (out->r_cut * (1.0 + 1e-4)));
+    if (nc < 2) nc = 2;
+    if (nc > 1024) nc = 1024;
+    out->ncell = nc;
+    out->self_mobility = self_real(xi, a) / (6 * kPi * a);
+    return PSE_OK;
+}
+
+extern "C" pse_status pse_real_scalars(double xi, double a, int64_t n, const double *r, double *F, double *G) {
+    if (!(xi > 0) || !(a > 0) || n < 0 || (n > 0 && (!r || !F || !G))) return PSE_EINVAL;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(r[i] >= 0) || !isfinite(r[i])) return PSE_EINVAL;
+        if (r[i] == 0.0) {
+            F[i] = G[i] = self_real(xi, a);
+        } else if (r[i] < 0.2 * a) {
+            fg_small(r[i], xi, a, &F[i], &G[i]);
+        } else {
+            fg_closed(r[i], xi, a, &F[i], &G[i]);
+        }
+    }
+    return PSE_OK;
+}
+
+extern "C" const char *pse_strerror(pse_status s) {
+    switch (s) {
+        case PSE_OK: return "ok";
+        case PSE_EINVAL: return "invalid argument";
+        case PSE_ENOMEM: return "out of memory or capacity exceeded";
+        case PSE_ECUDA: return "CUDA runtime error";
+        case PSE_ECUFFT: return "cuFFT error";
+        case PSE_ENOTCONVERGED: return "Lanczos iteration did not converge within max_iter";
+        case PSE_ENOTSUPPORTED: return "operation not supported for this context";
+        case PSE_ENOTREADY: return "required state (e.g. preconditioner weights) not set";
+    }
+    return "unknown status";
+}
