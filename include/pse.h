@@ -192,6 +192,32 @@ pse_status pse_profile_stages(pse_ctx *ctx, int64_t N, const float *d_pos, uint6
                               uint64_t sample_index, float *d_out, double *ms, int *launches,
                               void *stream);
 
+/* Near-field product d_out = M_r d_v, like pse_real_matvec, for callers that
+ * cannot allocate device memory: code that must not call cudaMalloc (or any
+ * allocating library routine) because device memory is owned by someone else
+ * -- an application's own memory pool, a plugin with a fixed footprint, a
+ * real-time loop that may not block in the allocator.  The paper has no
+ * counterpart; this is a deployment variant of pse_real_matvec.
+ *   L, a, xi, tol: as for pse_create (xi <= 0 selects 0.5/a);
+ *   d_pos, d_v, d_out: 3N float32 device arrays in the caller's order.
+ * No context and no allocation: all scratch (cell list, sorted positions,
+ * neighbour list, F/G table) lives in one static device array of about
+ * 11.8 MB that every GPU loading this library reserves until the process
+ * exits.  Limits: N <= 16384, ncell^3 <= 32768 cells (box side up to about
+ * 32 r_cut), at most 2,621,440 directed neighbour pairs; beyond the first
+ * two it returns PSE_EINVAL before launching anything, beyond the last
+ * PSE_ENOMEM after the run (the output is then incomplete).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and fills the F/G table; make that first call
+ * before any stream capture.  The table is rebuilt when (xi, a, r_cut)
+ * change.  The array is shared by every call and keeps the last call's
+ * contents (what must start at zero is cleared on each call); calls that
+ * overlap on the GPU -- concurrent streams, threads or devices sharing a
+ * context -- race on it, so serialise them.  The call synchronises `stream`
+ * before returning. */
+pse_status pse_real_matvec_noalloc(double L, double a, double xi, double tol, int64_t N,
+                                   const float *d_pos, const float *d_v, float *d_out, void *stream);
+
 /* Statistics of the last sample (synchronises the context's last stream). */
 pse_status pse_get_stats(pse_ctx *ctx, pse_stats *out);
 

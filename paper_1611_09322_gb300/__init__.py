@@ -14,7 +14,7 @@ import numpy as np
 from . import _lib
 from ._lib import PSE_FP32, PSE_FP64, PseError, pse_params, pse_plan_info, pse_stats
 
-__all__ = ["Sampler", "pse_plan", "pse_real_scalars", "PseError", "PSE_FP32", "PSE_FP64", "make_params"]
+__all__ = ["Sampler", "pse_plan", "pse_real_scalars", "pse_real_matvec_noalloc", "PseError", "PSE_FP32", "PSE_FP64", "make_params"]
 
 
 def make_params(tol=1e-3, xi=0.5, precision=PSE_FP32, max_iter=0, fixed_iter=0, grid_M=0, support_P=0,
@@ -51,6 +51,18 @@ def pse_real_scalars(r, xi, a=1.0):
     vp = lambda x: x.ctypes.data_as(ctypes.c_void_p)
     _lib.check(lib.pse_real_scalars(xi, a, r.size, vp(r), vp(F), vp(G)), "pse_real_scalars")
     return F, G
+
+
+def pse_real_matvec_noalloc(L, a, xi, tol, pos, v, out):
+    """M_r v through the allocation-free entry point (static device scratch, N <= 16384).
+
+    For callers that may not allocate device memory: `out` must be
+    preallocated by the caller; nothing is allocated by the library.
+    """
+    lib = _lib.load()
+    _lib.check(lib.pse_real_matvec_noalloc(L, a, xi, tol, pos.shape[0], _ptr(pos), _ptr(v), _ptr(out), _stream()),
+               "pse_real_matvec_noalloc")
+    return out
 
 
 def _stream():

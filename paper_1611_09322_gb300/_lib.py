@@ -71,6 +71,8 @@ SIGNATURES = {
     "pse_get_stats": (_ST, [_VP, ctypes.POINTER(pse_stats)]),
     "pse_strerror": (ctypes.c_char_p, [_ST]),
     "pse_profile_stages": (_ST, [_VP, _I64, _VP, _U64, _U64, _VP, _VP, _VP, _VP]),
+    "pse_real_matvec_noalloc": (_ST, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _I64,
+                                      _VP, _VP, _VP, _VP]),
     "pse_real_scalars": (_ST, [ctypes.c_double, ctypes.c_double, _I64, _VP, _VP, _VP]),
 }
 
