@@ -180,7 +180,7 @@ def main():
     torch.cuda.set_device(dev)
 
     pos, L, _ = workloads.hard_spheres(N_PART, PHI, SEED_POS)
-    s = Sampler(L, 1.0, xi=XI, tol=TOL)
+    s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=1)
     d_pos = torch.from_numpy(pos).to(dev)
     out = torch.empty_like(d_pos)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)

@@ -65,7 +65,11 @@ typedef struct {
     int use_graph;       /* >= 0 (default): one CUDA graph per sample with a
                             device-side Lanczos loop; -1: plain stream launches
                             with a host-side loop (one sync per iteration)      */
-    int reserved[7];
+    int autotune;        /* bit 0: time cuFFT C2R for every 2,3,5,7-smooth grid
+                            size in [M, 1.12 M] at creation and keep the fastest
+                            (a finer grid only lowers the NUFFT error); needs
+                            the GPU at pse_create_ex.  0: the Sec. II C grid.   */
+    int reserved[6];
 } pse_params;
 
 /* Parameters derived from (L, a, xi, tol) by Sec. II C of the paper:
@@ -202,11 +206,12 @@ pse_status pse_profile_stages(pse_ctx *ctx, int64_t N, const float *d_pos, uint6
  *   d_pos, d_v, d_out: 3N float32 device arrays in the caller's order.
  * No context and no allocation: all scratch (cell list, sorted positions,
  * neighbour list, F/G table) lives in one static device array of about
- * 11.8 MB that every GPU loading this library reserves until the process
+ * 12 MB that every GPU loading this library reserves until the process
  * exits.  Limits: N <= 16384, ncell^3 <= 32768 cells (box side up to about
- * 32 r_cut), at most 2,621,440 directed neighbour pairs; beyond the first
- * two it returns PSE_EINVAL before launching anything, beyond the last
- * PSE_ENOMEM after the run (the output is then incomplete).
+ * 32 r_cut), at most 2,621,440 / N neighbours within r_cut per particle
+ * (160 at N = 16384); beyond the first two it returns PSE_EINVAL before
+ * launching anything, beyond the last PSE_ENOMEM after the run (the output
+ * is then incomplete).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) and fills the F/G table; make that first call
  * before any stream capture.  The table is rebuilt when (xi, a, r_cut)

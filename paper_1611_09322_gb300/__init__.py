@@ -18,7 +18,7 @@ __all__ = ["Sampler", "pse_plan", "pse_real_scalars", "pse_real_matvec_noalloc",
 
 
 def make_params(tol=1e-3, xi=0.5, precision=PSE_FP32, max_iter=0, fixed_iter=0, grid_M=0, support_P=0,
-                use_precond=0, lanczos_tol=0.0, use_graph=True):
+                use_precond=0, lanczos_tol=0.0, use_graph=True, autotune=0):
     p = pse_params()
     p.tol = tol
     p.xi = xi
@@ -30,6 +30,7 @@ def make_params(tol=1e-3, xi=0.5, precision=PSE_FP32, max_iter=0, fixed_iter=0, 
     p.use_precond = use_precond
     p.lanczos_tol = lanczos_tol
     p.use_graph = 0 if use_graph else -1
+    p.autotune = autotune
     return p
 
 

@@ -30,7 +30,7 @@ class pse_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("xi", ctypes.c_double), ("precision", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("fixed_iter", ctypes.c_int), ("grid_M", ctypes.c_int),
                 ("support_P", ctypes.c_int), ("use_precond", ctypes.c_int), ("lanczos_tol", ctypes.c_double),
-                ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class pse_plan_info(ctypes.Structure):

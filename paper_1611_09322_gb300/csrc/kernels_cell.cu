@@ -1,9 +1,9 @@
 // Cell list, device scan and near-field neighbour list (the linked-cell
 // search the paper's real-space sum uses, Sec. III), sm_103a.
 //
-// Particles are binned into ncell^3 cells of side >= r_cut, counting-sorted
-// into cell order (deterministic: ties in a cell are ordered by caller
-// index), and every sorted particle gets a CSR list of the particles within
+// Particles are binned into ncell^3 cells of side >= r_cut (ids in 4x4x4
+// brick-major order), counting-sorted into cell order (deterministic: ties in a cell are ordered by caller
+// index), and every sorted particle gets an ELL list of the particles within
 // r_cut.  Each entry packs the neighbour's sorted index with the 3x3x3
 // stencil offset of its cell, so pair vectors are formed from cell-local
 // offsets: d = (l_i - l_t) - dc * cs, accurate to a few float ulps of the
@@ -40,20 +40,21 @@ __global__ void k_bin(int64_t N, const SampleArgs<T> *args, Geom<T> g, int *cell
     const T x = wrap_box(p[0], g.L), y = wrap_box(p[1], g.L), z = wrap_box(p[2], g.L);
     const int cx = cell_coord(x, g.inv_cs, g.nc), cy = cell_coord(y, g.inv_cs, g.nc),
               cz = cell_coord(z, g.inv_cs, g.nc);
-    const int c = (cx * g.nc + cy) * g.nc + cz;
+    const int c = cell_id(cx, cy, cz, g.nb);
     cell_of[i] = c;
     slot[i] = atomicAdd(count + c, 1);
 }
 
 template <typename T>
 __global__ void k_scatter(int64_t N, const SampleArgs<T> *args, Geom<T> g, const int *cell_of, const int *slot,
-                          const int *start, V4<T> *pos_sorted, V4<T> *loc_sorted) {
+                          const int *start, V4<T> *pos_sorted, V4<T> *loc_sorted, Rec<T> *rec) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
     const T *p = args->pos + 3 * i;
     const T x = wrap_box(p[0], g.L), y = wrap_box(p[1], g.L), z = wrap_box(p[2], g.L);
     const int c = cell_of[i];
-    const int cz = c % g.nc, cy = (c / g.nc) % g.nc, cx = c / (g.nc * g.nc);
+    int cx, cy, cz;
+    cell_xyz(c, g.nb, cx, cy, cz);
     const int dst = start[c] + slot[i];
     V4<T> a;
     a.x = x; a.y = y; a.z = z;
@@ -67,6 +68,7 @@ __global__ void k_scatter(int64_t N, const SampleArgs<T> *args, Geom<T> g, const
     if constexpr (sizeof(T) == 4) l.w = __int_as_float(c);
     else l.w = __longlong_as_double((long long)c);
     loc_sorted[dst] = l;
+    rec[dst].l = l;
 }
 
 template <typename T> __device__ __forceinline__ long long w_bits(T w) {
@@ -77,7 +79,7 @@ template <typename T> __device__ __forceinline__ long long w_bits(T w) {
 // Insertion sort of each cell's entries by caller index: makes the sorted
 // order, and every summation order downstream, independent of atomics.
 template <typename T>
-__global__ void k_cellsort(int ncell3, const int *start, V4<T> *pos_sorted, V4<T> *loc_sorted) {
+__global__ void k_cellsort(int ncell3, const int *start, V4<T> *pos_sorted, V4<T> *loc_sorted, Rec<T> *rec) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell3) return;
     const int b = start[c], e = start[c + 1];
@@ -93,52 +95,65 @@ __global__ void k_cellsort(int ncell3, const int *start, V4<T> *pos_sorted, V4<T
         pos_sorted[j + 1] = pa;
         loc_sorted[j + 1] = la;
     }
+    for (int i = b; i < e; ++i) rec[i].l = loc_sorted[i];
 }
 
-// One thread per sorted particle: count (fill = false) or write (fill = true)
-// the neighbours within r_cut over the 27 stencil cells.  With ncell = 2 the
-// same cell appears under two offsets; r_cut < L/2 leaves at most one image
-// of each pair inside r_cut, so the distance test keeps the right one.
-template <typename T, bool FILL>
-__global__ void k_nbr(int64_t N, Geom<T> g, const V4<T> *loc, const int *cell_start, int *count,
-                      const int *nbr_start, int *nbr, int64_t cap, int *overflow) {
+// One thread per sorted particle, one pass: every neighbour within r_cut over
+// the 27 stencil cells goes to ELL column cnt (nbr[cnt * N + s], coalesced
+// across a warp when counts agree) as (t << 6) | stencil code.  With
+// ncell = 2 the same cell appears under two offsets; r_cut < L/2 leaves at
+// most one image of each pair inside r_cut, so the distance test keeps the
+// right one.  Lists longer than K are cut and flag an overflow.
+template <typename T>
+__global__ void __launch_bounds__(128) k_nbr(int64_t N, Geom<T> g, const V4<T> *__restrict__ loc,
+                                             const int *__restrict__ cell_start, int *count, int *nbr, int K,
+                                             int *overflow, unsigned long long *n_pairs) {
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= N) return;
-    const V4<T> li = loc[s];
-    const int c = (int)w_bits(li.w);
-    const int nc = g.nc;
-    const int cz = c % nc, cy = (c / nc) % nc, cx = c / (nc * nc);
     int cnt = 0;
-    int64_t base = FILL ? nbr_start[s] : 0;
-    for (int ox = -1; ox <= 1; ++ox) {
-        const int ax = (cx + ox + nc) % nc;
-        for (int oy = -1; oy <= 1; ++oy) {
-            const int ay = (cy + oy + nc) % nc;
-            for (int oz = -1; oz <= 1; ++oz) {
-                const int az = (cz + oz + nc) % nc;
-                const int code = (ox + 1) * 9 + (oy + 1) * 3 + (oz + 1);
-                const int c2 = (ax * nc + ay) * nc + az;
-                const int b = cell_start[c2], e = cell_start[c2 + 1];
-                for (int t = b; t < e; ++t) {
-                    if (t == s && code == 13) continue;
-                    const V4<T> lt = loc[t];
-                    const T dx = (li.x - lt.x) - T(ox) * g.cs;
-                    const T dy = (li.y - lt.y) - T(oy) * g.cs;
-                    const T dz = (li.z - lt.z) - T(oz) * g.cs;
-                    const T r2 = dx * dx + dy * dy + dz * dz;
-                    if (r2 < g.rc2) {
-                        if (FILL) {
-                            const int64_t pos = base + cnt;
-                            if (pos < cap) nbr[pos] = (t << 5) | code;
-                            else atomicExch(overflow, 1);
+    if (s < N) {
+        const V4<T> li = loc[s];
+        const int c = (int)w_bits(li.w);
+        const int nc = g.nc;
+        int cx, cy, cz;
+        cell_xyz(c, g.nb, cx, cy, cz);
+        for (int ox = -1; ox <= 1; ++ox) {
+            const int ax = (cx + ox + nc) % nc;
+            const T sx = T(ox) * g.cs + T(ox) * g.cs_lo;
+            for (int oy = -1; oy <= 1; ++oy) {
+                const int ay = (cy + oy + nc) % nc;
+                const T sy = T(oy) * g.cs + T(oy) * g.cs_lo;
+                for (int oz = -1; oz <= 1; ++oz) {
+                    const int az = (cz + oz + nc) % nc;
+                    const T sz = T(oz) * g.cs + T(oz) * g.cs_lo;
+                    const int code = ((ox + 1) << 4) | ((oy + 1) << 2) | (oz + 1);
+                    const int c2 = cell_id(ax, ay, az, g.nb);
+                    const int b = cell_start[c2], e = cell_start[c2 + 1];
+                    for (int t = b; t < e; ++t) {
+                        if (t == s && code == 21) continue;
+                        const V4<T> lt = loc[t];
+                        const T dx = (li.x - lt.x) - sx;
+                        const T dy = (li.y - lt.y) - sy;
+                        const T dz = (li.z - lt.z) - sz;
+                        const T r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 < g.rc2) {
+                            if (cnt < K) nbr[(int64_t)cnt * N + s] = (t << 6) | code;
+                            ++cnt;
                         }
-                        ++cnt;
                     }
                 }
             }
         }
+        if (cnt > K) {
+            atomicExch(overflow, 1);
+            cnt = K;
+        }
+        count[s] = cnt;
     }
-    if (!FILL) count[s] = cnt;
+    // pair total for the statistics: one atomic per warp
+    int tot = cnt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(n_pairs, (unsigned long long)tot);
 }
 
 // ------------------------------------------------------------------ exclusive scan
@@ -198,6 +213,19 @@ __global__ void k_scan_add(int *out, int64_t n, const int *sums) {
     if (i < n) out[i] += sums[i / PSE_SCAN_ITEMS];
 }
 
+int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            n = 132;
+    }
+    return n;
+}
+
 void launch_scan(const int *in, int *out, int64_t n, int *sums, cudaStream_t s) {
     const int nb = (int)((n + PSE_SCAN_ITEMS - 1) / PSE_SCAN_ITEMS);
     if (nb > 0) k_scan_block<<<nb, 1024, 0, s>>>(in, out, n, sums);
@@ -210,7 +238,7 @@ static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / 
 
 template <typename T>
 void launch_bin(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
-    const int64_t nc3 = (int64_t)g.nc * g.nc * g.nc;
+    const int64_t nc3 = cell_slots(g.nc);
     cudaMemsetAsync(d.cell_count, 0, sizeof(int) * nc3, s);
     k_bin<T><<<nblk(N, 256), 256, 0, s>>>(N, args, g, d.cell_of, d.slot, d.cell_count);
     launch_scan(d.cell_count, d.cell_start, nc3, d.scan_sums, s);
@@ -219,29 +247,23 @@ void launch_bin(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d
 template <typename T>
 void launch_scatter(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
     k_scatter<T><<<nblk(N, 256), 256, 0, s>>>(N, args, g, d.cell_of, d.slot, d.cell_start, d.pos_sorted,
-                                              d.loc_sorted);
+                                              d.loc_sorted, d.rec);
 }
 
 template <typename T> void launch_cellsort(int ncell3, const Dev<T> &d, cudaStream_t s) {
-    k_cellsort<T><<<nblk(ncell3, 256), 256, 0, s>>>(ncell3, d.cell_start, d.pos_sorted, d.loc_sorted);
+    k_cellsort<T><<<nblk(ncell3, 256), 256, 0, s>>>(ncell3, d.cell_start, d.pos_sorted, d.loc_sorted, d.rec);
 }
 
-template <typename T> void launch_nbr(int64_t N, Geom<T> g, const Dev<T> &d, bool fill, cudaStream_t s) {
-    if (!fill) {
-        k_nbr<T, false><<<nblk(N, 128), 128, 0, s>>>(N, g, d.loc_sorted, d.cell_start, d.nbr_count, nullptr,
-                                                     nullptr, 0, nullptr);
-        launch_scan(d.nbr_count, d.nbr_start, N, d.scan_sums, s);
-    } else {
-        k_nbr<T, true><<<nblk(N, 128), 128, 0, s>>>(N, g, d.loc_sorted, d.cell_start, nullptr, d.nbr_start,
-                                                    d.nbr, d.nbr_cap, &d.lz->overflow);
-    }
+template <typename T> void launch_nbr(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
+    k_nbr<T><<<nblk(N, 128), 128, 0, s>>>(N, g, d.loc_sorted, d.cell_start, d.nbr_count, d.nbr,
+                                          nbr_k(N, d.nbr_cap), &d.lz->overflow, &d.lz->n_pairs);
 }
 
 #define PSE_INST(T)                                                                                       \
     template void launch_bin<T>(int64_t, const SampleArgs<T> *, Geom<T>, const Dev<T> &, cudaStream_t);     \
     template void launch_scatter<T>(int64_t, const SampleArgs<T> *, Geom<T>, const Dev<T> &, cudaStream_t); \
     template void launch_cellsort<T>(int, const Dev<T> &, cudaStream_t);                                  \
-    template void launch_nbr<T>(int64_t, Geom<T>, const Dev<T> &, bool, cudaStream_t);
+    template void launch_nbr<T>(int64_t, Geom<T>, const Dev<T> &, cudaStream_t);
 PSE_INST(float)
 PSE_INST(double)
 #undef PSE_INST

@@ -12,8 +12,9 @@
 //           ||y_j - [y_{j-1}; 0]|| / ||y_j|| < tol  (= ||x_j - x_{j-1}|| / ||x_j||
 //           for an orthonormal basis)
 // and finally x = beta_0 sum_i y_i q_i / beta_{i-1}.  Scalars are FP64; the
-// per-block partial sums are reduced in block order by the last block to
-// arrive, so results do not depend on scheduling.
+// reducing kernels run persistent grids (a fixed multiple of the SM count)
+// and their per-block partial sums are added in block order by the last
+// block to arrive, so results do not depend on scheduling.
 #include "pse_internal.cuh"
 
 namespace pse {
@@ -23,24 +24,35 @@ template <typename T> __device__ __forceinline__ long long w_bits_r(T w) {
     else return __double_as_longlong(w);
 }
 
+// per-thread partial: float for the float path (summed per warp in float,
+// then in double), double for the FP64 path
+template <typename T> struct Part { using type = float; };
+template <> struct Part<double> { using type = double; };
+
+template <typename T> __device__ __forceinline__ double block_total(typename Part<T>::type v, double *sh) {
+    if constexpr (sizeof(T) == 4) return block_sum_fw(v, sh);
+    else return block_sum(v, sh);
+}
+
 // ------------------------------------------------------------------ init: q_1 = z1, beta_0
 template <typename T>
-__global__ void k_lz_init(int64_t N, const SampleArgs<T> *args, int system, const V4<T> *pos_sorted, V4<T> *q1,
-                          double *partials, LzState *lz) {
+__global__ void __launch_bounds__(256) k_lz_init(int64_t N, const SampleArgs<T> *args, int system,
+                                                 const V4<T> *pos_sorted, V4<T> *q1, Rec<T> *rec, double *partials,
+                                                 LzState *lz) {
     __shared__ double sh[32];
-    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double part = 0.0;
-    if (s < N) {
+    typename Part<T>::type part = 0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t orig = (uint32_t)w_bits_r(pos_sorted[s].w);
         const Normals4<T> z = normals4<T>(orig, 2u * system, args->seed, args->sample);
         V4<T> v;
         v.x = z.v[0]; v.y = z.v[1]; v.z = z.v[2]; v.w = T(0);
         q1[s] = v;
-        part = (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z;
+        rec[s].q = v;
+        part += v.x * v.x + v.y * v.y + v.z * v.z;
     }
-    part = block_sum(part, sh);
+    const double bsum = block_total<T>(part, sh);
     double total;
-    if (grid_sum_last(part, partials, &lz->counter_init, sh, &total) && threadIdx.x == 0) {
+    if (grid_sum_last(bsum, partials, &lz->counter_init, sh, &total) && threadIdx.x == 0) {
         lz->beta[0] = sqrt(total);
         lz->iter = 1;
         lz->jeig = 0;
@@ -52,81 +64,121 @@ __global__ void k_lz_init(int64_t N, const SampleArgs<T> *args, int system, cons
 }
 
 // ------------------------------------------------------------------ near-field matvec
-// One thread per sorted particle: u_s = self q_s + sum_t [F (I - rr) + G rr] q_t,
-// F, G linearly interpolated from the FP64-built table (stored / 6 pi a).
-template <typename T>
-__device__ __forceinline__ V4<T> mr_row(int64_t s, Geom<T> g, const V4<T> *__restrict__ loc,
-                                        const int *__restrict__ nbr_start, const int *__restrict__ nbr,
-                                        const V4<T> *__restrict__ table, const V4<T> *__restrict__ q) {
-    const V4<T> li = loc[s];
-    const V4<T> qi = q[s];
-    T ax = g.self_m * qi.x, ay = g.self_m * qi.y, az = g.self_m * qi.z;
-    const int e0 = nbr_start[s], e1 = nbr_start[s + 1];
-    for (int e = e0; e < e1; ++e) {
-        const int ent = __ldg(nbr + e);
-        const int t = ent >> 5, code = ent & 31;
-        const int ox = code / 9 - 1, oy = (code / 3) % 3 - 1, oz = code % 3 - 1;
-        const V4<T> lt = loc[t];
-        const V4<T> qt = q[t];
-        const T dx = (li.x - lt.x) - (T(ox) * g.cs + T(ox) * g.cs_lo);
-        const T dy = (li.y - lt.y) - (T(oy) * g.cs + T(oy) * g.cs_lo);
-        const T dz = (li.z - lt.z) - (T(oz) * g.cs + T(oz) * g.cs_lo);
-        const T r2 = dx * dx + dy * dy + dz * dz;
-        T rinv, r;
-        if constexpr (sizeof(T) == 4) {
-            rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-        } else {
-            rinv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
-        }
-        r = r2 * rinv;
-        T F, GmF;
-        if (sizeof(T) == 8 && r >= T(0.2) * g.a) {
-            // FP64 context: Appendix A evaluated exactly instead of interpolated
-            double Fd, Gd;
-            fg_closed_hd((double)r, (double)g.xi, (double)g.a, &Fd, &Gd);
-            const double sc = 1.0 / (6.0 * 3.14159265358979323846 * (double)g.a);
-            F = (T)(Fd * sc);
-            GmF = (T)((Gd - Fd) * sc);
-        } else {
-            const T uu = r * g.tab_inv_dr;
-            int it = (int)uu;
-            it = it > PSE_TABLE_N - 2 ? PSE_TABLE_N - 2 : it;
-            const T f = uu - T(it);
-            const V4<T> tb = table[it];
-            F = tb.x + f * tb.z;
-            GmF = tb.y + f * tb.w;
-        }
-        const T hx = dx * rinv, hy = dy * rinv, hz = dz * rinv;
-        const T dot = GmF * (hx * qt.x + hy * qt.y + hz * qt.z);
-        ax += F * qt.x + dot * hx;
-        ay += F * qt.y + dot * hy;
-        az += F * qt.z + dot * hz;
-    }
-    V4<T> o;
-    o.x = ax; o.y = ay; o.z = az; o.w = T(0);
-    return o;
-}
+// u_s = self q_s + sum_t [F (I - rr) + G rr] q_t over the ELL list of s, F and
+// G linearly interpolated from the FP64-built table (stored / 6 pi a).  A
+// group of TPP consecutive threads shares one particle: thread g of the
+// group takes entries g, g + TPP, ... and the group sums by shuffles.  Each
+// neighbour costs one 4-byte list entry and one 32-byte record; a thread
+// issues MV_ILP list loads, then MV_ILP record loads, before any arithmetic,
+// so that many independent gathers are in flight.
+#define MV_ILP 4
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_lz_matvec(int64_t N, Geom<T> g, const V4<T> *__restrict__ loc,
-                                                   const int *__restrict__ nbr_start, const int *__restrict__ nbr,
-                                                   const V4<T> *__restrict__ table, const V4<T> *basis, V4<T> *u,
-                                                   double *partials, LzState *lz) {
+__device__ __forceinline__ void pair_fg(T r, const Geom<T> &g, const V4<T> *__restrict__ table, T &F, T &GmF) {
+    if (sizeof(T) == 8 && r >= T(0.2) * g.a) {
+        // FP64 context: Appendix A evaluated exactly instead of interpolated
+        double Fd, Gd;
+        fg_closed_hd((double)r, (double)g.xi, (double)g.a, &Fd, &Gd);
+        const double sc = 1.0 / (6.0 * 3.14159265358979323846 * (double)g.a);
+        F = (T)(Fd * sc);
+        GmF = (T)((Gd - Fd) * sc);
+    } else {
+        const T uu = r * g.tab_inv_dr;
+        int it = (int)uu;
+        it = it > PSE_TABLE_N - 2 ? PSE_TABLE_N - 2 : it;
+        const T f = uu - T(it);
+        const V4<T> tb = table[it];
+        F = tb.x + f * tb.z;
+        GmF = tb.y + f * tb.w;
+    }
+}
+
+// Row s of M_r q without the self term, summed over the TPP-thread group.
+template <typename T, int TPP>
+__device__ __forceinline__ void mr_row_part(int64_t N, int64_t s, int lane_g, bool active, const Geom<T> &g,
+                                            const Rec<T> *__restrict__ rec, const int *__restrict__ count,
+                                            const int *__restrict__ nbr, const V4<T> *__restrict__ table,
+                                            V4<T> &li, V4<T> &qi, T &ax, T &ay, T &az) {
+    ax = ay = az = T(0);
+    if (active) {
+        const Rec<T> ri = rec[s];
+        li = ri.l;
+        qi = ri.q;
+        const int cnt = count[s];
+        for (int k0 = lane_g; k0 < cnt; k0 += MV_ILP * TPP) {
+            int ent[MV_ILP];
+#pragma unroll
+            for (int u = 0; u < MV_ILP; ++u) {
+                const int k = k0 + u * TPP;
+                ent[u] = k < cnt ? __ldg(nbr + (int64_t)k * N + s) : -1;
+            }
+            Rec<T> rt[MV_ILP];
+#pragma unroll
+            for (int u = 0; u < MV_ILP; ++u) rt[u] = rec[ent[u] >= 0 ? (ent[u] >> 6) : s];
+#pragma unroll
+            for (int u = 0; u < MV_ILP; ++u) {
+                if (ent[u] < 0) continue;
+                const int e = ent[u];
+                const int ox = ((e >> 4) & 3) - 1, oy = ((e >> 2) & 3) - 1, oz = (e & 3) - 1;
+                const T dx = (li.x - rt[u].l.x) - (T(ox) * g.cs + T(ox) * g.cs_lo);
+                const T dy = (li.y - rt[u].l.y) - (T(oy) * g.cs + T(oy) * g.cs_lo);
+                const T dz = (li.z - rt[u].l.z) - (T(oz) * g.cs + T(oz) * g.cs_lo);
+                const T r2 = dx * dx + dy * dy + dz * dz;
+                T rinv;
+                if constexpr (sizeof(T) == 4) rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                else rinv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
+                T F, GmF;
+                pair_fg(r2 * rinv, g, table, F, GmF);
+                const T hx = dx * rinv, hy = dy * rinv, hz = dz * rinv;
+                const T dot = GmF * (hx * rt[u].q.x + hy * rt[u].q.y + hz * rt[u].q.z);
+                ax += F * rt[u].q.x + dot * hx;
+                ay += F * rt[u].q.y + dot * hy;
+                az += F * rt[u].q.z + dot * hz;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = TPP / 2; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        az += __shfl_xor_sync(0xffffffffu, az, o);
+    }
+}
+
+template <typename T, int TPP>
+__global__ void __launch_bounds__(128) k_lz_matvec(int64_t N, Geom<T> g, const Rec<T> *__restrict__ rec,
+                                                   const int *__restrict__ count, const int *__restrict__ nbr,
+                                                   const V4<T> *__restrict__ table, V4<T> *u, double *partials,
+                                                   LzState *lz) {
     __shared__ double sh[32];
     const int j = lz->iter;
     if (j > PSE_MAXIT) return;  // uniform across the grid
-    const V4<T> *q = basis + (int64_t)(j - 1) * N;
-    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double part = 0.0;
-    if (s < N) {
-        const V4<T> o = mr_row<T>(s, g, loc, nbr_start, nbr, table, q);
-        u[s] = o;
-        const V4<T> qs = q[s];
-        part = (double)(qs.x * o.x + qs.y * o.y + qs.z * o.z);
+    typename Part<T>::type part = 0;
+    const int lane_g = threadIdx.x % TPP;
+    const int64_t per_block = blockDim.x / TPP;
+    // contiguous chunk of particles per block (spatial locality across
+    // iterations); whole groups stride together so group shuffles converge
+    const int64_t chunk = ((N + gridDim.x - 1) / gridDim.x + per_block - 1) / per_block * per_block;
+    const int64_t end = (blockIdx.x + 1) * chunk < N ? (blockIdx.x + 1) * chunk : N;
+    for (int64_t base = blockIdx.x * chunk; base < end; base += per_block) {
+        const int64_t s = base + threadIdx.x / TPP;
+        const bool active = s < end;
+        V4<T> li, qi;
+        T ax, ay, az;
+        mr_row_part<T, TPP>(N, s, lane_g, active, g, rec, count, nbr, table, li, qi, ax, ay, az);
+        if (active && lane_g == 0) {
+            V4<T> o;
+            o.x = ax + g.self_m * qi.x;
+            o.y = ay + g.self_m * qi.y;
+            o.z = az + g.self_m * qi.z;
+            o.w = T(0);
+            u[s] = o;
+            part += qi.x * o.x + qi.y * o.y + qi.z * o.z;
+        }
     }
-    part = block_sum(part, sh);
+    const double bsum = block_total<T>(part, sh);
     double total;
-    if (grid_sum_last(part, partials, &lz->counter_mv, sh, &total) && threadIdx.x == 0) {
+    if (grid_sum_last(bsum, partials, &lz->counter_mv, sh, &total) && threadIdx.x == 0) {
         const double b1 = lz->beta[j - 1];
         const bool ok = b1 > 0.0;  // beta_{j-1} = 0: invariant subspace, the eigen kernel stops the loop
         const double alpha = ok ? total / (b1 * b1) : 0.0;
@@ -138,43 +190,47 @@ __global__ void __launch_bounds__(128) k_lz_matvec(int64_t N, Geom<T> g, const V
 }
 
 template <typename T>
-__global__ void k_lz_update(int64_t N, V4<T> *basis, const V4<T> *u, double *partials, LzState *lz) {
+__global__ void __launch_bounds__(256) k_lz_update(int64_t N, V4<T> *basis, Rec<T> *rec, const V4<T> *u,
+                                                   double *partials, LzState *lz) {
     __shared__ double sh[32];
     const int j = lz->iter;
     if (j > PSE_MAXIT) return;
-    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double part = 0.0;
-    if (s < N) {
-        // coefficients in the working precision; the FP64 path recomputes them exactly
-        T cu, cq, cp;
-        if constexpr (sizeof(T) == 4) {
-            cu = lz->c_u; cq = lz->c_q; cp = lz->c_p;
-        } else {
-            const double b1 = lz->beta[j - 1];
-            const bool ok = b1 > 0.0;
-            cu = ok ? 1.0 / b1 : 0.0;
-            cq = ok ? lz->alpha[j] / b1 : 0.0;
-            cp = (ok && j >= 2) ? b1 / lz->beta[j - 2] : 0.0;
-        }
+    // coefficients in the working precision; the FP64 path recomputes them exactly
+    T cu, cq, cp;
+    if constexpr (sizeof(T) == 4) {
+        cu = lz->c_u; cq = lz->c_q; cp = lz->c_p;
+    } else {
+        const double b1 = lz->beta[j - 1];
+        const bool ok = b1 > 0.0;
+        cu = ok ? 1.0 / b1 : 0.0;
+        cq = ok ? lz->alpha[j] / b1 : 0.0;
+        cp = (ok && j >= 2) ? b1 / lz->beta[j - 2] : 0.0;
+    }
+    const V4<T> *qj = basis + (int64_t)(j - 1) * N;
+    const V4<T> *qp = basis + (int64_t)(j - 2) * N;
+    V4<T> *qn = basis + (int64_t)j * N;
+    typename Part<T>::type part = 0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
         const V4<T> us = u[s];
-        const V4<T> qj = basis[(int64_t)(j - 1) * N + s];
+        const V4<T> a = qj[s];
         V4<T> w;
-        w.x = cu * us.x - cq * qj.x;
-        w.y = cu * us.y - cq * qj.y;
-        w.z = cu * us.z - cq * qj.z;
+        w.x = cu * us.x - cq * a.x;
+        w.y = cu * us.y - cq * a.y;
+        w.z = cu * us.z - cq * a.z;
         w.w = T(0);
         if (j >= 2) {
-            const V4<T> qp = basis[(int64_t)(j - 2) * N + s];
-            w.x -= cp * qp.x;
-            w.y -= cp * qp.y;
-            w.z -= cp * qp.z;
+            const V4<T> b = qp[s];
+            w.x -= cp * b.x;
+            w.y -= cp * b.y;
+            w.z -= cp * b.z;
         }
-        basis[(int64_t)j * N + s] = w;
-        part = (double)w.x * w.x + (double)w.y * w.y + (double)w.z * w.z;
+        qn[s] = w;
+        rec[s].q = w;
+        part += w.x * w.x + w.y * w.y + w.z * w.z;
     }
-    part = block_sum(part, sh);
+    const double bsum = block_total<T>(part, sh);
     double total;
-    if (grid_sum_last(part, partials, &lz->counter_up, sh, &total) && threadIdx.x == 0) {
+    if (grid_sum_last(bsum, partials, &lz->counter_up, sh, &total) && threadIdx.x == 0) {
         lz->beta[j] = sqrt(total);
         lz->iter = j + 1;
     }
@@ -337,41 +393,54 @@ __global__ void k_lz_final(int64_t N, const SampleArgs<T> *args, const V4<T> *po
 
 // ------------------------------------------------------------------ caller-vector matvec
 template <typename T>
-__global__ void k_gather_vec(int64_t N, const SampleArgs<T> *args, const V4<T> *pos_sorted, V4<T> *q) {
+__global__ void k_gather_vec(int64_t N, const SampleArgs<T> *args, const V4<T> *pos_sorted, Rec<T> *rec) {
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= N) return;
     const int64_t o = 3 * w_bits_r(pos_sorted[s].w);
     V4<T> v;
     v.x = args->vin[o]; v.y = args->vin[o + 1]; v.z = args->vin[o + 2]; v.w = T(0);
-    q[s] = v;
+    rec[s].q = v;
 }
 
-template <typename T>
-__global__ void k_matvec_scatter(int64_t N, const SampleArgs<T> *args, Geom<T> g, const V4<T> *loc,
-                                 const int *nbr_start, const int *nbr, const V4<T> *table, const V4<T> *q,
-                                 const V4<T> *pos_sorted) {
-    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= N) return;
-    const V4<T> o = mr_row<T>(s, g, loc, nbr_start, nbr, table, q);
+template <typename T, int TPP>
+__global__ void __launch_bounds__(128) k_matvec_scatter(int64_t N, const SampleArgs<T> *args, Geom<T> g,
+                                                        const Rec<T> *rec, const int *count, const int *nbr,
+                                                        const V4<T> *table, const V4<T> *pos_sorted) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t s = tid / TPP;
+    const int lane_g = (int)(tid % TPP);
+    const bool active = s < N;
+    V4<T> li, qi;
+    T ax, ay, az;
+    mr_row_part<T, TPP>(N, s, lane_g, active, g, rec, count, nbr, table, li, qi, ax, ay, az);
+    if (!active || lane_g != 0) return;
     const int64_t i = 3 * w_bits_r(pos_sorted[s].w);
-    args->out[i] = o.x;
-    args->out[i + 1] = o.y;
-    args->out[i + 2] = o.z;
+    args->out[i] = ax + g.self_m * qi.x;
+    args->out[i + 1] = ay + g.self_m * qi.y;
+    args->out[i + 2] = az + g.self_m * qi.z;
 }
 
 // ------------------------------------------------------------------ launchers
 static inline unsigned nb(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+// persistent grid: at most `per_sm` resident blocks per SM
+static inline unsigned pgrid(int64_t work_items, int items_per_block, int per_sm) {
+    const int64_t need = (work_items + items_per_block - 1) / items_per_block;
+    const int64_t cap = (int64_t)num_sms() * per_sm;
+    return (unsigned)(need < cap ? (need > 0 ? need : 1) : cap);
+}
+
+static constexpr int kMvTpp = 4;
 
 template <typename T>
 void launch_lz_init(int64_t N, const SampleArgs<T> *args, int system, const Dev<T> &d, cudaStream_t s) {
-    k_lz_init<T><<<nb(N, 256), 256, 0, s>>>(N, args, system, d.pos_sorted, d.basis, d.partials, d.lz);
+    k_lz_init<T><<<pgrid(N, 256, 8), 256, 0, s>>>(N, args, system, d.pos_sorted, d.basis, d.rec, d.partials, d.lz);
 }
 template <typename T> void launch_lz_matvec(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
-    k_lz_matvec<T><<<nb(N, 128), 128, 0, s>>>(N, g, d.loc_sorted, d.nbr_start, d.nbr, d.table, d.basis, d.u,
-                                              d.partials, d.lz);
+    k_lz_matvec<T, kMvTpp><<<pgrid(N, 128 / kMvTpp, 16), 128, 0, s>>>(N, g, d.rec, d.nbr_count, d.nbr, d.table,
+                                                                        d.u, d.partials, d.lz);
 }
 template <typename T> void launch_lz_update(int64_t N, int, const Dev<T> &d, cudaStream_t s) {
-    k_lz_update<T><<<nb(N, 256), 256, 0, s>>>(N, d.basis, d.u, d.partials + (N + 127) / 128 + 8, d.lz);
+    k_lz_update<T><<<pgrid(N, 256, 8), 256, 0, s>>>(N, d.basis, d.rec, d.u, d.partials + num_sms() * 16 + 32, d.lz);
 }
 void launch_lz_eig(LzState *lz, int max_iter, int fixed_iter, double tol, cudaGraphConditionalHandle h,
                    cudaStream_t s) {
@@ -383,9 +452,9 @@ void launch_lz_final(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, bool
 }
 template <typename T>
 void launch_matvec_caller(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
-    k_gather_vec<T><<<nb(N, 256), 256, 0, s>>>(N, args, d.pos_sorted, d.u);
-    k_matvec_scatter<T><<<nb(N, 128), 128, 0, s>>>(N, args, g, d.loc_sorted, d.nbr_start, d.nbr, d.table, d.u,
-                                                   d.pos_sorted);
+    k_gather_vec<T><<<nb(N, 256), 256, 0, s>>>(N, args, d.pos_sorted, d.rec);
+    k_matvec_scatter<T, kMvTpp><<<nb(N * kMvTpp, 128), 128, 0, s>>>(N, args, g, d.rec, d.nbr_count, d.nbr, d.table,
+                                                                    d.pos_sorted);
 }
 
 #define PSE_INST(T)                                                                                          \

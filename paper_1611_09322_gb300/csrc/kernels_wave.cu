@@ -113,48 +113,77 @@ __device__ __forceinline__ void support(double x, const WaveGeom<double> &w, int
     u = rem + 0.5 * w.P - 1.0;
 }
 
-#define PSE_PMAX 12
+#define PSE_PMAX 16
 
-// One thread per sorted particle: u_w = norm * sum_{P^3} g_x g_y g_z v(node),
-// separable weights exp(-ch2 (u - p)^2) per axis, periodic node indices.
-template <typename T>
+__device__ __forceinline__ int wrap_grid(int i, int M) {  // valid for i in [-M, 2M)
+    i = i < 0 ? i + M : i;
+    return i >= M ? i - M : i;
+}
+
+// G lanes per sorted particle (G = 8, 16 or 32 divides the warp):
+// u_w = norm * sum_{P^3} g_x g_y g_z v(node), separable weights
+// exp(-ch2 (u - p)^2) per axis, periodic node indices.  Lane g of the group
+// owns the (y, z) node pairs g, g + G, ...; for each x node the group's loads
+// are runs of consecutive floats along z (the grid's contiguous axis).  The
+// first P lanes of the group evaluate the 3P one-dimensional weights, shared
+// by shuffles inside the group.
+template <typename T, int G>
 __global__ void __launch_bounds__(128) k_interp(int64_t N, WaveGeom<T> w, const V4<T> *__restrict__ pos_sorted,
                                                 const T *__restrict__ grid, V4<T> *uwave) {
-    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= N) return;
-    const V4<T> p = pos_sorted[s];
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t s = tid / G;
+    const int lg = threadIdx.x % G;
+    const int gbase = (threadIdx.x & 31) - lg;  // first lane of this group in the warp
+    const bool active = s < N;
+    const V4<T> p = pos_sorted[active ? s : 0];
     const int M = w.M, P = w.P;
     const int64_t M3 = (int64_t)M * M * M;
-    T wx[PSE_PMAX], wy[PSE_PMAX], wz[PSE_PMAX];
-    int ix[PSE_PMAX], iy[PSE_PMAX], iz[PSE_PMAX];
-    int i0;
-    T u;
-    support(p.x, w, i0, u);
-    for (int k = 0; k < P; ++k) { const T d = u - T(k); wx[k] = exp_t(-w.ch2 * d * d); ix[k] = ((i0 + k) % M + M) % M; }
-    support(p.y, w, i0, u);
-    for (int k = 0; k < P; ++k) { const T d = u - T(k); wy[k] = exp_t(-w.ch2 * d * d); iy[k] = ((i0 + k) % M + M) % M; }
-    support(p.z, w, i0, u);
-    for (int k = 0; k < P; ++k) { const T d = u - T(k); wz[k] = exp_t(-w.ch2 * d * d); iz[k] = ((i0 + k) % M + M) % M; }
+    int i0x, i0y, i0z;
+    T ux, uy, uz;
+    support(p.x, w, i0x, ux);
+    support(p.y, w, i0y, uy);
+    support(p.z, w, i0z, uz);
+    T wxl = 0, wyl = 0, wzl = 0;
+    if (lg < P) {
+        const T dx = ux - T(lg), dy = uy - T(lg), dz = uz - T(lg);
+        wxl = exp_t(-w.ch2 * dx * dx);
+        wyl = exp_t(-w.ch2 * dy * dy);
+        wzl = exp_t(-w.ch2 * dz * dz);
+    }
     T ax = 0, ay = 0, az = 0;
-    for (int a = 0; a < P; ++a) {
-        for (int b = 0; b < P; ++b) {
-            const T wab = wx[a] * wy[b];
-            const int64_t rowb = ((int64_t)ix[a] * M + iy[b]) * M;
-            T sx = 0, sy = 0, sz = 0;
-            for (int c = 0; c < P; ++c) {
-                const int64_t idx = rowb + iz[c];
-                sx += wz[c] * __ldg(grid + idx);
-                sy += wz[c] * __ldg(grid + M3 + idx);
-                sz += wz[c] * __ldg(grid + 2 * M3 + idx);
+    const int PP = P * P;
+    for (int q0 = 0; q0 < PP; q0 += G) {
+        const int q = q0 + lg;
+        const bool on = active && q < PP;
+        const int b = q < PP ? q / P : 0;
+        const int c = q < PP ? q - b * P : 0;
+        const T wy = __shfl_sync(0xffffffffu, wyl, gbase + (b < G ? b : 0));
+        const T wz = __shfl_sync(0xffffffffu, wzl, gbase + (c < G ? c : 0));
+        const int iy = wrap_grid(i0y + b, M), iz = wrap_grid(i0z + c, M);
+        const T wyz = wy * wz;
+        const int64_t rowyz = (int64_t)iy * M + iz;
+        for (int a = 0; a < P; ++a) {
+            const T wx = __shfl_sync(0xffffffffu, wxl, gbase + (a < G ? a : 0));
+            if (on) {
+                const int64_t idx = (int64_t)wrap_grid(i0x + a, M) * M * M + rowyz;
+                const T wt = wx * wyz;
+                ax += wt * __ldg(grid + idx);
+                ay += wt * __ldg(grid + M3 + idx);
+                az += wt * __ldg(grid + 2 * M3 + idx);
             }
-            ax += wab * sx;
-            ay += wab * sy;
-            az += wab * sz;
         }
     }
-    V4<T> o;
-    o.x = ax * w.norm; o.y = ay * w.norm; o.z = az * w.norm; o.w = T(0);
-    uwave[s] = o;
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        az += __shfl_xor_sync(0xffffffffu, az, o);
+    }
+    if (active && lg == 0) {
+        V4<T> o;
+        o.x = ax * w.norm; o.y = ay * w.norm; o.z = az * w.norm; o.w = T(0);
+        uwave[s] = o;
+    }
 }
 
 static inline unsigned nbw(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -164,13 +193,17 @@ void launch_wave_noise(WaveGeom<T> w, const SampleArgs<T> *args, int system, voi
     const int64_t plane = (int64_t)w.M * w.M * w.Mh1;
     k_wave_noise<T><<<nbw(plane, 256), 256, 0, s>>>(w, args, system, (typename Cplx<T>::type *)spec, plane);
 }
-template <typename T> void launch_interp(int64_t N, WaveGeom<T> w, const Dev<T> &d, cudaStream_t s) {
-    k_interp<T><<<nbw(N, 128), 128, 0, s>>>(N, w, d.pos_sorted, d.grid, d.uwave);
+template <typename T> void launch_interp(int64_t N, WaveGeom<T> w, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
+    // the group must hold the P lanes that evaluate the 1-D weights
+    const int G = w.interp_lanes >= w.P ? w.interp_lanes : (w.P <= 8 ? 8 : (w.P <= 16 ? 16 : 32));
+    if (G <= 8) k_interp<T, 8><<<nbw(N * 8, 128), 128, 0, s>>>(N, w, d.pos_sorted, d.grid, d.uwave);
+    else if (G <= 16) k_interp<T, 16><<<nbw(N * 16, 128), 128, 0, s>>>(N, w, d.pos_sorted, d.grid, d.uwave);
+    else k_interp<T, 32><<<nbw(N * 32, 128), 128, 0, s>>>(N, w, d.pos_sorted, d.grid, d.uwave);
 }
 
 #define PSE_INST(T)                                                                                      \
     template void launch_wave_noise<T>(WaveGeom<T>, const SampleArgs<T> *, int, void *, cudaStream_t); \
-    template void launch_interp<T>(int64_t, WaveGeom<T>, const Dev<T> &, cudaStream_t);
+    template void launch_interp<T>(int64_t, WaveGeom<T>, Geom<T>, const Dev<T> &, cudaStream_t);
 PSE_INST(float)
 PSE_INST(double)
 #undef PSE_INST

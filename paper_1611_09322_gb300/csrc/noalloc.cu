@@ -15,18 +15,17 @@ namespace pse {
 namespace {
 
 constexpr int64_t kNoAllocMaxN = 16384;              // particles
-constexpr int64_t kNoAllocMaxCells = 32768;          // ncell^3
+constexpr int64_t kNoAllocMaxCells = 32768;          // cell slots (ncell <= 32)
 constexpr int64_t kNoAllocMaxPairs = kNoAllocMaxN * 160;  // directed neighbour entries
 
 struct NoAllocScratch {
     V4<float> pos_sorted[kNoAllocMaxN];
     V4<float> loc_sorted[kNoAllocMaxN];
-    V4<float> vsorted[kNoAllocMaxN];
+    Rec<float> rec[kNoAllocMaxN];
     V4<float> table[PSE_TABLE_N];
     int cell_of[kNoAllocMaxN];
     int slot[kNoAllocMaxN];
     int nbr_count[kNoAllocMaxN];
-    int nbr_start[kNoAllocMaxN + 1];
     int cell_count[kNoAllocMaxCells];
     int cell_start[kNoAllocMaxCells + 1];
     int scan_sums[PSE_SCAN_ITEMS];
@@ -38,7 +37,7 @@ struct NoAllocScratch {
 }  // namespace
 }  // namespace pse
 
-// The scratch itself (about 11.8 MB).  In host code this name is only a
+// The scratch itself (about 12 MB).  In host code this name is only a
 // stand-in for the device symbol; its device address comes from
 // cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(pse::NoAllocScratch)];
@@ -85,7 +84,7 @@ extern "C" pse_status pse_real_matvec_noalloc(double L, double a, double xi, dou
     pse_plan_info plan;
     pse_status st = pse_plan(L, a, &prm, &plan);
     if (st != PSE_OK) return st;
-    const int64_t nc3 = (int64_t)plan.ncell * plan.ncell * plan.ncell;
+    const int64_t nc3 = cell_slots(plan.ncell);
     if (nc3 > kNoAllocMaxCells) return PSE_EINVAL;  // box too large for the static cell arrays
 
     NoAllocScratch *sc = nullptr;
@@ -129,6 +128,7 @@ extern "C" pse_status pse_real_matvec_noalloc(double L, double a, double xi, dou
     g.a = (float)plan.a;
     g.xi = (float)plan.xi;
     g.nc = plan.ncell;
+    g.nb = bricks_per_side(plan.ncell);
 
     Dev<float> d{};
     d.pos_sorted = sc->pos_sorted;
@@ -138,11 +138,10 @@ extern "C" pse_status pse_real_matvec_noalloc(double L, double a, double xi, dou
     d.cell_count = sc->cell_count;
     d.cell_start = sc->cell_start;
     d.nbr_count = sc->nbr_count;
-    d.nbr_start = sc->nbr_start;
     d.nbr = sc->nbr;
     d.nbr_cap = kNoAllocMaxPairs;
     d.scan_sums = sc->scan_sums;
-    d.u = sc->vsorted;
+    d.rec = sc->rec;
     d.table = sc->table;
     d.lz = &sc->lz;
     d.args = &sc->args;
@@ -159,8 +158,7 @@ extern "C" pse_status pse_real_matvec_noalloc(double L, double a, double xi, dou
     launch_bin<float>(N, d.args, g, d, s);  // clears the cell counts first
     launch_scatter<float>(N, d.args, g, d, s);
     launch_cellsort<float>((int)nc3, d, s);
-    launch_nbr<float>(N, g, d, false, s);
-    launch_nbr<float>(N, g, d, true, s);
+    launch_nbr<float>(N, g, d, s);
     launch_matvec_caller<float>(N, d.args, g, d, s);
     int overflow = 0;
     if (cudaMemcpyAsync(&overflow, &sc->lz.overflow, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

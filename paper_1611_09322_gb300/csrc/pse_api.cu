@@ -118,6 +118,7 @@ template <typename T> void fill_geom(pse_ctx *c) {
     g.a = (T)p.a;
     g.xi = (T)p.xi;
     g.nc = p.ncell;
+    g.nb = bricks_per_side(p.ncell);
     geom<T>(c) = g;
     WaveGeom<T> w{};
     w.M = p.M;
@@ -133,12 +134,14 @@ template <typename T> void fill_geom(pse_ctx *c) {
     w.gl_lo = (T)(gl - (double)(T)gl);
     w.ch2 = (T)(2 * p.xi * p.xi * p.h * p.h / p.eta);
     w.norm = (T)(pow(2 * p.xi * p.xi / (M_PI * p.eta), 1.5) * p.h * p.h * p.h);
+    w.interp_lanes = 16;
     wgeom<T>(c) = w;
 }
 
 // Per-context buffers: table, spectrum, grid, FFT plan, streams, events.
 template <typename T> pse_status init_ctx(pse_ctx *c) {
     fill_geom<T>(c);
+
     Dev<T> &d = dev<T>(c);
     const pse_plan_info &p = c->plan;
     // F, G table in FP64, stored (F, G-F, dF, d(G-F)) / (6 pi a) in T
@@ -188,7 +191,7 @@ template <typename T> pse_status ensure(pse_ctx *c, int64_t N) {
     c->N = 0;
     Dev<T> &d = dev<T>(c);
     const pse_plan_info &p = c->plan;
-    const int64_t nc3 = (int64_t)p.ncell * p.ncell * p.ncell;
+    const int64_t nc3 = cell_slots(p.ncell);
     c->ncell3 = (int)nc3;
     if (nc3 + 1 > PSE_MAX_SCAN || N + 1 > PSE_MAX_SCAN || N >= (1 << 26)) return PSE_EINVAL;
     // neighbour capacity: spheres of radius a within r_cut + a, at most a
@@ -208,12 +211,12 @@ template <typename T> pse_status ensure(pse_ctx *c, int64_t N) {
     A(d.cell_count, sizeof(int) * nc3);
     A(d.cell_start, sizeof(int) * (nc3 + 1));
     A(d.nbr_count, sizeof(int) * N);
-    A(d.nbr_start, sizeof(int) * (N + 1));
     A(d.nbr, sizeof(int) * cap);
     A(d.basis, sizeof(V4<T>) * N * (c->max_iter + 2));
     A(d.u, sizeof(V4<T>) * N);
+    A(d.rec, sizeof(Rec<T>) * N);
     A(d.uwave, sizeof(V4<T>) * N);
-    A(d.partials, sizeof(double) * (2 * ((N + 127) / 128 + 16) + 64));
+    A(d.partials, sizeof(double) * (2 * num_sms() * 16 + 64));
     A(c->stage_pos, sizeof(T) * 3 * N);
     A(c->stage_out, sizeof(T) * 3 * N);
 #undef A
@@ -228,6 +231,7 @@ template <typename T> void pre(pse_ctx *c, int64_t N, cudaStream_t s) {
     launch_scatter<T>(N, d.args, geom<T>(c), d, s);
     launch_cellsort<T>(c->ncell3, d, s);
     cudaMemsetAsync(&d.lz->overflow, 0, sizeof(int), s);
+    cudaMemsetAsync(&d.lz->n_pairs, 0, sizeof(unsigned long long), s);
 }
 
 template <typename T> pse_status wave_branch(pse_ctx *c, int64_t N, cudaStream_t s) {
@@ -239,7 +243,7 @@ template <typename T> pse_status wave_branch(pse_ctx *c, int64_t N, cudaStream_t
     } else {
         CKF(cufftExecZ2D(c->fft, (cufftDoubleComplex *)d.spec, (cufftDoubleReal *)d.grid));
     }
-    launch_interp<T>(N, wgeom<T>(c), d, s);
+    launch_interp<T>(N, wgeom<T>(c), geom<T>(c), d, s);
     return PSE_OK;
 }
 
@@ -255,8 +259,7 @@ template <typename T> pse_status build_graph(pse_ctx *c) {
     cudaStreamWaitEvent(c->s_wave, c->ev[0], 0);
     pse_status wst = wave_branch<T>(c, N, c->s_wave);
     cudaEventRecord(c->ev[1], c->s_wave);
-    launch_nbr<T>(N, geom<T>(c), d, false, s);
-    launch_nbr<T>(N, geom<T>(c), d, true, s);
+    launch_nbr<T>(N, geom<T>(c), d, s);
     // WHILE node for the Lanczos loop
     cudaStreamCaptureStatus cs;
     cudaGraph_t g = nullptr;
@@ -318,8 +321,7 @@ template <typename T> pse_status run_plain(pse_ctx *c, cudaStream_t s) {
     launch_lz_init<T>(N, d.args, 0, d, s);
     pse_status st = wave_branch<T>(c, N, s);
     if (st != PSE_OK) return st;
-    launch_nbr<T>(N, geom<T>(c), d, false, s);
-    launch_nbr<T>(N, geom<T>(c), d, true, s);
+    launch_nbr<T>(N, geom<T>(c), d, s);
     for (int it = 0; it < c->max_iter + 2; ++it) {
         launch_lz_matvec<T>(N, geom<T>(c), d, s);
         launch_lz_update<T>(N, c->max_iter, d, s);
@@ -366,6 +368,60 @@ pse_status sample_impl(pse_ctx *c, int64_t N, const T *pos, uint64_t seed, uint6
     return PSE_OK;
 }
 
+// Fastest cuFFT C2R (batch 3) grid among the 2,3,5,7-smooth sizes in
+// [M, 1.12 M]: each candidate is timed over 3 transforms after one warm-up.
+static int smooth_2357(int n) {
+    const int pr[4] = {2, 3, 5, 7};
+    for (int i = 0; i < 4; ++i) while (n % pr[i] == 0) n /= pr[i];
+    return n == 1;
+}
+
+template <typename T> pse_status tune_fft_size(int M0, int *best_M) {
+    *best_M = M0;
+    const int Mmax = (int)(M0 * 1.12) + 1;
+    const size_t cbytes = sizeof(T) * 2 * 3 * (size_t)Mmax * Mmax * (Mmax / 2 + 1);
+    const size_t rbytes = sizeof(T) * 3 * (size_t)Mmax * Mmax * Mmax;
+    void *spec = nullptr, *grid = nullptr;
+    if (cudaMalloc(&spec, cbytes) != cudaSuccess || cudaMalloc(&grid, rbytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(spec);
+        return PSE_OK;  // keep the planned grid
+    }
+    cudaMemset(spec, 0, cbytes);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int M = M0; M <= Mmax; ++M) {
+        if (!smooth_2357(M)) continue;
+        cufftHandle h;
+        int n[3] = {M, M, M};
+        if (cufftPlanMany(&h, 3, n, nullptr, 1, M * M * (M / 2 + 1), nullptr, 1, M * M * M,
+                          sizeof(T) == 4 ? CUFFT_C2R : CUFFT_Z2D, 3) != CUFFT_SUCCESS)
+            continue;
+        float ms = 0.f;
+        for (int rep = 0; rep < 4; ++rep) {
+            if (rep == 1) cudaEventRecord(e0, 0);
+            if constexpr (sizeof(T) == 4) cufftExecC2R(h, (cufftComplex *)spec, (cufftReal *)grid);
+            else cufftExecZ2D(h, (cufftDoubleComplex *)spec, (cufftDoubleReal *)grid);
+        }
+        cudaEventRecord(e1, 0);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        cufftDestroy(h);
+        if (ms < best) {
+            best = ms;
+            *best_M = M;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(spec);
+    cudaFree(grid);
+    cudaGetLastError();
+    return PSE_OK;
+}
+
 pse_status create_impl(pse_ctx **out, double L, double a, const pse_params *p) {
     if (!out) return PSE_EINVAL;
     *out = nullptr;
@@ -375,6 +431,15 @@ pse_status create_impl(pse_ctx **out, double L, double a, const pse_params *p) {
     c->params = *p;
     pse_status st = pse_plan(L, a, p, &c->plan);
     if (st != PSE_OK) { delete c; return st; }
+    if ((p->autotune & 1) && p->grid_M <= 0) {
+        int Mbest = c->plan.M;
+        st = (p->precision == PSE_FP64) ? tune_fft_size<double>(c->plan.M, &Mbest) : tune_fft_size<float>(c->plan.M, &Mbest);
+        if (st == PSE_OK && Mbest != c->plan.M) {
+            c->params.grid_M = Mbest;
+            st = pse_plan(L, a, &c->params, &c->plan);
+            if (st != PSE_OK) { delete c; return st; }
+        }
+    }
     if (p->max_iter < 0 || p->max_iter > PSE_MAXIT || p->fixed_iter < 0 || p->fixed_iter > PSE_MAXIT) {
         delete c;
         return PSE_EINVAL;
@@ -476,8 +541,7 @@ pse_status pse_real_matvec(pse_ctx *c, int64_t N, const float *d_pos, const floa
     a.vin = d_v;
     CK(cudaMemcpyAsync(c->df.args, &a, sizeof(a), cudaMemcpyHostToDevice, s));
     pre<float>(c, N, s);
-    launch_nbr<float>(N, c->gf, c->df, false, s);
-    launch_nbr<float>(N, c->gf, c->df, true, s);
+    launch_nbr<float>(N, c->gf, c->df, s);
     launch_matvec_caller<float>(N, c->df.args, c->gf, c->df, s);
     c->last_stream = s;
     CK(cudaGetLastError());
@@ -524,6 +588,7 @@ pse_status pse_profile_stages(pse_ctx *c, int64_t N, const float *d_pos, uint64_
         launch_scatter<float>(N, d.args, c->gf, d, s);
         launch_cellsort<float>(c->ncell3, d, s);
         cudaMemsetAsync(&d.lz->overflow, 0, sizeof(int), s);
+        cudaMemsetAsync(&d.lz->n_pairs, 0, sizeof(unsigned long long), s);
         return PSE_OK; });
     if (r == PSE_OK) r = timed(PSE_STAGE_REAL_NOISE, 1, [&] { launch_lz_init<float>(N, d.args, 0, d, s); return PSE_OK; });
     if (r == PSE_OK) r = timed(PSE_STAGE_WAVE_NOISE, 1, [&] { launch_wave_noise<float>(c->wf, d.args, 0, d.spec, s); return PSE_OK; });
@@ -531,10 +596,9 @@ pse_status pse_profile_stages(pse_ctx *c, int64_t N, const float *d_pos, uint64_
         CKF(cufftSetStream(c->fft, s));
         CKF(cufftExecC2R(c->fft, (cufftComplex *)d.spec, (cufftReal *)d.grid));
         return PSE_OK; });
-    if (r == PSE_OK) r = timed(PSE_STAGE_INTERP, 1, [&] { launch_interp<float>(N, c->wf, d, s); return PSE_OK; });
-    if (r == PSE_OK) r = timed(PSE_STAGE_NEIGHBOURS, 2 + nscan, [&] {
-        launch_nbr<float>(N, c->gf, d, false, s);
-        launch_nbr<float>(N, c->gf, d, true, s);
+    if (r == PSE_OK) r = timed(PSE_STAGE_INTERP, 1, [&] { launch_interp<float>(N, c->wf, c->gf, d, s); return PSE_OK; });
+    if (r == PSE_OK) r = timed(PSE_STAGE_NEIGHBOURS, 1, [&] {
+        launch_nbr<float>(N, c->gf, d, s);
         return PSE_OK; });
     for (int it = 0; r == PSE_OK && it < c->max_iter + 2; ++it) {
         r = timed(PSE_STAGE_MATVEC, 1, [&] { launch_lz_matvec<float>(N, c->gf, d, s); return PSE_OK; });
@@ -564,10 +628,8 @@ pse_status pse_get_stats(pse_ctx *c, pse_stats *out) {
     CK(cudaDeviceSynchronize());
     LzState lz;
     const LzState *src = c->plan.precision == PSE_FP64 ? c->dd.lz : c->df.lz;
-    const int *ns = c->plan.precision == PSE_FP64 ? c->dd.nbr_start : c->df.nbr_start;
     CK(cudaMemcpy(&lz, src, sizeof(lz), cudaMemcpyDeviceToHost));
-    int np = 0;
-    CK(cudaMemcpy(&np, ns + c->N, sizeof(int), cudaMemcpyDeviceToHost));
+    const int64_t np = (int64_t)lz.n_pairs;
     out->lanczos_iters = lz.J;
     out->converged = lz.converged;
     out->lanczos_rel_change = lz.rel;

@@ -18,6 +18,37 @@ namespace pse {
 // 16-byte (float) / 32-byte (double) aligned 4-vector.
 template <typename T> struct alignas(4 * sizeof(T)) V4 { T x, y, z, w; };
 
+// Cell ids are brick-major: cells are grouped in 4x4x4 bricks (bricks in
+// x-major order, cells x-major inside a brick), so consecutive sorted
+// particles fill compact 3-D regions.  The id space covers whole bricks
+// (nb^3 * 64 slots, nb = ceil(ncell / 4)); slots past ncell stay empty.
+#ifdef __CUDACC__
+#define PSE_HD __host__ __device__
+#else
+#define PSE_HD
+#endif
+PSE_HD inline int bricks_per_side(int nc) { return (nc + 3) >> 2; }
+PSE_HD inline int64_t cell_slots(int nc) {
+    const int64_t nb = bricks_per_side(nc);
+    return nb * nb * nb * 64;
+}
+PSE_HD inline int cell_id(int cx, int cy, int cz, int nb) {
+    const int brick = ((cx >> 2) * nb + (cy >> 2)) * nb + (cz >> 2);
+    return (brick << 6) | ((cx & 3) << 4) | ((cy & 3) << 2) | (cz & 3);
+}
+PSE_HD inline void cell_xyz(int id, int nb, int &cx, int &cy, int &cz) {
+    const int brick = id >> 6, in = id & 63;
+    const int bz = brick % nb, by = (brick / nb) % nb, bx = brick / (nb * nb);
+    cx = (bx << 2) | (in >> 4);
+    cy = (by << 2) | ((in >> 2) & 3);
+    cz = (bz << 2) | (in & 3);
+}
+
+// Matvec record of one sorted particle: cell-local offsets and the current
+// Lanczos vector side by side, so a neighbour gather is one 32-byte sector
+// (float) instead of two.
+template <typename T> struct alignas(8 * sizeof(T)) Rec { V4<T> l; V4<T> q; };
+
 // Geometry of one periodic system, by value into kernels.
 template <typename T> struct Geom {
     T L;          // box side
@@ -30,6 +61,7 @@ template <typename T> struct Geom {
     T a;          // sphere radius (FP64 path: closed-form F, G for r >= 0.2 a)
     T xi;         // splitting parameter
     int nc;       // cells per side
+    int nb;       // bricks per side (4x4x4 cells each)
 };
 
 // Wave-space parameters of one system.
@@ -43,6 +75,7 @@ template <typename T> struct WaveGeom {
     T gl_hi, gl_lo;      // M / L split in two (compensated product x * M / L)
     T ch2;               // 2 xi^2 h^2 / eta: Gaussian exponent per squared grid unit
     T norm;              // (2 xi^2 / (pi eta))^{3/2} h^3
+    int interp_lanes;    // lanes per particle in the interpolation (8, 16, 32; 0 = pick)
 };
 
 // Per-sample arguments, read by the kernels from device memory so that one
@@ -72,6 +105,8 @@ struct LzState {
     double rel;                     // last ||y_j - y_{j-1}|| / ||y_j||
     unsigned int counter_mv, counter_up, counter_init;
     int overflow;                   // neighbour list capacity exceeded
+    int pad_;
+    unsigned long long n_pairs;     // directed pairs found by the neighbour search
 };
 
 // Appendix A, cases 1 and 2 (FP64): 6 pi eta a M^(r) = F (I - rr) + G rr.
@@ -127,12 +162,14 @@ __device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
 // bits (exact in float), Box-Muller with sincospi.
 template <typename T> struct Normals4 { T v[4]; };
 
+// Float path: the hardware log2 / sin / cos approximations (absolute error
+// ~2^-21 on these ranges, far below the sampler's tolerance).
 __device__ __forceinline__ void bm_pair(uint32_t xa, uint32_t xb, float &z0, float &z1) {
     const float ua = ((float)(xa >> 9) + 0.5f) * 1.1920928955078125e-07f;  // 2^-23
     const float ub = ((float)(xb >> 9) + 0.5f) * 1.1920928955078125e-07f;
-    const float r = sqrtf(-2.0f * logf(ua));
+    const float r = sqrtf(-2.0f * __logf(ua));
     float s, c;
-    sincospif(2.0f * ub, &s, &c);
+    __sincosf(6.28318530717958648f * ub, &s, &c);
     z0 = r * c;
     z1 = r * s;
 }
@@ -161,6 +198,30 @@ __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of per-thread float partials: float inside each warp (the
+// operands are float products), double across warps and blocks.  Result
+// valid in all threads.
+__device__ __forceinline__ double block_sum_fw(float v, double *sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum_f(v);
+    __syncthreads();
+    if (lane == 0) sh[wid] = (double)v;
+    __syncthreads();
+    double t = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (wid == 0) t = warp_sum(t);
+    if (threadIdx.x == 0) sh[0] = t;
+    __syncthreads();
+    const double r = sh[0];
+    __syncthreads();
+    return r;
 }
 
 // Block-wide sum (blockDim.x a multiple of 32, <= 1024); result valid in all threads.
@@ -213,11 +274,12 @@ template <typename T> struct Dev {
     int *slot;           // per caller particle
     int *cell_count;     // ncell^3
     int *cell_start;     // ncell^3 + 1
-    int *nbr_count;      // N
-    int *nbr_start;      // N + 1
-    int *nbr;            // capacity entries: (t << 5) | stencil code
-    int64_t nbr_cap;
+    int *nbr_count;      // N: neighbours of each sorted particle
+    int *nbr;            // ELL, column-major: entry k of particle s at nbr[k * N + s],
+                         // (t << 6) | stencil code (2 bits per axis, offset + 1)
+    int64_t nbr_cap;     // total entries; per-particle capacity = nbr_cap / N
     int *scan_sums;      // PSE_SCAN_ITEMS
+    Rec<T> *rec;         // N: cell-local offsets + current q_j (matvec input)
     V4<T> *basis;        // (PSE_MAXIT + 2) * N, q_1 .. q_{J+1}
     V4<T> *u;            // matvec output
     V4<T> *uwave;        // wave part at sorted particles
@@ -229,6 +291,10 @@ template <typename T> struct Dev {
     SampleArgs<T> *args;
 };
 
+// SM count of the current device (cached): persistent grids of the
+// reducing kernels are sized from it.
+int num_sms();
+
 // cells / scan / neighbour list
 template <typename T> void launch_bin(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d,
                                       cudaStream_t s);
@@ -236,7 +302,12 @@ void launch_scan(const int *in, int *out, int64_t n, int *sums, cudaStream_t s);
 template <typename T> void launch_scatter(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d,
                                           cudaStream_t s);
 template <typename T> void launch_cellsort(int ncell3, const Dev<T> &d, cudaStream_t s);
-template <typename T> void launch_nbr(int64_t N, Geom<T> g, const Dev<T> &d, bool fill, cudaStream_t s);
+template <typename T> void launch_nbr(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s);
+
+inline int nbr_k(int64_t N, int64_t cap) {
+    const int64_t k = cap / (N > 0 ? N : 1);
+    return (int)(k > 4096 ? 4096 : k);
+}
 
 // Lanczos
 template <typename T> void launch_lz_init(int64_t N, const SampleArgs<T> *args, int system, const Dev<T> &d,
@@ -254,7 +325,7 @@ template <typename T> void launch_matvec_caller(int64_t N, const SampleArgs<T> *
 // wave space
 template <typename T> void launch_wave_noise(WaveGeom<T> w, const SampleArgs<T> *args, int system, void *spec,
                                              cudaStream_t s);
-template <typename T> void launch_interp(int64_t N, WaveGeom<T> w, const Dev<T> &d, cudaStream_t s);
+template <typename T> void launch_interp(int64_t N, WaveGeom<T> w, Geom<T> g, const Dev<T> &d, cudaStream_t s);
 
 // host-side setup (FP64 arithmetic)
 void build_fg_table(double r_cut, double xi, double a, int n, double *F, double *G);
