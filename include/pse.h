@@ -170,6 +170,56 @@ pse_status pse_sample_f64(pse_ctx *ctx, int64_t N, const double *d_pos, uint64_t
 pse_status pse_real_matvec(pse_ctx *ctx, int64_t N, const float *d_pos, const float *d_v,
                            float *d_out, void *stream);
 
+/* ---------------------------------------------------------------- learned preconditioner
+ * Not in the paper.  The real-space Lanczos may run on S M_r S for any
+ * invertible block-diagonal S; the sample S^{-1} (S M_r S)^{1/2} z1 keeps
+ * covariance M_r exactly and only the iteration count changes.  Block i is
+ *   S_i = s0 exp(a_i) (I + tanh(b_i) T_i / (1 + tr T_i)),
+ *   T_i = sum_j exp(-((r_ij - 2a)/a)^2) rr_ij over the neighbours within r_cut,
+ * SPD and rotation-equivariant; s0 = self_mobility^{-1/2}, so a = b = 0 is the
+ * analytic self-mobility block.  (a_i, b_i) = MLP(f_i), 8 -> 16 -> 16 -> 2 with
+ * tanh, f_i = invariant features of i's neighbourhood (tr T, tr T^2, det T,
+ * smooth neighbour counts within 2.5a, 3.5a, 4.5a, r_cut, mean 2a/r; scaled).
+ * Parameter vector (float32, PSE_PRECOND_NPARAM): W1 (16x8, row-major), b1,
+ * W2 (16x16), b2, W3 (2x16), b3.  FP32 contexts only. */
+#define PSE_PRECOND_NPARAM 450
+
+/* Training inputs for positions d_pos (3N float32, device): d_feat (N x 8)
+ * features and d_tens (N x 6: xx, yy, zz, xy, xz, yz) structure tensors, in
+ * the caller's particle order (device arrays, caller-owned). */
+pse_status pse_precond_features(pse_ctx *ctx, int64_t N, const float *d_pos, float *d_feat, float *d_tens,
+                                void *stream);
+
+/* Training targets: the diagonal 3x3 block of (M_loc)^{-1/2}, M_loc = M_r
+ * restricted to particle i and its neighbours within 3a (the 16 nearest,
+ * ties by caller index), by Newton-Schulz iteration in float32.  d_target:
+ * N x 6 (xx, yy, zz, xy, xz, yz), caller order, device. */
+pse_status pse_precond_targets(pse_ctx *ctx, int64_t N, const float *d_pos, float *d_target, void *stream);
+
+/* Loss mean_i ||S_i - target_i||_F^2 / s0^2 over n samples and its gradient
+ * d_grad (PSE_PRECOND_NPARAM floats) w.r.t. d_theta; *d_loss (device double).
+ * All device arrays.  Gradients are summed with atomics (order-dependent
+ * rounding). */
+pse_status pse_precond_loss_grad(int64_t n, const float *d_feat, const float *d_tens, const float *d_target,
+                                 const float *d_theta, float s0, float *d_grad, double *d_loss, void *stream);
+
+/* `steps` full-batch Adam steps (lr, beta 0.9/0.999) on d_theta in place.
+ * d_work: device scratch of 3 * PSE_PRECOND_NPARAM + 4 floats; d_loss_hist:
+ * device array of `steps` doubles receiving the loss before each step (or
+ * NULL). */
+pse_status pse_precond_train(int64_t n, const float *d_feat, const float *d_tens, const float *d_target,
+                             float *d_theta, float s0, int steps, float lr, float *d_work, double *d_loss_hist,
+                             void *stream);
+
+/* Install network weights (host array of PSE_PRECOND_NPARAM floats) and turn
+ * the preconditioner on (h_theta = NULL turns it off).  Subsequent samples
+ * run Lanczos on S M_r S and return S^{-1} x.  Rebuilds the sample graph. */
+pse_status pse_precond_set_weights(pse_ctx *ctx, const float *h_theta, int nparam);
+
+/* The blocks S_i the installed network assigns to positions d_pos: d_S is
+ * N x 6 (xx, yy, zz, xy, xz, yz), caller order, device. */
+pse_status pse_precond_blocks(pse_ctx *ctx, int64_t N, const float *d_pos, float *d_S, void *stream);
+
 /* Stage indices of pse_profile_stages (the paper's Fig. gel split: real-space
  * matvecs, other Lanczos work, FFT + scaling + RNG, spreading/interpolation). */
 enum {

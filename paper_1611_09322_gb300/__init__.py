@@ -14,7 +14,8 @@ import numpy as np
 from . import _lib
 from ._lib import PSE_FP32, PSE_FP64, PseError, pse_params, pse_plan_info, pse_stats
 
-__all__ = ["Sampler", "pse_plan", "pse_real_scalars", "pse_real_matvec_noalloc", "PseError", "PSE_FP32", "PSE_FP64", "make_params"]
+__all__ = ["Sampler", "pse_plan", "pse_real_scalars", "pse_real_matvec_noalloc", "pse_precond_loss_grad",
+           "pse_precond_train", "PseError", "PSE_FP32", "PSE_FP64", "make_params"]
 
 
 def make_params(tol=1e-3, xi=0.5, precision=PSE_FP32, max_iter=0, fixed_iter=0, grid_M=0, support_P=0,
@@ -64,6 +65,28 @@ def pse_real_matvec_noalloc(L, a, xi, tol, pos, v, out):
     _lib.check(lib.pse_real_matvec_noalloc(L, a, xi, tol, pos.shape[0], _ptr(pos), _ptr(v), _ptr(out), _stream()),
                "pse_real_matvec_noalloc")
     return out
+
+
+def pse_precond_loss_grad(feat, tens, target, theta, s0):
+    """Loss and gradient of the preconditioner network on the GPU (torch CUDA tensors)."""
+    import torch
+    lib = _lib.load()
+    grad = torch.empty(_lib.PSE_PRECOND_NPARAM, dtype=torch.float32, device=feat.device)
+    loss = torch.empty(1, dtype=torch.float64, device=feat.device)
+    _lib.check(lib.pse_precond_loss_grad(feat.shape[0], _ptr(feat), _ptr(tens), _ptr(target), _ptr(theta), s0,
+                                         _ptr(grad), _ptr(loss), _stream()), "pse_precond_loss_grad")
+    return loss, grad
+
+
+def pse_precond_train(feat, tens, target, theta, s0, steps, lr):
+    """Full-batch Adam on the GPU; theta (CUDA float32) is updated in place. Returns the loss history."""
+    import torch
+    lib = _lib.load()
+    work = torch.zeros(3 * _lib.PSE_PRECOND_NPARAM + 4, dtype=torch.float32, device=feat.device)
+    hist = torch.zeros(steps, dtype=torch.float64, device=feat.device)
+    _lib.check(lib.pse_precond_train(feat.shape[0], _ptr(feat), _ptr(tens), _ptr(target), _ptr(theta), s0, steps,
+                                     lr, _ptr(work), _ptr(hist), _stream()), "pse_precond_train")
+    return hist
 
 
 def _stream():
@@ -164,6 +187,49 @@ class Sampler:
         _lib.check(self.lib.pse_profile_stages(self.ctx, pos.shape[0], _ptr(pos), seed, sample_index, _ptr(out),
                                                ms, nl, _stream()), "pse_profile_stages")
         return {name: (ms[i], nl[i]) for i, name in enumerate(_lib.STAGES)}
+
+    # ---------------------------------------------------------- learned preconditioner
+    def precond_features(self, pos):
+        """(N, 8) features and (N, 6) structure tensors (xx, yy, zz, xy, xz, yz), caller order."""
+        import torch
+        self._check_pos(pos)
+        N = pos.shape[0]
+        feat = torch.empty((N, 8), dtype=torch.float32, device=pos.device)
+        tens = torch.empty((N, 6), dtype=torch.float32, device=pos.device)
+        _lib.check(self.lib.pse_precond_features(self.ctx, N, _ptr(pos), _ptr(feat), _ptr(tens), _stream()),
+                   "pse_precond_features")
+        return feat, tens
+
+    def precond_targets(self, pos):
+        """(N, 6) local inverse-square-root blocks [(M_loc)^{-1/2}]_ii, caller order."""
+        import torch
+        self._check_pos(pos)
+        N = pos.shape[0]
+        tgt = torch.empty((N, 6), dtype=torch.float32, device=pos.device)
+        _lib.check(self.lib.pse_precond_targets(self.ctx, N, _ptr(pos), _ptr(tgt), _stream()), "pse_precond_targets")
+        return tgt
+
+    def precond_set_weights(self, theta):
+        """Install network weights (PSE_PRECOND_NPARAM floats) or None to switch it off."""
+        if theta is None:
+            _lib.check(self.lib.pse_precond_set_weights(self.ctx, None, 0), "pse_precond_set_weights")
+            return
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float32).ravel())
+        _lib.check(self.lib.pse_precond_set_weights(self.ctx, th.ctypes.data_as(ctypes.c_void_p), th.size),
+                   "pse_precond_set_weights")
+
+    def precond_blocks(self, pos):
+        """(N, 6) blocks S_i of the installed network, caller order."""
+        import torch
+        self._check_pos(pos)
+        N = pos.shape[0]
+        S = torch.empty((N, 6), dtype=torch.float32, device=pos.device)
+        _lib.check(self.lib.pse_precond_blocks(self.ctx, N, _ptr(pos), _ptr(S), _stream()), "pse_precond_blocks")
+        return S
+
+    @property
+    def precond_s0(self):
+        return float(self.plan["self_mobility"] ** -0.5)
 
     def stats(self, strict=False):
         s = pse_stats()

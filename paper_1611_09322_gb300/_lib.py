@@ -14,6 +14,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libpse.so")
 
 PSE_FP32, PSE_FP64 = 0, 1
+PSE_PRECOND_NPARAM = 450
 STAGES = ["cells", "sort", "real_noise", "neighbours", "matvec", "lanczos_update", "eigen", "final",
           "wave_noise", "fft", "interp"]
 STATUS = {0: "PSE_OK", 1: "PSE_EINVAL", 2: "PSE_ENOMEM", 3: "PSE_ECUDA", 4: "PSE_ECUFFT",
@@ -73,6 +74,13 @@ SIGNATURES = {
     "pse_profile_stages": (_ST, [_VP, _I64, _VP, _U64, _U64, _VP, _VP, _VP, _VP]),
     "pse_real_matvec_noalloc": (_ST, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _I64,
                                       _VP, _VP, _VP, _VP]),
+    "pse_precond_features": (_ST, [_VP, _I64, _VP, _VP, _VP, _VP]),
+    "pse_precond_targets": (_ST, [_VP, _I64, _VP, _VP, _VP]),
+    "pse_precond_loss_grad": (_ST, [_I64, _VP, _VP, _VP, _VP, ctypes.c_float, _VP, _VP, _VP]),
+    "pse_precond_train": (_ST, [_I64, _VP, _VP, _VP, _VP, ctypes.c_float, ctypes.c_int, ctypes.c_float, _VP, _VP,
+                                _VP]),
+    "pse_precond_set_weights": (_ST, [_VP, _VP, ctypes.c_int]),
+    "pse_precond_blocks": (_ST, [_VP, _I64, _VP, _VP, _VP]),
     "pse_real_scalars": (_ST, [ctypes.c_double, ctypes.c_double, _I64, _VP, _VP, _VP]),
 }
 

@@ -38,7 +38,7 @@ template <typename T> __device__ __forceinline__ double block_total(typename Par
 template <typename T>
 __global__ void __launch_bounds__(256) k_lz_init(int64_t N, const SampleArgs<T> *args, int system,
                                                  const V4<T> *pos_sorted, V4<T> *q1, Rec<T> *rec, double *partials,
-                                                 LzState *lz) {
+                                                 LzState *lz, const float *__restrict__ pc) {
     __shared__ double sh[32];
     typename Part<T>::type part = 0;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
@@ -47,7 +47,18 @@ __global__ void __launch_bounds__(256) k_lz_init(int64_t N, const SampleArgs<T> 
         V4<T> v;
         v.x = z.v[0]; v.y = z.v[1]; v.z = z.v[2]; v.w = T(0);
         q1[s] = v;
-        rec[s].q = v;
+        if constexpr (sizeof(T) == 4) {
+            if (pc) {  // matvec input is S q
+                V4<T> p;
+                sym3_apply(pc + s * 16, v.x, v.y, v.z, p.x, p.y, p.z);
+                p.w = T(0);
+                rec[s].q = p;
+            } else {
+                rec[s].q = v;
+            }
+        } else {
+            rec[s].q = v;
+        }
         part += v.x * v.x + v.y * v.y + v.z * v.z;
     }
     const double bsum = block_total<T>(part, sh);
@@ -149,7 +160,8 @@ template <typename T, int TPP>
 __global__ void __launch_bounds__(128) k_lz_matvec(int64_t N, Geom<T> g, const Rec<T> *__restrict__ rec,
                                                    const int *__restrict__ count, const int *__restrict__ nbr,
                                                    const V4<T> *__restrict__ table, V4<T> *u, double *partials,
-                                                   LzState *lz) {
+                                                   LzState *lz, const float *__restrict__ pc,
+                                                   const V4<T> *__restrict__ basis) {
     __shared__ double sh[32];
     const int j = lz->iter;
     if (j > PSE_MAXIT) return;  // uniform across the grid
@@ -172,6 +184,14 @@ __global__ void __launch_bounds__(128) k_lz_matvec(int64_t N, Geom<T> g, const R
             o.y = ay + g.self_m * qi.y;
             o.z = az + g.self_m * qi.z;
             o.w = T(0);
+            if constexpr (sizeof(T) == 4) {
+                if (pc) {  // A = S M_r S: the record holds S q, apply S to the row, dot with q
+                    T x, y, z;
+                    sym3_apply(pc + s * 16, o.x, o.y, o.z, x, y, z);
+                    o.x = x; o.y = y; o.z = z;
+                    qi = basis[(int64_t)(j - 1) * N + s];
+                }
+            }
             u[s] = o;
             part += qi.x * o.x + qi.y * o.y + qi.z * o.z;
         }
@@ -191,7 +211,7 @@ __global__ void __launch_bounds__(128) k_lz_matvec(int64_t N, Geom<T> g, const R
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_lz_update(int64_t N, V4<T> *basis, Rec<T> *rec, const V4<T> *u,
-                                                   double *partials, LzState *lz) {
+                                                   double *partials, LzState *lz, const float *__restrict__ pc) {
     __shared__ double sh[32];
     const int j = lz->iter;
     if (j > PSE_MAXIT) return;
@@ -225,7 +245,18 @@ __global__ void __launch_bounds__(256) k_lz_update(int64_t N, V4<T> *basis, Rec<
             w.z -= cp * b.z;
         }
         qn[s] = w;
-        rec[s].q = w;
+        if constexpr (sizeof(T) == 4) {
+            if (pc) {
+                V4<T> p;
+                sym3_apply(pc + s * 16, w.x, w.y, w.z, p.x, p.y, p.z);
+                p.w = T(0);
+                rec[s].q = p;
+            } else {
+                rec[s].q = w;
+            }
+        } else {
+            rec[s].q = w;
+        }
         part += w.x * w.x + w.y * w.y + w.z * w.z;
     }
     const double bsum = block_total<T>(part, sh);
@@ -359,7 +390,7 @@ __global__ void __launch_bounds__(32) k_lz_eig(LzState *lz, int max_iter, int fi
 // x_s = sum_{i=1..J} coef_i q_i[s]  (+ wave part), written in caller order.
 template <typename T>
 __global__ void k_lz_final(int64_t N, const SampleArgs<T> *args, const V4<T> *pos_sorted, const V4<T> *basis,
-                           const V4<T> *uwave, const LzState *lz, bool with_wave) {
+                           const V4<T> *uwave, const LzState *lz, bool with_wave, const float *__restrict__ pc) {
     __shared__ T cf[PSE_MAXIT + 2];
     __shared__ double cfd[PSE_MAXIT + 2];
     const int J = lz->J;
@@ -379,6 +410,13 @@ __global__ void k_lz_final(int64_t N, const SampleArgs<T> *args, const V4<T> *po
         x += c * q.x;
         y += c * q.y;
         z += c * q.z;
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (pc) {  // real part = S^{-1} (S M_r S)^{1/2} z1
+            T a, b, c;
+            sym3_apply(pc + s * 16 + 8, x, y, z, a, b, c);
+            x = a; y = b; z = c;
+        }
     }
     const int64_t o = 3 * w_bits_r(pos_sorted[s].w);
     T wx = 0, wy = 0, wz = 0;
@@ -433,14 +471,17 @@ static constexpr int kMvTpp = 4;
 
 template <typename T>
 void launch_lz_init(int64_t N, const SampleArgs<T> *args, int system, const Dev<T> &d, cudaStream_t s) {
-    k_lz_init<T><<<pgrid(N, 256, 8), 256, 0, s>>>(N, args, system, d.pos_sorted, d.basis, d.rec, d.partials, d.lz);
+    k_lz_init<T><<<pgrid(N, 256, 8), 256, 0, s>>>(N, args, system, d.pos_sorted, d.basis, d.rec, d.partials, d.lz,
+                                                  sizeof(T) == 4 ? d.pc_on : nullptr);
 }
 template <typename T> void launch_lz_matvec(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
     k_lz_matvec<T, kMvTpp><<<pgrid(N, 128 / kMvTpp, 16), 128, 0, s>>>(N, g, d.rec, d.nbr_count, d.nbr, d.table,
-                                                                        d.u, d.partials, d.lz);
+                                                                        d.u, d.partials, d.lz,
+                                                                        sizeof(T) == 4 ? d.pc_on : nullptr, d.basis);
 }
 template <typename T> void launch_lz_update(int64_t N, int, const Dev<T> &d, cudaStream_t s) {
-    k_lz_update<T><<<pgrid(N, 256, 8), 256, 0, s>>>(N, d.basis, d.rec, d.u, d.partials + num_sms() * 16 + 32, d.lz);
+    k_lz_update<T><<<pgrid(N, 256, 8), 256, 0, s>>>(N, d.basis, d.rec, d.u, d.partials + num_sms() * 16 + 32, d.lz,
+                                                    sizeof(T) == 4 ? d.pc_on : nullptr);
 }
 void launch_lz_eig(LzState *lz, int max_iter, int fixed_iter, double tol, cudaGraphConditionalHandle h,
                    cudaStream_t s) {
@@ -448,7 +489,8 @@ void launch_lz_eig(LzState *lz, int max_iter, int fixed_iter, double tol, cudaGr
 }
 template <typename T>
 void launch_lz_final(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, bool with_wave, cudaStream_t s) {
-    k_lz_final<T><<<nb(N, 256), 256, 0, s>>>(N, args, d.pos_sorted, d.basis, d.uwave, d.lz, with_wave);
+    k_lz_final<T><<<nb(N, 256), 256, 0, s>>>(N, args, d.pos_sorted, d.basis, d.uwave, d.lz, with_wave,
+                                             sizeof(T) == 4 ? d.pc_on : nullptr);
 }
 template <typename T>
 void launch_matvec_caller(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d, cudaStream_t s) {

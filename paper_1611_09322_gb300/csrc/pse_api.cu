@@ -44,6 +44,8 @@ struct pse_ctx {
     void *stage_pos = nullptr, *stage_out = nullptr;  // device staging for the host-buffer call
     std::vector<void *> per_n;                          // buffers freed when N changes
     std::vector<void *> per_ctx;                        // buffers freed at destroy
+    bool pc_enabled = false;                            // learned preconditioner installed
+    float pc_s0 = 0.f;                                  // self mobility^{-1/2}
 };
 
 #define CK(call)                                            \
@@ -169,6 +171,8 @@ template <typename T> pse_status init_ctx(pse_ctx *c) {
     CK(cudaMemset(d.lz, 0, sizeof(LzState)));
     if ((st = alloc(c->per_ctx, (void **)&d.args, sizeof(SampleArgs<T>))) != PSE_OK) return st;
     if ((st = alloc(c->per_ctx, (void **)&d.scan_sums, sizeof(int) * PSE_SCAN_ITEMS)) != PSE_OK) return st;
+    if ((st = alloc(c->per_ctx, (void **)&d.pc_theta, sizeof(float) * PSE_PRECOND_NPARAM)) != PSE_OK) return st;
+    c->pc_s0 = (float)(1.0 / sqrt(p.self_mobility));
     int n[3] = {(int)M, (int)M, (int)M};
     CKF(cufftPlanMany(&c->fft, 3, n, nullptr, 1, (int)plane, nullptr, 1, (int)(M * M * M),
                       sizeof(T) == 4 ? CUFFT_C2R : CUFFT_Z2D, 3));
@@ -215,6 +219,8 @@ template <typename T> pse_status ensure(pse_ctx *c, int64_t N) {
     A(d.basis, sizeof(V4<T>) * N * (c->max_iter + 2));
     A(d.u, sizeof(V4<T>) * N);
     A(d.rec, sizeof(Rec<T>) * N);
+    A(d.pc, sizeof(float) * 16 * N);
+    d.pc_on = c->pc_enabled ? d.pc : nullptr;
     A(d.uwave, sizeof(V4<T>) * N);
     A(d.partials, sizeof(double) * (2 * num_sms() * 16 + 64));
     A(c->stage_pos, sizeof(T) * 3 * N);
@@ -232,6 +238,15 @@ template <typename T> void pre(pse_ctx *c, int64_t N, cudaStream_t s) {
     launch_cellsort<T>(c->ncell3, d, s);
     cudaMemsetAsync(&d.lz->overflow, 0, sizeof(int), s);
     cudaMemsetAsync(&d.lz->n_pairs, 0, sizeof(unsigned long long), s);
+}
+
+// After the neighbour list: preconditioner blocks (if installed), then q_1 = z1.
+template <typename T> void real_setup(pse_ctx *c, int64_t N, cudaStream_t s) {
+    Dev<T> &d = dev<T>(c);
+    if constexpr (sizeof(T) == 4) {
+        if (c->pc_enabled) launch_pc_infer(N, c->gf, c->df, c->df.pc_theta, c->pc_s0, c->df.pc, s);
+    }
+    launch_lz_init<T>(N, d.args, 0, d, s);
 }
 
 template <typename T> pse_status wave_branch(pse_ctx *c, int64_t N, cudaStream_t s) {
@@ -254,12 +269,12 @@ template <typename T> pse_status build_graph(pse_ctx *c) {
     const double ltol = c->params.lanczos_tol > 0 ? c->params.lanczos_tol : c->plan.tol;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     pre<T>(c, N, s);
-    launch_lz_init<T>(N, d.args, 0, d, s);
     cudaEventRecord(c->ev[0], s);
     cudaStreamWaitEvent(c->s_wave, c->ev[0], 0);
     pse_status wst = wave_branch<T>(c, N, c->s_wave);
     cudaEventRecord(c->ev[1], c->s_wave);
     launch_nbr<T>(N, geom<T>(c), d, s);
+    real_setup<T>(c, N, s);
     // WHILE node for the Lanczos loop
     cudaStreamCaptureStatus cs;
     cudaGraph_t g = nullptr;
@@ -318,10 +333,10 @@ template <typename T> pse_status run_plain(pse_ctx *c, cudaStream_t s) {
     Dev<T> &d = dev<T>(c);
     const double ltol = c->params.lanczos_tol > 0 ? c->params.lanczos_tol : c->plan.tol;
     pre<T>(c, N, s);
-    launch_lz_init<T>(N, d.args, 0, d, s);
     pse_status st = wave_branch<T>(c, N, s);
     if (st != PSE_OK) return st;
     launch_nbr<T>(N, geom<T>(c), d, s);
+    real_setup<T>(c, N, s);
     for (int it = 0; it < c->max_iter + 2; ++it) {
         launch_lz_matvec<T>(N, geom<T>(c), d, s);
         launch_lz_update<T>(N, c->max_iter, d, s);
@@ -590,7 +605,6 @@ pse_status pse_profile_stages(pse_ctx *c, int64_t N, const float *d_pos, uint64_
         cudaMemsetAsync(&d.lz->overflow, 0, sizeof(int), s);
         cudaMemsetAsync(&d.lz->n_pairs, 0, sizeof(unsigned long long), s);
         return PSE_OK; });
-    if (r == PSE_OK) r = timed(PSE_STAGE_REAL_NOISE, 1, [&] { launch_lz_init<float>(N, d.args, 0, d, s); return PSE_OK; });
     if (r == PSE_OK) r = timed(PSE_STAGE_WAVE_NOISE, 1, [&] { launch_wave_noise<float>(c->wf, d.args, 0, d.spec, s); return PSE_OK; });
     if (r == PSE_OK) r = timed(PSE_STAGE_FFT, 0, [&] {
         CKF(cufftSetStream(c->fft, s));
@@ -599,6 +613,9 @@ pse_status pse_profile_stages(pse_ctx *c, int64_t N, const float *d_pos, uint64_
     if (r == PSE_OK) r = timed(PSE_STAGE_INTERP, 1, [&] { launch_interp<float>(N, c->wf, c->gf, d, s); return PSE_OK; });
     if (r == PSE_OK) r = timed(PSE_STAGE_NEIGHBOURS, 1, [&] {
         launch_nbr<float>(N, c->gf, d, s);
+        return PSE_OK; });
+    if (r == PSE_OK) r = timed(PSE_STAGE_REAL_NOISE, c->pc_enabled ? 2 : 1, [&] {
+        real_setup<float>(c, N, s);
         return PSE_OK; });
     for (int it = 0; r == PSE_OK && it < c->max_iter + 2; ++it) {
         r = timed(PSE_STAGE_MATVEC, 1, [&] { launch_lz_matvec<float>(N, c->gf, d, s); return PSE_OK; });
@@ -615,6 +632,73 @@ pse_status pse_profile_stages(pse_ctx *c, int64_t N, const float *d_pos, uint64_
     cudaEventDestroy(e1);
     c->last_stream = s;
     if (r != PSE_OK) return r;
+    CK(cudaGetLastError());
+    return PSE_OK;
+}
+
+// ---------------------------------------------------------------- learned preconditioner
+static pse_status pc_prepare(pse_ctx *c, int64_t N, const float *d_pos, cudaStream_t s) {
+    if (!c) return PSE_EINVAL;
+    if (c->plan.precision != PSE_FP32) return PSE_ENOTSUPPORTED;
+    if (!d_pos || N < 1) return PSE_EINVAL;
+    pse_status st = ensure<float>(c, N);
+    if (st != PSE_OK) return st;
+    SampleArgs<float> a{};
+    a.pos = d_pos;
+    CK(cudaMemcpyAsync(c->df.args, &a, sizeof(a), cudaMemcpyHostToDevice, s));
+    pre<float>(c, N, s);
+    launch_nbr<float>(N, c->gf, c->df, s);
+    return PSE_OK;
+}
+
+pse_status pse_precond_features(pse_ctx *c, int64_t N, const float *d_pos, float *d_feat, float *d_tens,
+                                void *stream) {
+    if (!d_feat || !d_tens) return PSE_EINVAL;
+    DeviceGuard guard(c ? c->device : 0);
+    cudaStream_t s = (cudaStream_t)stream;
+    pse_status st = pc_prepare(c, N, d_pos, s);
+    if (st != PSE_OK) return st;
+    launch_pc_features(N, c->gf, c->df, d_feat, d_tens, s);
+    c->last_stream = s;
+    CK(cudaGetLastError());
+    return PSE_OK;
+}
+
+pse_status pse_precond_targets(pse_ctx *c, int64_t N, const float *d_pos, float *d_target, void *stream) {
+    if (!d_target) return PSE_EINVAL;
+    DeviceGuard guard(c ? c->device : 0);
+    cudaStream_t s = (cudaStream_t)stream;
+    pse_status st = pc_prepare(c, N, d_pos, s);
+    if (st != PSE_OK) return st;
+    launch_pc_targets(N, c->gf, c->df, d_target, s);
+    c->last_stream = s;
+    CK(cudaGetLastError());
+    return PSE_OK;
+}
+
+pse_status pse_precond_set_weights(pse_ctx *c, const float *h_theta, int nparam) {
+    if (!c) return PSE_EINVAL;
+    if (c->plan.precision != PSE_FP32) return PSE_ENOTSUPPORTED;
+    if (h_theta && nparam != PSE_PRECOND_NPARAM) return PSE_EINVAL;
+    DeviceGuard guard(c->device);
+    CK(cudaDeviceSynchronize());
+    if (h_theta) CK(cudaMemcpy(c->df.pc_theta, h_theta, sizeof(float) * PSE_PRECOND_NPARAM, cudaMemcpyHostToDevice));
+    c->pc_enabled = h_theta != nullptr;
+    c->df.pc_on = (c->pc_enabled && c->N > 0) ? c->df.pc : nullptr;
+    drop_graph(c);  // kernel arguments changed
+    return PSE_OK;
+}
+
+pse_status pse_precond_blocks(pse_ctx *c, int64_t N, const float *d_pos, float *d_S, void *stream) {
+    if (!d_S) return PSE_EINVAL;
+    if (c && !c->pc_enabled) return PSE_ENOTREADY;
+    DeviceGuard guard(c ? c->device : 0);
+    cudaStream_t s = (cudaStream_t)stream;
+    pse_status st = pc_prepare(c, N, d_pos, s);
+    if (st != PSE_OK) return st;
+    launch_pc_infer(N, c->gf, c->df, c->df.pc_theta, c->pc_s0, c->df.pc, s);
+    launch_pc_blocks_caller(N, c->df, d_S, s);
+    c->last_stream = s;
     CK(cudaGetLastError());
     return PSE_OK;
 }

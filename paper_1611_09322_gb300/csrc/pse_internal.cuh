@@ -281,6 +281,9 @@ template <typename T> struct Dev {
     int *scan_sums;      // PSE_SCAN_ITEMS
     Rec<T> *rec;         // N: cell-local offsets + current q_j (matvec input)
     V4<T> *basis;        // (PSE_MAXIT + 2) * N, q_1 .. q_{J+1}
+    float *pc;           // N x 16: preconditioner blocks S (0..5), S^{-1} (8..13), sorted order
+    const float *pc_on;  // == pc while the learned preconditioner is active, else null
+    float *pc_theta;     // network parameters (PSE_PRECOND_NPARAM)
     V4<T> *u;            // matvec output
     V4<T> *uwave;        // wave part at sorted particles
     double *partials;    // per-block partial sums
@@ -326,6 +329,23 @@ template <typename T> void launch_matvec_caller(int64_t N, const SampleArgs<T> *
 template <typename T> void launch_wave_noise(WaveGeom<T> w, const SampleArgs<T> *args, int system, void *spec,
                                              cudaStream_t s);
 template <typename T> void launch_interp(int64_t N, WaveGeom<T> w, Geom<T> g, const Dev<T> &d, cudaStream_t s);
+
+// learned preconditioner (float contexts)
+void launch_pc_infer(int64_t N, Geom<float> g, const Dev<float> &d, const float *theta, float s0, float *pc,
+                     cudaStream_t s);
+void launch_pc_features(int64_t N, Geom<float> g, const Dev<float> &d, float *feat, float *tens, cudaStream_t s);
+void launch_pc_targets(int64_t N, Geom<float> g, const Dev<float> &d, float *target, cudaStream_t s);
+void launch_pc_blocks_caller(int64_t N, const Dev<float> &d, float *S, cudaStream_t s);
+
+// symmetric 3x3 (xx, yy, zz, xy, xz, yz) times a vector
+#ifdef __CUDACC__
+__device__ __forceinline__ void sym3_apply(const float *M, float x, float y, float z, float &ox, float &oy,
+                                           float &oz) {
+    ox = M[0] * x + M[3] * y + M[4] * z;
+    oy = M[3] * x + M[1] * y + M[5] * z;
+    oz = M[4] * x + M[5] * y + M[2] * z;
+}
+#endif
 
 // host-side setup (FP64 arithmetic)
 void build_fg_table(double r_cut, double xi, double a, int n, double *F, double *G);
