@@ -254,11 +254,13 @@ static int cca_merge(cluster_t *A, cluster_t *B, double a, double df, double kf,
 }
 
 /*
- * Fractal gel stand-in: clusters of `csize` monomers (a power of two) are
- * grown by hierarchical tunable-dimension cluster-cluster aggregation
- * (target df, prefactor kf, contact at 2a), then each cluster is dropped
- * into the periodic box at a random position and orientation, retried while
- * any of its monomers would overlap an earlier one.  The last cluster is
+ * Fractal gel stand-in: clusters of up to `csize` monomers (a power of two,
+ * capped so that a cluster's extent 4 R_g stays below L/2) are grown by
+ * hierarchical tunable-dimension cluster-cluster aggregation (target df,
+ * prefactor kf, contact at 2a), then each cluster is dropped into the
+ * periodic box at a random position and orientation, retried while any of
+ * its monomers would overlap an earlier one; after 200 failed tries the
+ * cluster size is halved for the rest of the box.  The last cluster is
  * truncated to reach exactly N.  Returns the number placed.
  */
 int64_t wl_cca_gel(int64_t N, double L, double a, double df, double kf, int64_t csize, uint64_t seed,
@@ -271,11 +273,15 @@ int64_t wl_cca_gel(int64_t N, double L, double a, double df, double kf, int64_t 
     double *best = (double *)malloc(sizeof(double) * 3 * (csize + 1));
     cluster_t *lvl = (cluster_t *)malloc(sizeof(cluster_t) * csize);
     if (!scratch || !lvl || !best) { grid_free(&g); free(scratch); free(best); free(lvl); return -1; }
+    /* clusters must fit the box: extent ~ 4 R_g = 4 a (n/kf)^(1/df) <= L/2 */
+    int64_t cmax = 1;
+    while (cmax * 2 <= csize && 4.0 * a * pow((double)(cmax * 2) / kf, 1.0 / df) <= 0.5 * L) cmax *= 2;
+    int64_t cs = cmax;
     int64_t placed = 0;
     int64_t fails = 0;
-    while (placed < N && fails < 200000) {
-        /* grow one cluster */
-        int64_t m = csize;
+    while (placed < N) {
+        /* grow one cluster of cs monomers */
+        int64_t m = cs;
         for (int64_t i = 0; i < m; ++i) {
             lvl[i].n = 1;
             lvl[i].p = (double *)calloc(3, sizeof(double));
@@ -323,8 +329,12 @@ int64_t wl_cca_gel(int64_t N, double L, double a, double df, double kf, int64_t 
             placed += take;
             done = 1;
         }
-        if (!done) ++fails;
         free(c->p);
+        if (!done) {
+            /* crowded box: smaller clusters from now on (size 1 is plain RSA) */
+            if (cs > 1) cs /= 2;
+            else if (++fails > 1000000) break;
+        }
     }
     free(scratch);
     free(best);
