@@ -69,7 +69,10 @@ typedef struct {
                             size in [M, 1.12 M] at creation and keep the fastest
                             (a finer grid only lowers the NUFFT error); needs
                             the GPU at pse_create_ex.  0: the Sec. II C grid.   */
-    int reserved[6];
+    int system;          /* Philox stream index of this system (streams 2*system
+                            and 2*system + 1): independent noise for systems
+                            sampled side by side; 0 by default                 */
+    int reserved[5];
 } pse_params;
 
 /* Parameters derived from (L, a, xi, tol) by Sec. II C of the paper:
@@ -272,6 +275,33 @@ pse_status pse_profile_stages(pse_ctx *ctx, int64_t N, const float *d_pos, uint6
  * before returning. */
 pse_status pse_real_matvec_noalloc(double L, double a, double xi, double tol, int64_t N,
                                    const float *d_pos, const float *d_v, float *d_out, void *stream);
+
+/* ---------------------------------------------------------------- batched systems
+ * Many independent periodic systems of uneven size sampled together (not in
+ * the paper).  Each system has its own box, radius and parameters (its own
+ * xi, cut-offs and grid); one pse_batch_sample is ONE CUDA graph launch in
+ * which every system's complete sample (cell list, neighbour list, device-side
+ * Lanczos loop, wave branch) is a parallel branch.  System k draws its noise
+ * from Philox streams 2k and 2k + 1, so its output equals that of a lone
+ * context created with params.system = k. */
+typedef struct pse_batch pse_batch;
+
+/* nsys >= 1 systems: L[k], a[k] and params p[k] (host arrays of nsys
+ * entries).  p[k].system is set to k.  FP32 only. */
+pse_status pse_batch_create(pse_batch **out, int nsys, const double *L, const double *a, const pse_params *p);
+
+/* Sample all systems.  offsets: host array of nsys + 1 particle offsets
+ * (offsets[0] = 0, system k owns particles offsets[k] .. offsets[k+1]-1,
+ * each N_k >= 1); d_pos / d_out: 3 * offsets[nsys] float32 device arrays,
+ * concatenated in system order.  The graph is rebuilt (with a device
+ * synchronisation) when any N_k changes. */
+pse_status pse_batch_sample(pse_batch *b, const int64_t *offsets, const float *d_pos, uint64_t seed,
+                            uint64_t sample_index, float *d_out, void *stream);
+
+/* Statistics of system k after the last batch sample (synchronises). */
+pse_status pse_batch_get_stats(pse_batch *b, int k, pse_stats *out);
+pse_status pse_batch_get_plan(const pse_batch *b, int k, pse_plan_info *out);
+void pse_batch_destroy(pse_batch *b);
 
 /* Statistics of the last sample (synchronises the context's last stream). */
 pse_status pse_get_stats(pse_ctx *ctx, pse_stats *out);

@@ -14,12 +14,12 @@ import numpy as np
 from . import _lib
 from ._lib import PSE_FP32, PSE_FP64, PseError, pse_params, pse_plan_info, pse_stats
 
-__all__ = ["Sampler", "pse_plan", "pse_real_scalars", "pse_real_matvec_noalloc", "pse_precond_loss_grad",
+__all__ = ["Sampler", "BatchSampler", "pse_plan", "pse_real_scalars", "pse_real_matvec_noalloc", "pse_precond_loss_grad",
            "pse_precond_train", "PseError", "PSE_FP32", "PSE_FP64", "make_params"]
 
 
 def make_params(tol=1e-3, xi=0.5, precision=PSE_FP32, max_iter=0, fixed_iter=0, grid_M=0, support_P=0,
-                use_precond=0, lanczos_tol=0.0, use_graph=True, autotune=0):
+                use_precond=0, lanczos_tol=0.0, use_graph=True, autotune=0, system=0):
     p = pse_params()
     p.tol = tol
     p.xi = xi
@@ -32,6 +32,7 @@ def make_params(tol=1e-3, xi=0.5, precision=PSE_FP32, max_iter=0, fixed_iter=0, 
     p.lanczos_tol = lanczos_tol
     p.use_graph = 0 if use_graph else -1
     p.autotune = autotune
+    p.system = system
     return p
 
 
@@ -239,3 +240,56 @@ class Sampler:
         d = s.as_dict()
         d["status"] = _lib.STATUS.get(st, st)
         return d
+
+
+class BatchSampler:
+    """Many independent systems sampled by one CUDA-graph launch (pse_batch_*)."""
+
+    def __init__(self, Ls, a=1.0, params=None, **kw):
+        self.lib = _lib.load()
+        n = len(Ls)
+        a_arr = np.full(n, a, dtype=np.float64) if np.isscalar(a) else np.asarray(a, dtype=np.float64)
+        L_arr = np.asarray(Ls, dtype=np.float64)
+        if params is None:
+            params = [dict(kw) for _ in range(n)]
+        arr = (pse_params * n)(*[make_params(**pk) for pk in params])
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.pse_batch_create(ctypes.byref(h), n, L_arr.ctypes.data_as(ctypes.c_void_p),
+                                             a_arr.ctypes.data_as(ctypes.c_void_p), ctypes.cast(arr, ctypes.c_void_p)),
+                   "pse_batch_create")
+        self.h = h
+        self.n = n
+        self._keep = (L_arr, a_arr, arr)
+
+    def plan(self, k):
+        info = pse_plan_info()
+        _lib.check(self.lib.pse_batch_get_plan(self.h, k, ctypes.byref(info)), "pse_batch_get_plan")
+        return info.as_dict()
+
+    def sample(self, pos_all, offsets, seed, sample_index=0, out=None):
+        """pos_all: (sum N, 3) float32 CUDA, systems concatenated; offsets: n+1 ints."""
+        import torch
+        if out is None:
+            out = torch.empty_like(pos_all)
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        _lib.check(self.lib.pse_batch_sample(self.h, off.ctypes.data_as(ctypes.c_void_p), _ptr(pos_all), seed,
+                                             sample_index, _ptr(out), _stream()), "pse_batch_sample")
+        return out
+
+    def stats(self, k):
+        s = pse_stats()
+        st = self.lib.pse_batch_get_stats(self.h, k, ctypes.byref(s))
+        d = s.as_dict()
+        d["status"] = _lib.STATUS.get(st, st)
+        return d
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pse_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

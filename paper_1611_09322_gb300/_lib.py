@@ -31,7 +31,8 @@ class pse_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("xi", ctypes.c_double), ("precision", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("fixed_iter", ctypes.c_int), ("grid_M", ctypes.c_int),
                 ("support_P", ctypes.c_int), ("use_precond", ctypes.c_int), ("lanczos_tol", ctypes.c_double),
-                ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int), ("system", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class pse_plan_info(ctypes.Structure):
@@ -81,6 +82,11 @@ SIGNATURES = {
                                 _VP]),
     "pse_precond_set_weights": (_ST, [_VP, _VP, ctypes.c_int]),
     "pse_precond_blocks": (_ST, [_VP, _I64, _VP, _VP, _VP]),
+    "pse_batch_create": (_ST, [ctypes.POINTER(_VP), ctypes.c_int, _VP, _VP, _VP]),
+    "pse_batch_sample": (_ST, [_VP, _VP, _VP, _U64, _U64, _VP, _VP]),
+    "pse_batch_get_stats": (_ST, [_VP, ctypes.c_int, ctypes.POINTER(pse_stats)]),
+    "pse_batch_get_plan": (_ST, [_VP, ctypes.c_int, ctypes.POINTER(pse_plan_info)]),
+    "pse_batch_destroy": (None, [_VP]),
     "pse_real_scalars": (_ST, [ctypes.c_double, ctypes.c_double, _I64, _VP, _VP, _VP]),
 }
 

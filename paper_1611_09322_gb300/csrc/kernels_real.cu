@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(256) k_lz_init(int64_t N, const SampleArgs<T> 
         lz->J = 0;
         lz->converged = 0;
         lz->cont = 1;
+        lz->active = 1;
         lz->rel = 0.0;
     }
 }
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(128) k_lz_matvec(int64_t N, Geom<T> g, const R
                                                    const V4<T> *__restrict__ basis) {
     __shared__ double sh[32];
     const int j = lz->iter;
-    if (j > PSE_MAXIT) return;  // uniform across the grid
+    if (j > PSE_MAXIT || !lz->active) return;  // uniform across the grid
     typename Part<T>::type part = 0;
     const int lane_g = threadIdx.x % TPP;
     const int64_t per_block = blockDim.x / TPP;
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(256) k_lz_update(int64_t N, V4<T> *basis, Rec<
                                                    double *partials, LzState *lz, const float *__restrict__ pc) {
     __shared__ double sh[32];
     const int j = lz->iter;
-    if (j > PSE_MAXIT) return;
+    if (j > PSE_MAXIT || !lz->active) return;
     // coefficients in the working precision; the FP64 path recomputes them exactly
     T cu, cq, cp;
     if constexpr (sizeof(T) == 4) {
@@ -278,6 +279,7 @@ __global__ void __launch_bounds__(32) k_lz_eig(LzState *lz, int max_iter, int fi
     __shared__ double Q[PSE_MAXIT][PSE_MAXIT + 1];
     __shared__ double d[PSE_MAXIT + 1], e[PSE_MAXIT + 1], y[PSE_MAXIT + 1];
     const int lane = threadIdx.x;
+    if (!lz->active) return;  // this system has stopped (batched loop)
     const int k = lz->jeig;
     __syncwarp();
     if (lane == 0) lz->jeig = k + 1;
@@ -386,6 +388,23 @@ __global__ void __launch_bounds__(32) k_lz_eig(LzState *lz, int max_iter, int fi
     }
 }
 
+// One thread per system: the systems whose stop test passed in this loop
+// body become inactive for the next one; the shared WHILE node continues
+// while any system is still active.
+__global__ void k_batch_cond(LzState *const *lzs, int nsys, cudaGraphConditionalHandle h) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < nsys; k += blockDim.x) {
+        LzState *lz = lzs[k];
+        const int c = lz->active && lz->cont;
+        lz->active = c;
+        if (c) atomicOr(&any, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
 // ------------------------------------------------------------------ final combination
 // x_s = sum_{i=1..J} coef_i q_i[s]  (+ wave part), written in caller order.
 template <typename T>
@@ -486,6 +505,9 @@ template <typename T> void launch_lz_update(int64_t N, int, const Dev<T> &d, cud
 void launch_lz_eig(LzState *lz, int max_iter, int fixed_iter, double tol, cudaGraphConditionalHandle h,
                    cudaStream_t s) {
     k_lz_eig<<<1, 32, 0, s>>>(lz, max_iter, fixed_iter, tol, h);
+}
+void launch_batch_cond(LzState *const *lzs, int nsys, cudaGraphConditionalHandle h, cudaStream_t s) {
+    k_batch_cond<<<1, 256, 0, s>>>(lzs, nsys, h);
 }
 template <typename T>
 void launch_lz_final(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, bool with_wave, cudaStream_t s) {

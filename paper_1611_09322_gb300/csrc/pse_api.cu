@@ -246,12 +246,12 @@ template <typename T> void real_setup(pse_ctx *c, int64_t N, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
         if (c->pc_enabled) launch_pc_infer(N, c->gf, c->df, c->df.pc_theta, c->pc_s0, c->df.pc, s);
     }
-    launch_lz_init<T>(N, d.args, 0, d, s);
+    launch_lz_init<T>(N, d.args, c->params.system, d, s);
 }
 
 template <typename T> pse_status wave_branch(pse_ctx *c, int64_t N, cudaStream_t s) {
     Dev<T> &d = dev<T>(c);
-    launch_wave_noise<T>(wgeom<T>(c), d.args, 0, d.spec, s);
+    launch_wave_noise<T>(wgeom<T>(c), d.args, c->params.system, d.spec, s);
     CKF(cufftSetStream(c->fft, s));
     if constexpr (sizeof(T) == 4) {
         CKF(cufftExecC2R(c->fft, (cufftComplex *)d.spec, (cufftReal *)d.grid));
@@ -262,60 +262,97 @@ template <typename T> pse_status wave_branch(pse_ctx *c, int64_t N, cudaStream_t
     return PSE_OK;
 }
 
-template <typename T> pse_status build_graph(pse_ctx *c) {
+// Capture pieces of one sample.  The prologue runs on c->s_main (which must
+// be capturing): cell list, wave branch forked onto c->s_wave, neighbour
+// list, preconditioner blocks and q_1.  The loop body is one Lanczos step
+// (matvec -> update on `sa`, eigen-solve of the previous T on `sb`).  The
+// epilogue joins the wave branch and writes the output.
+template <typename T> pse_status capture_pre(pse_ctx *c) {
     const int64_t N = c->N;
     Dev<T> &d = dev<T>(c);
     cudaStream_t s = c->s_main;
-    const double ltol = c->params.lanczos_tol > 0 ? c->params.lanczos_tol : c->plan.tol;
-    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     pre<T>(c, N, s);
     cudaEventRecord(c->ev[0], s);
     cudaStreamWaitEvent(c->s_wave, c->ev[0], 0);
-    pse_status wst = wave_branch<T>(c, N, c->s_wave);
+    const pse_status wst = wave_branch<T>(c, N, c->s_wave);
     cudaEventRecord(c->ev[1], c->s_wave);
     launch_nbr<T>(N, geom<T>(c), d, s);
     real_setup<T>(c, N, s);
-    // WHILE node for the Lanczos loop
+    return wst;
+}
+
+template <typename T>
+void capture_body(pse_ctx *c, cudaStream_t sa, cudaStream_t sb, cudaGraphConditionalHandle h) {
+    Dev<T> &d = dev<T>(c);
+    const double ltol = c->params.lanczos_tol > 0 ? c->params.lanczos_tol : c->plan.tol;
+    launch_lz_matvec<T>(c->N, geom<T>(c), d, sa);
+    launch_lz_update<T>(c->N, c->max_iter, d, sa);
+    launch_lz_eig(d.lz, c->max_iter, c->params.fixed_iter, ltol, h, sb);
+}
+
+template <typename T> void capture_post(pse_ctx *c) {
+    Dev<T> &d = dev<T>(c);
+    cudaStreamWaitEvent(c->s_main, c->ev[1], 0);
+    launch_lz_final<T>(c->N, d.args, d, true, c->s_main);
+}
+
+// Insert a WHILE node (default condition 1) at the capture point of `s`;
+// returns its handle and body graph, and makes `s` continue after it.
+static cudaError_t add_while(cudaStream_t s, cudaGraphConditionalHandle *h, cudaGraph_t *body) {
     cudaStreamCaptureStatus cs;
     cudaGraph_t g = nullptr;
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
     cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &ndeps);
-    cudaGraphNode_t node = nullptr;
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    e = cudaGraphConditionalHandleCreate(h, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return e;
     cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-    if (e == cudaSuccess && cs == cudaStreamCaptureStatusActive) {
-        e = cudaGraphConditionalHandleCreate(&c->cond, g, 1, cudaGraphCondAssignDefault);
-        if (e == cudaSuccess) {
-            cp.conditional.handle = c->cond;
-            cp.conditional.type = cudaGraphCondTypeWhile;
-            cp.conditional.size = 1;
-            e = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp);
-        }
-        if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
-    }
+    cp.conditional.handle = *h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp);
+    if (e != cudaSuccess) return e;
+    *body = cp.conditional.phGraph_out[0];
+    return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// One whole sample on c->s_main (capturing): prologue, a WHILE node whose
+// body is one Lanczos step with the eigen kernel setting the condition, and
+// the epilogue.
+template <typename T> pse_status capture_sample(pse_ctx *c) {
+    const pse_status wst = capture_pre<T>(c);
+    cudaGraph_t body = nullptr;
+    cudaError_t e = add_while(c->s_main, &c->cond, &body);
     if (e == cudaSuccess) {
-        cudaGraph_t body = cp.conditional.phGraph_out[0];
         e = cudaStreamBeginCaptureToGraph(c->s_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaEventRecord(c->ev[2], c->s_body);
             cudaStreamWaitEvent(c->s_body2, c->ev[2], 0);
-            launch_lz_matvec<T>(N, geom<T>(c), d, c->s_body);
-            launch_lz_update<T>(N, c->max_iter, d, c->s_body);
-            launch_lz_eig(d.lz, c->max_iter, c->params.fixed_iter, ltol, c->cond, c->s_body2);
+            capture_body<T>(c, c->s_body, c->s_body2, c->cond);
             cudaEventRecord(c->ev[3], c->s_body2);
             cudaStreamWaitEvent(c->s_body, c->ev[3], 0);
             cudaGraph_t body_out = nullptr;
             e = cudaStreamEndCapture(c->s_body, &body_out);
         }
     }
-    cudaStreamWaitEvent(s, c->ev[1], 0);
-    launch_lz_final<T>(N, d.args, d, true, s);
+    capture_post<T>(c);
+    if (wst != PSE_OK) return wst;
+    return e == cudaSuccess ? PSE_OK : PSE_ECUDA;
+}
+
+template <typename T> pse_status build_graph(pse_ctx *c) {
+    cudaStream_t s = c->s_main;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const pse_status st = capture_sample<T>(c);
     cudaGraph_t graph = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(s, &graph);
-    if (e != cudaSuccess || e2 != cudaSuccess || wst != PSE_OK) {
+    const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+    if (st != PSE_OK || e2 != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
         cudaGetLastError();
-        return wst != PSE_OK ? wst : PSE_ECUDA;
+        return st != PSE_OK ? st : PSE_ECUDA;
     }
     c->graph = graph;
     if (cudaGraphInstantiate(&c->exec, graph, 0) != cudaSuccess) {
@@ -455,7 +492,8 @@ pse_status create_impl(pse_ctx **out, double L, double a, const pse_params *p) {
             if (st != PSE_OK) { delete c; return st; }
         }
     }
-    if (p->max_iter < 0 || p->max_iter > PSE_MAXIT || p->fixed_iter < 0 || p->fixed_iter > PSE_MAXIT) {
+    if (p->max_iter < 0 || p->max_iter > PSE_MAXIT || p->fixed_iter < 0 || p->fixed_iter > PSE_MAXIT ||
+        p->system < 0 || p->system > 0x3fffffff) {
         delete c;
         return PSE_EINVAL;
     }
@@ -605,7 +643,7 @@ pse_status pse_profile_stages(pse_ctx *c, int64_t N, const float *d_pos, uint64_
         cudaMemsetAsync(&d.lz->overflow, 0, sizeof(int), s);
         cudaMemsetAsync(&d.lz->n_pairs, 0, sizeof(unsigned long long), s);
         return PSE_OK; });
-    if (r == PSE_OK) r = timed(PSE_STAGE_WAVE_NOISE, 1, [&] { launch_wave_noise<float>(c->wf, d.args, 0, d.spec, s); return PSE_OK; });
+    if (r == PSE_OK) r = timed(PSE_STAGE_WAVE_NOISE, 1, [&] { launch_wave_noise<float>(c->wf, d.args, c->params.system, d.spec, s); return PSE_OK; });
     if (r == PSE_OK) r = timed(PSE_STAGE_FFT, 0, [&] {
         CKF(cufftSetStream(c->fft, s));
         CKF(cufftExecC2R(c->fft, (cufftComplex *)d.spec, (cufftReal *)d.grid));
@@ -725,3 +763,205 @@ pse_status pse_get_stats(pse_ctx *c, pse_stats *out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- batched systems
+struct pse_batch {
+    std::vector<pse_ctx *> sys;
+    int device = 0;
+    cudaStream_t root = nullptr;
+    cudaEvent_t ev_fork = nullptr;
+    std::vector<cudaEvent_t> ev_join;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int64_t> built_N;
+    SampleArgs<float> *d_args = nullptr;  // one per system, read by that system's kernels
+    std::vector<SampleArgs<float>> h_args;
+    LzState **d_lzs = nullptr;            // each system's Lanczos state, for the loop condition
+    cudaStream_t body = nullptr;          // captures the shared loop body
+    cudaEvent_t ev_body = nullptr, ev_after = nullptr;
+    std::vector<cudaEvent_t> ev_pre;
+    cudaGraphConditionalHandle cond = 0;
+};
+
+static void batch_drop_graph(pse_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+extern "C" void pse_batch_destroy(pse_batch *b) {
+    if (!b) return;
+    DeviceGuard guard(b->device);
+    cudaDeviceSynchronize();
+    batch_drop_graph(b);
+    for (pse_ctx *c : b->sys) pse_destroy(c);
+    if (b->d_args) cudaFree(b->d_args);
+    if (b->d_lzs) cudaFree(b->d_lzs);
+    if (b->root) cudaStreamDestroy(b->root);
+    if (b->body) cudaStreamDestroy(b->body);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_body) cudaEventDestroy(b->ev_body);
+    if (b->ev_after) cudaEventDestroy(b->ev_after);
+    for (cudaEvent_t e : b->ev_join) if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->ev_pre) if (e) cudaEventDestroy(e);
+    delete b;
+}
+
+extern "C" pse_status pse_batch_create(pse_batch **out, int nsys, const double *L, const double *a,
+                                       const pse_params *p) {
+    if (!out) return PSE_EINVAL;
+    *out = nullptr;
+    if (nsys < 1 || !L || !a || !p) return PSE_EINVAL;
+    pse_batch *b = new (std::nothrow) pse_batch();
+    if (!b) return PSE_ENOMEM;
+    if (cudaGetDevice(&b->device) != cudaSuccess) { cudaGetLastError(); delete b; return PSE_ECUDA; }
+    pse_status st = PSE_OK;
+    for (int k = 0; k < nsys && st == PSE_OK; ++k) {
+        if (p[k].precision != PSE_FP32) { st = PSE_ENOTSUPPORTED; break; }
+        pse_params q = p[k];
+        q.system = k;
+        pse_ctx *c = nullptr;
+        st = pse_create_ex(&c, L[k], a[k], &q);
+        if (st == PSE_OK) b->sys.push_back(c);
+    }
+    if (st == PSE_OK && cudaMalloc(&b->d_args, sizeof(SampleArgs<float>) * nsys) != cudaSuccess) {
+        cudaGetLastError();
+        st = PSE_ENOMEM;
+    }
+    if (st == PSE_OK && cudaMalloc((void **)&b->d_lzs, sizeof(LzState *) * nsys) != cudaSuccess) {
+        cudaGetLastError();
+        st = PSE_ENOMEM;
+    }
+    if (st == PSE_OK && (cudaStreamCreateWithFlags(&b->root, cudaStreamNonBlocking) != cudaSuccess ||
+                         cudaStreamCreateWithFlags(&b->body, cudaStreamNonBlocking) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&b->ev_body, cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&b->ev_after, cudaEventDisableTiming) != cudaSuccess))
+        st = PSE_ECUDA;
+    if (st == PSE_OK) {
+        b->ev_join.assign(nsys, nullptr);
+        b->ev_pre.assign(nsys, nullptr);
+        for (int k = 0; k < nsys && st == PSE_OK; ++k)
+            if (cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&b->ev_pre[k], cudaEventDisableTiming) != cudaSuccess)
+                st = PSE_ECUDA;
+        std::vector<LzState *> lzs(nsys);
+        for (int k = 0; k < nsys; ++k) lzs[k] = b->sys[k]->df.lz;
+        if (st == PSE_OK && cudaMemcpy(b->d_lzs, lzs.data(), sizeof(LzState *) * nsys, cudaMemcpyHostToDevice) != cudaSuccess)
+            st = PSE_ECUDA;
+        // every system's kernels read their per-call arguments from the batch array
+        for (int k = 0; k < nsys; ++k) b->sys[k]->df.args = b->d_args + k;
+        b->h_args.assign(nsys, SampleArgs<float>{});
+        b->built_N.assign(nsys, 0);
+    }
+    if (st != PSE_OK) {
+        pse_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return PSE_OK;
+}
+
+extern "C" pse_status pse_batch_sample(pse_batch *b, const int64_t *offsets, const float *d_pos, uint64_t seed,
+                                       uint64_t sample_index, float *d_out, void *stream) {
+    if (!b || !offsets || !d_pos || !d_out) return PSE_EINVAL;
+    const int S = (int)b->sys.size();
+    if (offsets[0] != 0) return PSE_EINVAL;
+    for (int k = 0; k < S; ++k)
+        if (offsets[k + 1] - offsets[k] < 1) return PSE_EINVAL;
+    DeviceGuard guard(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    bool rebuild = b->exec == nullptr;
+    for (int k = 0; k < S; ++k) {
+        const int64_t N = offsets[k + 1] - offsets[k];
+        if (N != b->built_N[k]) rebuild = true;
+        pse_status st = ensure<float>(b->sys[k], N);
+        if (st != PSE_OK) return st;
+        b->sys[k]->df.args = b->d_args + k;  // kept across re-allocation
+    }
+    if (rebuild) {
+        batch_drop_graph(b);
+        // prologues of all systems in parallel, one shared WHILE node whose body
+        // holds every system's Lanczos step and the batch condition, epilogues
+        CK(cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal));
+        cudaEventRecord(b->ev_fork, b->root);
+        pse_status st = PSE_OK;
+        for (int k = 0; k < S; ++k) {
+            pse_ctx *c = b->sys[k];
+            cudaStreamWaitEvent(c->s_main, b->ev_fork, 0);
+            const pse_status sk = capture_pre<float>(c);
+            if (sk != PSE_OK && st == PSE_OK) st = sk;
+            cudaEventRecord(b->ev_pre[k], c->s_main);
+            cudaStreamWaitEvent(b->root, b->ev_pre[k], 0);
+        }
+        cudaGraph_t body = nullptr;
+        cudaError_t e = add_while(b->root, &b->cond, &body);
+        if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(b->body, body, nullptr, nullptr, 0,
+                                                              cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaEventRecord(b->ev_body, b->body);
+            for (int k = 0; k < S; ++k) {
+                pse_ctx *c = b->sys[k];
+                cudaStreamWaitEvent(c->s_body, b->ev_body, 0);
+                cudaStreamWaitEvent(c->s_body2, b->ev_body, 0);
+                capture_body<float>(c, c->s_body, c->s_body2, 0);
+                cudaEventRecord(c->ev[2], c->s_body);
+                cudaEventRecord(c->ev[3], c->s_body2);
+                cudaStreamWaitEvent(b->body, c->ev[2], 0);
+                cudaStreamWaitEvent(b->body, c->ev[3], 0);
+            }
+            launch_batch_cond(b->d_lzs, S, b->cond, b->body);
+            cudaGraph_t body_out = nullptr;
+            e = cudaStreamEndCapture(b->body, &body_out);
+        }
+        if (e != cudaSuccess && st == PSE_OK) st = PSE_ECUDA;
+        cudaEventRecord(b->ev_after, b->root);
+        for (int k = 0; k < S; ++k) {
+            pse_ctx *c = b->sys[k];
+            cudaStreamWaitEvent(c->s_main, b->ev_after, 0);
+            capture_post<float>(c);
+            cudaEventRecord(b->ev_join[k], c->s_main);
+            cudaStreamWaitEvent(b->root, b->ev_join[k], 0);
+        }
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(b->root, &graph);
+        if (st != PSE_OK || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return st != PSE_OK ? st : PSE_ECUDA;
+        }
+        b->graph = graph;
+        if (cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) {
+            cudaGetLastError();
+            batch_drop_graph(b);
+            return PSE_ECUDA;
+        }
+        for (int k = 0; k < S; ++k) b->built_N[k] = offsets[k + 1] - offsets[k];
+    }
+    for (int k = 0; k < S; ++k) {
+        SampleArgs<float> &a = b->h_args[k];
+        a.pos = d_pos + 3 * offsets[k];
+        a.out = d_out + 3 * offsets[k];
+        a.real = nullptr;
+        a.wave = nullptr;
+        a.vin = nullptr;
+        a.seed = seed;
+        a.sample = sample_index;
+    }
+    CK(cudaMemcpyAsync(b->d_args, b->h_args.data(), sizeof(SampleArgs<float>) * S, cudaMemcpyHostToDevice, s));
+    CK(cudaGraphLaunch(b->exec, s));
+    for (pse_ctx *c : b->sys) c->last_stream = s;
+    CK(cudaGetLastError());
+    return PSE_OK;
+}
+
+extern "C" pse_status pse_batch_get_stats(pse_batch *b, int k, pse_stats *out) {
+    if (!b || k < 0 || k >= (int)b->sys.size()) return PSE_EINVAL;
+    return pse_get_stats(b->sys[k], out);
+}
+
+extern "C" pse_status pse_batch_get_plan(const pse_batch *b, int k, pse_plan_info *out) {
+    if (!b || k < 0 || k >= (int)b->sys.size()) return PSE_EINVAL;
+    return pse_get_plan(b->sys[k], out);
+}

@@ -102,6 +102,7 @@ struct LzState {
     int J;                          // accepted iteration count
     int converged;
     int cont;                       // loop continues (host-loop mode reads this)
+    int active;                     // matvec/update/eigen still run; changes only between loop bodies
     double rel;                     // last ||y_j - y_{j-1}|| / ||y_j||
     unsigned int counter_mv, counter_up, counter_init;
     int overflow;                   // neighbour list capacity exceeded
@@ -319,6 +320,8 @@ template <typename T> void launch_lz_matvec(int64_t N, Geom<T> g, const Dev<T> &
 template <typename T> void launch_lz_update(int64_t N, int max_iter, const Dev<T> &d, cudaStream_t s);
 void launch_lz_eig(LzState *lz, int max_iter, int fixed_iter, double tol, cudaGraphConditionalHandle h,
                    cudaStream_t s);
+// batch loop condition: active_k = cont_k for every system, continue while any is active
+void launch_batch_cond(LzState *const *lzs, int nsys, cudaGraphConditionalHandle h, cudaStream_t s);
 template <typename T> void launch_lz_final(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, bool with_wave,
                                            cudaStream_t s);
 // plain matvec of a caller vector (sorted gather -> M_r -> scatter back)

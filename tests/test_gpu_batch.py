@@ -1,0 +1,73 @@
+"""Batched sampling: one CUDA-graph launch for many independent systems."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+SEED = 31337
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.fail("GPU test run without a CUDA device")
+    from paper_1611_09322_gb300 import build
+    build.build_all()
+    return t
+
+
+def _systems():
+    from paper_1611_09322_gb300 import workloads
+    spec = [("hs", 1000, 0.1, 0.5), ("gel", 3000, 0.05, 0.6), ("hs", 777, 0.35, 0.5), ("hs", 5000, 0.2, 0.4),
+            ("gel", 1500, 0.15, 0.5)]
+    out = []
+    for k, (kind, N, phi, xi) in enumerate(spec):
+        pos, L, _ = workloads.make(kind, N, phi, 500 + k)
+        out.append((pos, L, xi))
+    return out
+
+
+def test_batch_equals_lone_contexts(torch):
+    from paper_1611_09322_gb300 import BatchSampler, Sampler
+    systems = _systems()
+    Ls = [L for _, L, _ in systems]
+    params = [dict(xi=xi, tol=1e-3) for _, _, xi in systems]
+    b = BatchSampler(Ls, 1.0, params=params)
+    offsets = np.cumsum([0] + [p.shape[0] for p, _, _ in systems])
+    pos_all = torch.from_numpy(np.concatenate([p for p, _, _ in systems])).cuda()
+    for sample in (3, 4):  # two launches of the same graph
+        out = b.sample(pos_all, offsets, SEED, sample).cpu().numpy()
+        for k, (pos, L, xi) in enumerate(systems):
+            s = Sampler(L, 1.0, xi=xi, tol=1e-3, system=k)
+            ref = s.sample(torch.from_numpy(pos).cuda(), SEED, sample).cpu().numpy()
+            assert np.array_equal(out[offsets[k]:offsets[k + 1]], ref), k
+            assert b.stats(k)["lanczos_iters"] == s.stats()["lanczos_iters"]
+            assert b.stats(k)["converged"] == 1
+            s.close()
+    b.close()
+
+
+def test_batch_systems_draw_independent_noise(torch):
+    from paper_1611_09322_gb300 import BatchSampler, workloads
+    pos, L, _ = workloads.hard_spheres(2000, 0.1, 9)
+    b = BatchSampler([L, L], 1.0, xi=0.5, tol=1e-3)
+    pos_all = torch.from_numpy(np.concatenate([pos, pos])).cuda()
+    out = b.sample(pos_all, [0, 2000, 4000], SEED, 0).cpu().numpy()
+    a, c = out[:2000], out[2000:]
+    assert abs(np.corrcoef(a.ravel(), c.ravel())[0, 1]) < 0.1
+    b.close()
+
+
+def test_batch_rebuilds_when_sizes_change(torch):
+    from paper_1611_09322_gb300 import BatchSampler, Sampler, workloads
+    p1, L1, _ = workloads.hard_spheres(1200, 0.1, 1)
+    p2, L2, _ = workloads.hard_spheres(900, 0.1, 2)
+    b = BatchSampler([L1, L2], 1.0, xi=0.5, tol=1e-3)
+    b.sample(torch.from_numpy(np.concatenate([p1, p2])).cuda(), [0, 1200, 2100], SEED, 0)
+    q2 = p2[:700]
+    out = b.sample(torch.from_numpy(np.concatenate([p1, q2])).cuda(), [0, 1200, 1900], SEED, 1).cpu().numpy()
+    s = Sampler(L2, 1.0, xi=0.5, tol=1e-3, system=1)
+    ref = s.sample(torch.from_numpy(q2).cuda(), SEED, 1).cpu().numpy()
+    assert np.array_equal(out[1200:], ref)
+    s.close()
+    b.close()
