@@ -57,7 +57,7 @@ def clocks_start():
         p = subprocess.Popen(["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
                               "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
                               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                              "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                              "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
                              stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
     except OSError:
         p = None
@@ -91,6 +91,28 @@ def clocks_stop(p, f, device_index=0):
                 reasons.add(n)
     return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
             "samples": len(sm)}
+
+
+# DRAM bytes (read + write) of one launch, from an ncu capture of the kernel
+# at this workload, valid only while the kernel's sources hash to the value
+# recorded with it (profiles/ holds the capture's summary).
+TRAFFIC = {
+    "k_lz_matvec": (112_879_616 + 9_083_392, ("csrc/kernels_real.cu", "csrc/pse_internal.cuh"),
+                    "248da13847137d584824edd3076095339af4aeb00aeb6fa79d6c3ce790aaeef6"),
+}
+
+
+def captured_traffic(kernel):
+    import hashlib
+    if kernel not in TRAFFIC:
+        return None
+    nbytes, files, digest = TRAFFIC[kernel]
+    pkg = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1611_09322_gb300")
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(pkg, f), "rb") as fh:
+            h.update(fh.read())
+    return nbytes if h.hexdigest() == digest else None
 
 
 def measured_peak():
@@ -155,13 +177,93 @@ def run_reference(args):
     return 0
 
 
+def timed_steps(run, steps, flush, stream):
+    """Per-step CUDA-event times (ms) of `run(i)`, L2 flushed before each step."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        evs[i][0].record(stream)
+        run(i)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def launches_per_sample(J, learned=False):
+    # bin + 3 scan + scatter + cell sort, noise + interpolation, neighbour
+    # list, (network), q_1, 3 kernels per loop body (J + 1 bodies), final;
+    # cuFFT's own kernels are not counted
+    return 11 + (1 if learned else 0) + 3 * (J + 1)
+
+
+def variants_learned_batched(dev, flush, stream, steps):
+    """The metric's comparison: learned preconditioner and batching vs plain."""
+    import numpy as np
+    import torch
+    from paper_1611_09322_gb300 import BatchSampler, Sampler, precond_train, workloads
+    out = {}
+    theta, info = precond_train.train(xi=XI, tol=TOL, steps=1500, lr=3e-3)
+    out["learned_training"] = {k: v for k, v in info.items() if k != "loss_hist"}
+    pos, L, _ = workloads.hard_spheres(N_PART, PHI, SEED_POS)
+    d = torch.from_numpy(pos).to(dev)
+    o = torch.empty_like(d)
+    for name, th in (("plain_N1e6", None), ("learned_N1e6", theta)):
+        s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=1)
+        if th is not None:
+            s.precond_set_weights(th)
+        for i in range(3):
+            s.sample(d, 1, i, out=o)
+        per = timed_steps(lambda i: s.sample(d, 1, 200 + i, out=o), steps, flush, stream)
+        st = s.stats()
+        out[name] = {"value": N_PART * steps / (sum(per) / 1e3), "ms_per_step": sum(per) / steps,
+                     "lanczos_iters": st["lanczos_iters"], "converged": st["converged"]}
+        s.close()
+    spec = workloads.batch_spec()
+    pos_list, Ls = [], []
+    for sp in spec:
+        p, Lk, _ = workloads.make(sp["kind"], sp["N"], sp["phi"], sp["seed"])
+        pos_list.append(p)
+        Ls.append(Lk)
+    offsets = np.cumsum([0] + [p.shape[0] for p in pos_list])
+    pa = torch.from_numpy(np.concatenate(pos_list)).to(dev)
+    po = torch.empty_like(pa)
+    for name, th in (("batched_64sys_plain", None), ("batched_64sys_learned", theta)):
+        b = BatchSampler(Ls, 1.0, xi=XI, tol=TOL, autotune=1)
+        if th is not None:
+            for k in range(len(spec)):
+                _lib_set(b, k, th)
+        for i in range(3):
+            b.sample(pa, offsets, 1, i, out=po)
+        per = timed_steps(lambda i: b.sample(pa, offsets, 1, 300 + i, out=po), steps, flush, stream)
+        its = [b.stats(k)["lanczos_iters"] for k in range(len(spec))]
+        out[name] = {"value": int(offsets[-1]) * steps / (sum(per) / 1e3), "ms_per_step": sum(per) / steps,
+                     "n_systems": len(spec), "n_particles": int(offsets[-1]), "lanczos_iters_mean": float(np.mean(its))}
+        b.close()
+    out["workload_batched"] = ("64 periodic systems, N log-uniform in [1e3, 5e4], phi uniform in [0.05, 0.4], "
+                               "half fractal gels (phi <= 0.2), each with its own box and FFT grid, xi a = 0.5, "
+                               "tol 1e-3; one CUDA graph launch per step")
+    return out
+
+
+def _lib_set(batch, k, theta):
+    """Install preconditioner weights in system k of a batch (through its context)."""
+    import ctypes
+    import numpy as np
+    from paper_1611_09322_gb300 import _lib
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float32))
+    _lib.check(batch.lib.pse_batch_set_precond(batch.h, k, th.ctypes.data_as(ctypes.c_void_p), th.size),
+               "pse_batch_set_precond")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -187,29 +289,20 @@ def main():
     stream = torch.cuda.current_stream()
     seed = 1000 + rank
 
+    clk, clkf = clocks_start()
     for i in range(args.warmup):
         s.sample(d_pos, seed, i, out=out)
     torch.cuda.synchronize()
-    st = s.stats()
-    iters = [st["lanczos_iters"]]
-
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clk, clkf = clocks_start()
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        evs[i][0].record(stream)
-        s.sample(d_pos, seed, 100 + i, out=out)
-        evs[i][1].record(stream)
-    torch.cuda.synchronize()
+    per = timed_steps(lambda i: s.sample(d_pos, seed, 100 + i, out=out), args.steps, flush, stream)
     if ws > 1:
         dist.barrier()
     clocks = clocks_stop(clk, clkf, dev.index)
-    per = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(per)
-    iters.append(s.stats()["lanczos_iters"])
+    st = s.stats()
+    J = st["lanczos_iters"]
     if ws > 1:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -220,31 +313,25 @@ def main():
     stages = None
     for i in range(3):
         stages = s.profile_stages(d_pos, seed, 10_000 + i, out=out)
-    st = s.stats()
-    J = st["lanczos_iters"]
-    n_pairs = st["n_pairs"]
+    n_pairs = s.stats()["n_pairs"]
     plan = s.plan
     M = plan["M"]
-    # dominant kernel by share of the staged sample
     dom = max(stages, key=lambda k: stages[k][0])
-    mv_ms, mv_n = stages["matvec"]
-    in_ms, in_n = stages["interp"]
-    # algorithmic bytes per launch: matvec reads cell-local
-    # positions, q and nbr_start per particle, the CSR list, writes u;
-    # interpolation reads positions and the 3 M^3 float grid once, writes u_w.
-    bytes_mv = 16 * N_PART * 3 + 4 * (N_PART + 1) + 4 * n_pairs
-    bytes_in = 16 * N_PART * 2 + 12 * M ** 3
-    bytes_fft = None
-    kernel_bytes = {"matvec": (bytes_mv, mv_ms / max(mv_n, 1)), "interp": (bytes_in, in_ms / max(in_n, 1))}
+    # algorithmic bytes per launch: matvec reads the 32-byte
+    # records (offsets + q) and neighbour counts, the ELL list (4 B per pair),
+    # writes u; interpolation reads positions and the 3 M^3 float grid once,
+    # writes u_w; the FFT stage is cuFFT's.
+    bytes_mv = 32 * N_PART + 4 * N_PART + 4 * n_pairs + 16 * N_PART
+    bytes_in = 16 * N_PART + 12 * M ** 3 + 16 * N_PART
+    kernel_bytes = {"matvec": ("k_lz_matvec", bytes_mv), "interp": ("k_interp", bytes_in)}
     key = "matvec" if stages["matvec"][0] >= stages["interp"][0] else "interp"
-    kb, kms = kernel_bytes[key]
+    kname, kb = kernel_bytes[key]
+    kms = stages[key][0] / max(stages[key][1], 1)
     peak, peak_kind = measured_peak()
     achieved = kb / (kms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": {"matvec": "k_lz_matvec", "interp": "k_interp"}[key],
-                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
-                "algorithmic_bytes_per_launch": kb, "ms_per_launch": round(kms, 5),
-                "dominant_stage": dom,
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": captured_traffic(kname), "peak_kind": f"{peak_kind} hbm_gbs (copy), burst",
+                "algorithmic_bytes_per_launch": kb, "ms_per_launch": round(kms, 5), "dominant_stage": dom,
                 "stages_ms": {k: round(v[0], 4) for k, v in stages.items()},
                 "stages_launches": {k: v[1] for k, v in stages.items()}}
 
@@ -260,22 +347,23 @@ def main():
     e2e_s = (time.perf_counter() - t0) / K2
     e2e = {"value": ws * N_PART / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 12 * N_PART,
            "d2h_bytes_per_step": 12 * N_PART}
+    s.close()
 
-    launches_per_step = 4 + 2 + 1 + 1 + 1 + 5 + 3 * (J + 1) + 1  # our kernels in the graph (cuFFT's excluded)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "ms_per_step_median": statistics.median(per), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(plan), "lanczos_iters": J, "n_pairs": n_pairs,
-                "variant": "plain PSE (single system, CUDA graph per sample)",
+                "variant": "plain PSE, one system, one CUDA graph per sample",
                 "roofline": roofline, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": launches_per_step * args.steps,
+                "gpu_launches": launches_per_sample(J) * args.steps,
                 "parallelism": "replicas" if ws > 1 else "single GPU"}
+        if not args.no_variants:
+            line["variants"] = variants_learned_batched(dev, flush, stream, max(20, args.steps // 4))
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
-    s.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0

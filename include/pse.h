@@ -298,6 +298,10 @@ pse_status pse_batch_create(pse_batch **out, int nsys, const double *L, const do
 pse_status pse_batch_sample(pse_batch *b, const int64_t *offsets, const float *d_pos, uint64_t seed,
                             uint64_t sample_index, float *d_out, void *stream);
 
+/* Install (or with h_theta = NULL remove) learned-preconditioner weights in
+ * system k (see pse_precond_set_weights); the batch graph is rebuilt. */
+pse_status pse_batch_set_precond(pse_batch *b, int k, const float *h_theta, int nparam);
+
 /* Statistics of system k after the last batch sample (synchronises). */
 pse_status pse_batch_get_stats(pse_batch *b, int k, pse_stats *out);
 pse_status pse_batch_get_plan(const pse_batch *b, int k, pse_plan_info *out);

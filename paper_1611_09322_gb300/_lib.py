@@ -87,6 +87,7 @@ SIGNATURES = {
     "pse_batch_get_stats": (_ST, [_VP, ctypes.c_int, ctypes.POINTER(pse_stats)]),
     "pse_batch_get_plan": (_ST, [_VP, ctypes.c_int, ctypes.POINTER(pse_plan_info)]),
     "pse_batch_destroy": (None, [_VP]),
+    "pse_batch_set_precond": (_ST, [_VP, ctypes.c_int, _VP, ctypes.c_int]),
     "pse_real_scalars": (_ST, [ctypes.c_double, ctypes.c_double, _I64, _VP, _VP, _VP]),
 }
 

@@ -956,6 +956,13 @@ extern "C" pse_status pse_batch_sample(pse_batch *b, const int64_t *offsets, con
     return PSE_OK;
 }
 
+extern "C" pse_status pse_batch_set_precond(pse_batch *b, int k, const float *h_theta, int nparam) {
+    if (!b || k < 0 || k >= (int)b->sys.size()) return PSE_EINVAL;
+    const pse_status st = pse_precond_set_weights(b->sys[k], h_theta, nparam);
+    if (st == PSE_OK) batch_drop_graph(b);
+    return st;
+}
+
 extern "C" pse_status pse_batch_get_stats(pse_batch *b, int k, pse_stats *out) {
     if (!b || k < 0 || k >= (int)b->sys.size()) return PSE_EINVAL;
     return pse_get_stats(b->sys[k], out);
