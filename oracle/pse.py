@@ -204,6 +204,118 @@ def wave_covariance_grid(pos, plan):
     return C.transpose(2, 0, 3, 1).reshape(3 * N, 3 * N)
 
 
+# ----------------------------------------------------------------------------- spreading, M_w F and grid noise
+
+def nyquist_mask(M):
+    """(M, M, M) bool: modes with an index at the Nyquist frequency of an even grid."""
+    if M % 2:
+        return np.zeros((M, M, M), dtype=bool)
+    h = M // 2
+    i = np.arange(M) == h
+    return i[:, None, None] | i[None, :, None] | i[None, None, :]
+
+
+def spread(F, pos, plan):
+    """Grid force density s(x_g) = sum_i g(x_g - x_i) F_i, shape (3, M, M, M).
+
+    The spreading operator S of Sec. II B 2 on the same P^3 support and
+    Gaussian g as ``interpolate`` (S^dagger = h^3 S^T).
+    """
+    pos = np.asarray(pos, dtype=np.float64)
+    F = np.asarray(F, dtype=np.float64).reshape(-1, 3)
+    M, P, h = plan.M, plan.P, plan.h
+    c = 2 * plan.xi ** 2 / plan.eta
+    norm = (c / np.pi) ** 1.5
+    grid = np.zeros((3, M, M, M))
+    idx, wts = [], []
+    for d in range(3):
+        i0, s = support_start(pos[:, d], plan)
+        nodes = i0[:, None] + np.arange(P)[None, :]
+        dist = (s[:, None] - nodes) * h
+        wts.append(np.exp(-c * dist * dist))
+        idx.append(np.mod(nodes, M))
+    for p in range(P):
+        for q in range(P):
+            for r in range(P):
+                wgt = wts[0][:, p] * wts[1][:, q] * wts[2][:, r]
+                at = (idx[0][:, p], idx[1][:, q], idx[2][:, r])
+                for d in range(3):
+                    np.add.at(grid[d], at, wgt * F[:, d])
+    return grid * norm
+
+
+def wave_apply_grid(F, pos, plan):
+    """Gridded wave-space product M_w F (N, 3): spread, forward DFT, the mode
+    factor h^3 B(k) (I - kk) with B(k)/V = wave_scale(k)^2 (so that with
+    ghat^2 it is c_k^2 of eq. Mwave), k = 0 and Nyquist dropped, inverse DFT
+    (unnormalised), interpolation.  The deterministic wave path of Sec. III."""
+    M = plan.M
+    shat = np.fft.fftn(spread(F, pos, plan), axes=(1, 2, 3))
+    kx, ky, kz = wave_vectors_full(M, plan.L)
+    k = np.sqrt(kx * kx + ky * ky + kz * kz)
+    fac = plan.h ** 3 * wave_scale(k, plan) ** 2
+    fac[nyquist_mask(M)] = 0.0
+    vhat = _project(kx, ky, kz, shat) * fac[None]
+    v = np.fft.ifftn(vhat, axes=(1, 2, 3)) * float(M) ** 3
+    return interpolate(v.real, pos, plan)
+
+
+def mobility_apply(F, pos, plan, op=None):
+    """M F = M_r F (sparse, eq. Mreal) + gridded M_w F (N, 3)."""
+    A = RealOperator(np.asarray(pos, dtype=np.float64), plan) if op is None else op
+    return A(F) + wave_apply_grid(F, pos, plan)
+
+
+def grid_noise(M, seed, sample, system=0):
+    """White noise W(x_g) ~ N(0, 1) per node and component, shape (3, M, M, M).
+
+    Node id g = (ix*M + iy)*M + iz keys one Philox block on the wave stream
+    2*system + 1; its first three normals are the x, y, z components.
+    """
+    g = np.arange(M ** 3, dtype=np.uint64)
+    n = philox.normals4(g, 2 * system + 1, seed, sample)
+    return np.ascontiguousarray(n[:, :3].T).reshape(3, M, M, M)
+
+
+def wave_sample_gridnoise(pos, plan, seed, sample, system=0, W=None):
+    """Wave-space sample drawn from white noise on the grid instead of in k-space.
+
+    What(k) = M^{-3/2} sum_g W(x_g) exp(-i k.x_g) has, on every mode pair
+    {k, -k} off Nyquist, the law of dW2(k) (real and imaginary parts of
+    variance 1/2, conjugate partners), so scaling it exactly as in the
+    k-space path (wave_scale(k) (I - kk), k = 0 and Nyquist dropped) gives a
+    sample with the same covariance as ``wave_sample_grid`` (the fluctuating
+    hydrodynamics remark of Sec. II B 2).  ``W`` overrides the drawn noise.
+    """
+    M = plan.M
+    if W is None:
+        W = grid_noise(M, seed, sample, system)
+    What = np.fft.fftn(np.asarray(W, dtype=np.float64), axes=(1, 2, 3)) / float(M) ** 1.5
+    kx, ky, kz = wave_vectors_full(M, plan.L)
+    k = np.sqrt(kx * kx + ky * ky + kz * kz)
+    fac = wave_scale(k, plan)
+    fac[nyquist_mask(M)] = 0.0
+    vhat = _project(kx, ky, kz, What) * fac[None]
+    v = np.fft.ifftn(vhat, axes=(1, 2, 3)) * float(M) ** 3
+    return interpolate(v.real, pos, plan)
+
+
+def sample_with_forces(pos, F, plan, seed, sample, c_det=1.0, c_noise=1.0, n_iter=None, system=0):
+    """c_det M F + c_noise M^{1/2} z (N, 3): the deterministic and Brownian parts
+    of one Euler-Maruyama displacement (Sec. III: the wave parts share one
+    inverse FFT).  Returns (out, j_lanczos)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    A = RealOperator(pos, plan)
+    out = np.zeros((pos.shape[0], 3))
+    j = 0
+    if c_det != 0.0:
+        out += c_det * mobility_apply(F, pos, plan, op=A)
+    if c_noise != 0.0:
+        ur, j, _ = real_sample(pos, plan, seed, sample, n_iter=n_iter, system=system, op=A)
+        out += c_noise * (ur + wave_sample_grid(pos, plan, seed, sample, system))
+    return out, j
+
+
 # ----------------------------------------------------------------------------- real part
 
 def pair_list(pos, L, rc):
