@@ -209,7 +209,7 @@ def variants_learned_batched(dev, flush, stream, steps):
     d = torch.from_numpy(pos).to(dev)
     o = torch.empty_like(d)
     for name, th in (("plain_N1e6", None), ("learned_N1e6", theta)):
-        s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=1)
+        s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=5)
         if th is not None:
             s.precond_set_weights(th)
         for i in range(3):
@@ -219,6 +219,28 @@ def variants_learned_batched(dev, flush, stream, steps):
         out[name] = {"value": N_PART * steps / (sum(per) / 1e3), "ms_per_step": sum(per) / steps,
                      "lanczos_iters": st["lanczos_iters"], "converged": st["converged"]}
         s.close()
+    # the forces path at the same workload: deterministic M F alone (the
+    # paper's deterministic benchmark), one fused Euler-Maruyama displacement
+    # dt M F + sqrt(2 dt) M^{1/2} z (kT = 1, dt = 1e-3), and the plain sample
+    # with the wave noise drawn on the grid
+    F = torch.randn(d.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(3))
+    s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=7)
+    runs = (("mobility_apply_N1e6", lambda i: s.sample_with_forces(d, F, 1, 400 + i, 1.0, 0.0, out=o)),
+            ("euler_maruyama_N1e6", lambda i: s.sample_with_forces(d, F, 1, 500 + i, 1e-3, math.sqrt(2e-3), out=o)))
+    for name, fn in runs:
+        for i in range(3):
+            fn(i)
+        per = timed_steps(fn, steps, flush, stream)
+        out[name] = {"value": N_PART * steps / (sum(per) / 1e3), "ms_per_step": sum(per) / steps}
+    out["euler_maruyama_N1e6"]["lanczos_iters"] = s.stats()["lanczos_iters"]
+    s.close()
+    s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=5, wave_noise=1)
+    for i in range(3):
+        s.sample(d, 1, i, out=o)
+    per = timed_steps(lambda i: s.sample(d, 1, 600 + i, out=o), steps, flush, stream)
+    out["grid_noise_sample_N1e6"] = {"value": N_PART * steps / (sum(per) / 1e3), "ms_per_step": sum(per) / steps,
+                                     "lanczos_iters": s.stats()["lanczos_iters"]}
+    s.close()
     spec = workloads.batch_spec()
     pos_list, Ls = [], []
     for sp in spec:
@@ -282,7 +304,7 @@ def main():
     torch.cuda.set_device(dev)
 
     pos, L, _ = workloads.hard_spheres(N_PART, PHI, SEED_POS)
-    s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=1)
+    s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=5)
     d_pos = torch.from_numpy(pos).to(dev)
     out = torch.empty_like(d_pos)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)

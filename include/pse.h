@@ -68,11 +68,27 @@ typedef struct {
     int autotune;        /* bit 0: time cuFFT C2R for every 2,3,5,7-smooth grid
                             size in [M, 1.12 M] at creation and keep the fastest
                             (a finer grid only lowers the NUFFT error); needs
-                            the GPU at pse_create_ex.  0: the Sec. II C grid.   */
+                            the GPU at pse_create_ex.  0: the Sec. II C grid.
+                            bit 1: time every spreading tile shape at the first
+                            forces call and keep the fastest.
+                            bit 2: time every near-field matvec launch shape
+                            at the first sample and keep the fastest.          */
     int system;          /* Philox stream index of this system (streams 2*system
                             and 2*system + 1): independent noise for systems
                             sampled side by side; 0 by default                 */
-    int reserved[5];
+    int wave_noise;      /* 0 (default): dW2 drawn in k-space (Sec. II B 2);
+                            1: white noise drawn on the M^3 grid and taken to
+                            k-space by a forward FFT -- same covariance, other
+                            samples (the fluctuating-hydrodynamics form)       */
+    int spread_tile;     /* 0 (default): spreading tile chosen automatically
+                            (largest that fits shared memory, or timed with
+                            autotune bit 1); 1, 2 or 4: tiles of that many
+                            cells per side (PSE_ENOTSUPPORTED at the first
+                            forces call if it does not fit shared memory)      */
+    int matvec_shape;    /* 0 (default): near-field matvec with 4 threads x 4
+                            gathers per particle (or timed with autotune bit 2);
+                            1..4 force shape 4x4, 8x2, 16x1, 4x2              */
+    int reserved[2];
 } pse_params;
 
 /* Parameters derived from (L, a, xi, tol) by Sec. II C of the paper:
@@ -95,7 +111,8 @@ typedef struct {
     double lanczos_rel_change; /* ||x_j - x_{j-1}|| / ||x_j|| at exit          */
     int64_t n_pairs;     /* directed near-field pairs within r_cut              */
     int overflow;        /* 1 if the neighbour list exceeded its capacity       */
-    int reserved[5];
+    int matvec_shape;    /* matvec launch shape in use (1..4 as in pse_params)  */
+    int reserved[4];
 } pse_stats;
 
 typedef struct pse_ctx pse_ctx;
@@ -166,6 +183,33 @@ pse_status pse_sample_host(pse_ctx *ctx, int64_t N, const float *h_pos, uint64_t
 pse_status pse_sample_f64(pse_ctx *ctx, int64_t N, const double *d_pos, uint64_t seed,
                           uint64_t sample_index, double *d_out, double *d_real, double *d_wave,
                           void *stream);
+
+/* One Euler-Maruyama displacement's two parts in one call (Sec. III: the
+ * deterministic and Brownian wave parts share one inverse FFT):
+ *   d_out = c_det M F + c_noise M^{1/2} z,
+ * M F = M_r F (sparse, eq. Mreal) + M_w F (spread F with the Gaussian, forward
+ * FFT, per mode h^3 B(k) (I - kk) with B from eq. Mwave and the Gaussian
+ * deconvolution, inverse FFT, interpolate), M^{1/2} z as in pse_sample with
+ * the same (seed, sample_index) noise.  c_noise = 0 skips the Lanczos loop
+ * and the noise (the deterministic product alone); for a Brownian step take
+ * c_det = dt and c_noise = sqrt(2 kT dt).  d_pos, d_force, d_out: 3N float32
+ * device arrays in the caller's order (d_out may not alias the inputs).
+ * Contexts with wave_noise = 1 support only c_noise = 0 here
+ * (PSE_ENOTSUPPORTED otherwise).  The spreading uses float atomics, so the
+ * last bits of M F may differ from call to call. */
+pse_status pse_sample_with_forces(pse_ctx *ctx, int64_t N, const float *d_pos, const float *d_force,
+                                  uint64_t seed, uint64_t sample_index, double c_det, double c_noise,
+                                  float *d_out, void *stream);
+
+/* FP64 context form of pse_sample_with_forces (float64 arrays). */
+pse_status pse_sample_with_forces_f64(pse_ctx *ctx, int64_t N, const double *d_pos, const double *d_force,
+                                      uint64_t seed, uint64_t sample_index, double c_det, double c_noise,
+                                      double *d_out, void *stream);
+
+/* The deterministic product d_out = M d_force alone (pse_sample_with_forces
+ * with c_det = 1, c_noise = 0), FP32 context. */
+pse_status pse_mobility_apply(pse_ctx *ctx, int64_t N, const float *d_pos, const float *d_force, float *d_out,
+                              void *stream);
 
 /* Near-field product d_out = M_r d_v (eq. Mreal with the App. A scalars and
  * the eq. self diagonal), FP32 context.  d_pos, d_v, d_out: 3N float32
@@ -247,6 +291,33 @@ enum {
  * The output equals pse_sample's for the same arguments. */
 pse_status pse_profile_stages(pse_ctx *ctx, int64_t N, const float *d_pos, uint64_t seed,
                               uint64_t sample_index, float *d_out, double *ms, int *launches,
+                              void *stream);
+
+/* One Euler-Maruyama displacement's two parts in one call (Sec. III: the
+ * deterministic and Brownian wave parts share one inverse FFT):
+ *   d_out = c_det M F + c_noise M^{1/2} z,
+ * M F = M_r F (sparse, eq. Mreal) + M_w F (spread F with the Gaussian, forward
+ * FFT, per mode h^3 B(k) (I - kk) with B from eq. Mwave and the Gaussian
+ * deconvolution, inverse FFT, interpolate), M^{1/2} z as in pse_sample with
+ * the same (seed, sample_index) noise.  c_noise = 0 skips the Lanczos loop
+ * and the noise (the deterministic product alone); for a Brownian step take
+ * c_det = dt and c_noise = sqrt(2 kT dt).  d_pos, d_force, d_out: 3N float32
+ * device arrays in the caller's order (d_out may not alias the inputs).
+ * Contexts with wave_noise = 1 support only c_noise = 0 here
+ * (PSE_ENOTSUPPORTED otherwise).  The spreading uses float atomics, so the
+ * last bits of M F may differ from call to call. */
+pse_status pse_sample_with_forces(pse_ctx *ctx, int64_t N, const float *d_pos, const float *d_force,
+                                  uint64_t seed, uint64_t sample_index, double c_det, double c_noise,
+                                  float *d_out, void *stream);
+
+/* FP64 context form of pse_sample_with_forces (float64 arrays). */
+pse_status pse_sample_with_forces_f64(pse_ctx *ctx, int64_t N, const double *d_pos, const double *d_force,
+                                      uint64_t seed, uint64_t sample_index, double c_det, double c_noise,
+                                      double *d_out, void *stream);
+
+/* The deterministic product d_out = M d_force alone (pse_sample_with_forces
+ * with c_det = 1, c_noise = 0), FP32 context. */
+pse_status pse_mobility_apply(pse_ctx *ctx, int64_t N, const float *d_pos, const float *d_force, float *d_out,
                               void *stream);
 
 /* Near-field product d_out = M_r d_v, like pse_real_matvec, for callers that

@@ -365,6 +365,38 @@ class RealOperator:
         return out
 
 
+def real_rows(pos, plan, rows, v):
+    """Rows `rows` of M_r v (eq. Mreal with the App. A scalars, eq. self on the
+    diagonal), evaluated one particle at a time from its neighbours within
+    r_cut (minimum image): the near-field product at sampled particles of a
+    system too large for the full pair list.  Returns (len(rows), 3)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64).reshape(-1, 3)
+    L, a, xi = plan.L, plan.a, plan.xi
+    p = np.mod(pos, L)
+    p[p >= L] = 0.0
+    tree = cKDTree(p, boxsize=L)
+    s = rpy.self_real(xi, a) / (6 * np.pi * a)
+    out = np.zeros((len(rows), 3))
+    for n, i in enumerate(rows):
+        nb = np.asarray(tree.query_ball_point(p[i], plan.r_cut), dtype=np.int64)
+        nb = nb[nb != i]
+        d = p[i] - p[nb]
+        d -= L * np.round(d / L)
+        r = np.linalg.norm(d, axis=1)
+        keep = r < plan.r_cut
+        nb, d, r = nb[keep], d[keep], r[keep]
+        acc = s * v[i]
+        if nb.size:
+            F, G = rpy.fg(r, xi, a)
+            rh = d / r[:, None]
+            vj = v[nb]
+            dot = np.einsum("kd,kd->k", rh, vj)
+            acc = acc + ((F[:, None] * vj + ((G - F) * dot)[:, None] * rh) / (6 * np.pi * a)).sum(axis=0)
+        out[n] = acc
+    return out
+
+
 def sqrt_tridiag_e1(alpha, beta):
     """T^{1/2} e_1 for the symmetric tridiagonal T (diag alpha, off-diag beta)."""
     j = len(alpha)

@@ -19,7 +19,8 @@ __all__ = ["Sampler", "BatchSampler", "pse_plan", "pse_real_scalars", "pse_real_
 
 
 def make_params(tol=1e-3, xi=0.5, precision=PSE_FP32, max_iter=0, fixed_iter=0, grid_M=0, support_P=0,
-                use_precond=0, lanczos_tol=0.0, use_graph=True, autotune=0, system=0):
+                use_precond=0, lanczos_tol=0.0, use_graph=True, autotune=0, system=0, wave_noise=0,
+                spread_tile=0, matvec_shape=0):
     p = pse_params()
     p.tol = tol
     p.xi = xi
@@ -33,6 +34,9 @@ def make_params(tol=1e-3, xi=0.5, precision=PSE_FP32, max_iter=0, fixed_iter=0, 
     p.use_graph = 0 if use_graph else -1
     p.autotune = autotune
     p.system = system
+    p.wave_noise = wave_noise
+    p.spread_tile = spread_tile
+    p.matvec_shape = matvec_shape
     return p
 
 
@@ -175,6 +179,23 @@ class Sampler:
         _lib.check(self.lib.pse_real_matvec(self.ctx, pos.shape[0], _ptr(pos), _ptr(v), _ptr(out), _stream()),
                    "pse_real_matvec")
         return out
+
+    def sample_with_forces(self, pos, force, seed, sample_index=0, c_det=1.0, c_noise=1.0, out=None):
+        """c_det M F + c_noise M^{1/2} z at `pos` (pse_sample_with_forces); (N, 3) CUDA tensors."""
+        import torch
+        self._check_pos(pos)
+        if force.dtype != pos.dtype or force.shape != pos.shape or not force.is_contiguous() or not force.is_cuda:
+            raise ValueError("force must be a contiguous CUDA tensor shaped and typed like pos")
+        if out is None:
+            out = torch.empty_like(pos)
+        fn = self.lib.pse_sample_with_forces_f64 if self.fp64 else self.lib.pse_sample_with_forces
+        _lib.check(fn(self.ctx, pos.shape[0], _ptr(pos), _ptr(force), seed, sample_index, float(c_det),
+                      float(c_noise), _ptr(out), _stream()), "pse_sample_with_forces")
+        return out
+
+    def mobility_apply(self, pos, force, out=None):
+        """The deterministic product M F (c_det = 1, c_noise = 0)."""
+        return self.sample_with_forces(pos, force, 0, 0, 1.0, 0.0, out=out)
 
     def profile_stages(self, pos, seed, sample_index=0, out=None):
         """Per-stage device times (ms) and launch counts of one sample (pse_profile_stages)."""

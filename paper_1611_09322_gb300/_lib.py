@@ -32,7 +32,8 @@ class pse_params(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("fixed_iter", ctypes.c_int), ("grid_M", ctypes.c_int),
                 ("support_P", ctypes.c_int), ("use_precond", ctypes.c_int), ("lanczos_tol", ctypes.c_double),
                 ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int), ("system", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("wave_noise", ctypes.c_int), ("spread_tile", ctypes.c_int),
+                ("matvec_shape", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class pse_plan_info(ctypes.Structure):
@@ -48,7 +49,8 @@ class pse_plan_info(ctypes.Structure):
 class pse_stats(ctypes.Structure):
     _fields_ = [("lanczos_iters", ctypes.c_int), ("converged", ctypes.c_int),
                 ("lanczos_rel_change", ctypes.c_double), ("n_pairs", ctypes.c_int64),
-                ("overflow", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("overflow", ctypes.c_int), ("matvec_shape", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
@@ -70,6 +72,10 @@ SIGNATURES = {
     "pse_sample_host": (_ST, [_VP, _I64, _VP, _U64, _U64, _VP, _VP]),
     "pse_sample_f64": (_ST, [_VP, _I64, _VP, _U64, _U64, _VP, _VP, _VP, _VP]),
     "pse_real_matvec": (_ST, [_VP, _I64, _VP, _VP, _VP, _VP]),
+    "pse_sample_with_forces": (_ST, [_VP, _I64, _VP, _VP, _U64, _U64, ctypes.c_double, ctypes.c_double, _VP, _VP]),
+    "pse_sample_with_forces_f64": (_ST, [_VP, _I64, _VP, _VP, _U64, _U64, ctypes.c_double, ctypes.c_double, _VP,
+                                         _VP]),
+    "pse_mobility_apply": (_ST, [_VP, _I64, _VP, _VP, _VP, _VP]),
     "pse_get_stats": (_ST, [_VP, ctypes.POINTER(pse_stats)]),
     "pse_strerror": (ctypes.c_char_p, [_ST]),
     "pse_profile_stages": (_ST, [_VP, _I64, _VP, _U64, _U64, _VP, _VP, _VP, _VP]),

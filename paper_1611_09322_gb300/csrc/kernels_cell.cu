@@ -117,13 +117,19 @@ __global__ void __launch_bounds__(128) k_nbr(int64_t N, Geom<T> g, const V4<T> *
         int cx, cy, cz;
         cell_xyz(c, g.nb, cx, cy, cz);
         for (int ox = -1; ox <= 1; ++ox) {
-            const int ax = (cx + ox + nc) % nc;
+            int ax = cx + ox;
+            ax += ax < 0 ? nc : 0;
+            ax -= ax >= nc ? nc : 0;
             const T sx = T(ox) * g.cs + T(ox) * g.cs_lo;
             for (int oy = -1; oy <= 1; ++oy) {
-                const int ay = (cy + oy + nc) % nc;
+                int ay = cy + oy;
+                ay += ay < 0 ? nc : 0;
+                ay -= ay >= nc ? nc : 0;
                 const T sy = T(oy) * g.cs + T(oy) * g.cs_lo;
                 for (int oz = -1; oz <= 1; ++oz) {
-                    const int az = (cz + oz + nc) % nc;
+                    int az = cz + oz;
+                    az += az < 0 ? nc : 0;
+                    az -= az >= nc ? nc : 0;
                     const T sz = T(oz) * g.cs + T(oz) * g.cs_lo;
                     const int code = ((ox + 1) << 4) | ((oy + 1) << 2) | (oz + 1);
                     const int c2 = cell_id(ax, ay, az, g.nb);

@@ -81,9 +81,10 @@ __global__ void __launch_bounds__(256) k_lz_init(int64_t N, const SampleArgs<T> 
 // group of TPP consecutive threads shares one particle: thread g of the
 // group takes entries g, g + TPP, ... and the group sums by shuffles.  Each
 // neighbour costs one 4-byte list entry and one 32-byte record; a thread
-// issues MV_ILP list loads, then MV_ILP record loads, before any arithmetic,
-// so that many independent gathers are in flight.
-#define MV_ILP 4
+// issues ILP list loads, then ILP record loads, before any arithmetic, so
+// that many independent gathers are in flight.  The first round's list
+// loads do not wait for the particle's count: entries up to the ELL
+// capacity K are always in the array, and those past the count are dropped.
 
 template <typename T>
 __device__ __forceinline__ void pair_fg(T r, const Geom<T> &g, const V4<T> *__restrict__ table, T &F, T &GmF) {
@@ -105,30 +106,54 @@ __device__ __forceinline__ void pair_fg(T r, const Geom<T> &g, const V4<T> *__re
     }
 }
 
+// One matvec record, read-only for the kernel's lifetime: a single 256-bit
+// load for float records (one L1 request per neighbour instead of two).
+template <typename T> __device__ __forceinline__ Rec<T> load_rec(const Rec<T> *__restrict__ p) {
+    if constexpr (sizeof(T) == 4) {
+        Rec<T> r;
+        asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+            : "=f"(r.l.x), "=f"(r.l.y), "=f"(r.l.z), "=f"(r.l.w), "=f"(r.q.x), "=f"(r.q.y), "=f"(r.q.z), "=f"(r.q.w)
+            : "l"(p));
+        return r;
+    } else {
+        return *p;
+    }
+}
+
 // Row s of M_r q without the self term, summed over the TPP-thread group.
-template <typename T, int TPP>
-__device__ __forceinline__ void mr_row_part(int64_t N, int64_t s, int lane_g, bool active, const Geom<T> &g,
+template <typename T, int TPP, int ILP>
+__device__ __forceinline__ void mr_row_part(int64_t N, int64_t s, int lane_g, bool active, int K, const Geom<T> &g,
                                             const Rec<T> *__restrict__ rec, const int *__restrict__ count,
                                             const int *__restrict__ nbr, const V4<T> *__restrict__ table,
                                             V4<T> &li, V4<T> &qi, T &ax, T &ay, T &az) {
     ax = ay = az = T(0);
     if (active) {
-        const Rec<T> ri = rec[s];
+        const int cnt = count[s];
+        int ent[ILP];
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+            const int k = lane_g + u * TPP;
+            ent[u] = k < K ? __ldg(nbr + (int64_t)k * N + s) : -1;
+        }
+        const Rec<T> ri = load_rec(rec + s);
         li = ri.l;
         qi = ri.q;
-        const int cnt = count[s];
-        for (int k0 = lane_g; k0 < cnt; k0 += MV_ILP * TPP) {
-            int ent[MV_ILP];
+        for (int k0 = lane_g; k0 < cnt; k0 += ILP * TPP) {
+            if (k0 != lane_g) {
 #pragma unroll
-            for (int u = 0; u < MV_ILP; ++u) {
-                const int k = k0 + u * TPP;
-                ent[u] = k < cnt ? __ldg(nbr + (int64_t)k * N + s) : -1;
+                for (int u = 0; u < ILP; ++u) {
+                    const int k = k0 + u * TPP;
+                    ent[u] = k < K ? __ldg(nbr + (int64_t)k * N + s) : -1;
+                }
             }
-            Rec<T> rt[MV_ILP];
 #pragma unroll
-            for (int u = 0; u < MV_ILP; ++u) rt[u] = rec[ent[u] >= 0 ? (ent[u] >> 6) : s];
+            for (int u = 0; u < ILP; ++u)
+                if (k0 + u * TPP >= cnt) ent[u] = -1;
+            Rec<T> rt[ILP];
 #pragma unroll
-            for (int u = 0; u < MV_ILP; ++u) {
+            for (int u = 0; u < ILP; ++u) rt[u] = load_rec(rec + (ent[u] >= 0 ? (ent[u] >> 6) : s));
+#pragma unroll
+            for (int u = 0; u < ILP; ++u) {
                 if (ent[u] < 0) continue;
                 const int e = ent[u];
                 const int ox = ((e >> 4) & 3) - 1, oy = ((e >> 2) & 3) - 1, oz = (e & 3) - 1;
@@ -157,8 +182,8 @@ __device__ __forceinline__ void mr_row_part(int64_t N, int64_t s, int lane_g, bo
     }
 }
 
-template <typename T, int TPP>
-__global__ void __launch_bounds__(128) k_lz_matvec(int64_t N, Geom<T> g, const Rec<T> *__restrict__ rec,
+template <typename T, int TPP, int ILP>
+__global__ void __launch_bounds__(128) k_lz_matvec(int64_t N, int K, Geom<T> g, const Rec<T> *__restrict__ rec,
                                                    const int *__restrict__ count, const int *__restrict__ nbr,
                                                    const V4<T> *__restrict__ table, V4<T> *u, double *partials,
                                                    LzState *lz, const float *__restrict__ pc,
@@ -178,7 +203,7 @@ __global__ void __launch_bounds__(128) k_lz_matvec(int64_t N, Geom<T> g, const R
         const bool active = s < end;
         V4<T> li, qi;
         T ax, ay, az;
-        mr_row_part<T, TPP>(N, s, lane_g, active, g, rec, count, nbr, table, li, qi, ax, ay, az);
+        mr_row_part<T, TPP, ILP>(N, s, lane_g, active, K, g, rec, count, nbr, table, li, qi, ax, ay, az);
         if (active && lane_g == 0) {
             V4<T> o;
             o.x = ax + g.self_m * qi.x;
@@ -407,9 +432,12 @@ __global__ void k_batch_cond(LzState *const *lzs, int nsys, cudaGraphConditional
 
 // ------------------------------------------------------------------ final combination
 // x_s = sum_{i=1..J} coef_i q_i[s]  (+ wave part), written in caller order.
+// On the forces path (udet != null) out = c_noise x + c_det M_r F + wave, the
+// wave part already carrying both weights.
 template <typename T>
 __global__ void k_lz_final(int64_t N, const SampleArgs<T> *args, const V4<T> *pos_sorted, const V4<T> *basis,
-                           const V4<T> *uwave, const LzState *lz, bool with_wave, const float *__restrict__ pc) {
+                           const V4<T> *uwave, const LzState *lz, bool with_wave, const float *__restrict__ pc,
+                           const V4<T> *udet) {
     __shared__ T cf[PSE_MAXIT + 2];
     __shared__ double cfd[PSE_MAXIT + 2];
     const int J = lz->J;
@@ -445,7 +473,28 @@ __global__ void k_lz_final(int64_t N, const SampleArgs<T> *args, const V4<T> *po
     }
     if (args->real) { args->real[o] = x; args->real[o + 1] = y; args->real[o + 2] = z; }
     if (args->wave && with_wave) { args->wave[o] = wx; args->wave[o + 1] = wy; args->wave[o + 2] = wz; }
+    if (udet) {
+        const T cn = (T)args->c_noise, cd = (T)args->c_det;
+        const V4<T> m = udet[s];
+        x = cn * x + cd * m.x;
+        y = cn * y + cd * m.y;
+        z = cn * z + cd * m.z;
+    }
     if (args->out) { args->out[o] = x + wx; args->out[o + 1] = y + wy; args->out[o + 2] = z + wz; }
+}
+
+// Forces path without noise: out = c_det M_r F + wave part (c_det M_w F), caller order.
+template <typename T>
+__global__ void k_det_final(int64_t N, const SampleArgs<T> *args, const V4<T> *pos_sorted, const V4<T> *udet,
+                            const V4<T> *uwave) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const int64_t o = 3 * w_bits_r(pos_sorted[s].w);
+    const T cd = (T)args->c_det;
+    const V4<T> m = udet[s], w = uwave[s];
+    args->out[o] = cd * m.x + w.x;
+    args->out[o + 1] = cd * m.y + w.y;
+    args->out[o + 2] = cd * m.z + w.z;
 }
 
 // ------------------------------------------------------------------ caller-vector matvec
@@ -460,7 +509,7 @@ __global__ void k_gather_vec(int64_t N, const SampleArgs<T> *args, const V4<T> *
 }
 
 template <typename T, int TPP>
-__global__ void __launch_bounds__(128) k_matvec_scatter(int64_t N, const SampleArgs<T> *args, Geom<T> g,
+__global__ void __launch_bounds__(128) k_matvec_scatter(int64_t N, int K, const SampleArgs<T> *args, Geom<T> g,
                                                         const Rec<T> *rec, const int *count, const int *nbr,
                                                         const V4<T> *table, const V4<T> *pos_sorted) {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -469,12 +518,33 @@ __global__ void __launch_bounds__(128) k_matvec_scatter(int64_t N, const SampleA
     const bool active = s < N;
     V4<T> li, qi;
     T ax, ay, az;
-    mr_row_part<T, TPP>(N, s, lane_g, active, g, rec, count, nbr, table, li, qi, ax, ay, az);
+    mr_row_part<T, TPP, 4>(N, s, lane_g, active, K, g, rec, count, nbr, table, li, qi, ax, ay, az);
     if (!active || lane_g != 0) return;
     const int64_t i = 3 * w_bits_r(pos_sorted[s].w);
     args->out[i] = ax + g.self_m * qi.x;
     args->out[i + 1] = ay + g.self_m * qi.y;
     args->out[i + 2] = az + g.self_m * qi.z;
+}
+
+// M_r v for v already gathered into the records; output in sorted order.
+template <typename T, int TPP>
+__global__ void __launch_bounds__(128) k_matvec_sorted(int64_t N, int K, Geom<T> g, const Rec<T> *rec,
+                                                       const int *count, const int *nbr, const V4<T> *table,
+                                                       V4<T> *out) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t s = tid / TPP;
+    const int lane_g = (int)(tid % TPP);
+    const bool active = s < N;
+    V4<T> li, qi;
+    T ax, ay, az;
+    mr_row_part<T, TPP, 4>(N, s, lane_g, active, K, g, rec, count, nbr, table, li, qi, ax, ay, az);
+    if (!active || lane_g != 0) return;
+    V4<T> o;
+    o.x = ax + g.self_m * qi.x;
+    o.y = ay + g.self_m * qi.y;
+    o.z = az + g.self_m * qi.z;
+    o.w = T(0);
+    out[s] = o;
 }
 
 // ------------------------------------------------------------------ launchers
@@ -493,10 +563,20 @@ void launch_lz_init(int64_t N, const SampleArgs<T> *args, int system, const Dev<
     k_lz_init<T><<<pgrid(N, 256, 8), 256, 0, s>>>(N, args, system, d.pos_sorted, d.basis, d.rec, d.partials, d.lz,
                                                   sizeof(T) == 4 ? d.pc_on : nullptr);
 }
+// Matvec launch shapes (threads per particle, independent gathers per thread),
+// selected by Geom::mv; the sampler may time them all and keep the fastest.
+template <typename T, int TPP, int ILP> void mv_launch(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
+    k_lz_matvec<T, TPP, ILP><<<pgrid(N, 128 / TPP, 16), 128, 0, s>>>(
+        N, nbr_k(N, d.nbr_cap), g, d.rec, d.nbr_count, d.nbr, d.table, d.u, d.partials, d.lz,
+        sizeof(T) == 4 ? d.pc_on : nullptr, d.basis);
+}
 template <typename T> void launch_lz_matvec(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
-    k_lz_matvec<T, kMvTpp><<<pgrid(N, 128 / kMvTpp, 16), 128, 0, s>>>(N, g, d.rec, d.nbr_count, d.nbr, d.table,
-                                                                        d.u, d.partials, d.lz,
-                                                                        sizeof(T) == 4 ? d.pc_on : nullptr, d.basis);
+    switch (g.mv) {
+        case 1: mv_launch<T, 8, 2>(N, g, d, s); break;
+        case 2: mv_launch<T, 16, 1>(N, g, d, s); break;
+        case 3: mv_launch<T, 4, 2>(N, g, d, s); break;
+        default: mv_launch<T, 4, 4>(N, g, d, s); break;
+    }
 }
 template <typename T> void launch_lz_update(int64_t N, int, const Dev<T> &d, cudaStream_t s) {
     k_lz_update<T><<<pgrid(N, 256, 8), 256, 0, s>>>(N, d.basis, d.rec, d.u, d.partials + num_sms() * 16 + 32, d.lz,
@@ -512,12 +592,28 @@ void launch_batch_cond(LzState *const *lzs, int nsys, cudaGraphConditionalHandle
 template <typename T>
 void launch_lz_final(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, bool with_wave, cudaStream_t s) {
     k_lz_final<T><<<nb(N, 256), 256, 0, s>>>(N, args, d.pos_sorted, d.basis, d.uwave, d.lz, with_wave,
-                                             sizeof(T) == 4 ? d.pc_on : nullptr);
+                                             sizeof(T) == 4 ? d.pc_on : nullptr, nullptr);
+}
+template <typename T>
+void launch_lz_final_forces(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, cudaStream_t s) {
+    k_lz_final<T><<<nb(N, 256), 256, 0, s>>>(N, args, d.pos_sorted, d.basis, d.uwave, d.lz, true,
+                                             sizeof(T) == 4 ? d.pc_on : nullptr, d.udet);
+}
+template <typename T> void launch_det_final(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, cudaStream_t s) {
+    k_det_final<T><<<nb(N, 256), 256, 0, s>>>(N, args, d.pos_sorted, d.udet, d.uwave);
+}
+template <typename T> void launch_gather_vec(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, cudaStream_t s) {
+    k_gather_vec<T><<<nb(N, 256), 256, 0, s>>>(N, args, d.pos_sorted, d.rec);
+}
+template <typename T> void launch_matvec_sorted(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
+    k_matvec_sorted<T, kMvTpp><<<nb(N * kMvTpp, 128), 128, 0, s>>>(N, nbr_k(N, d.nbr_cap), g, d.rec, d.nbr_count,
+                                                                    d.nbr, d.table, d.udet);
 }
 template <typename T>
 void launch_matvec_caller(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
     k_gather_vec<T><<<nb(N, 256), 256, 0, s>>>(N, args, d.pos_sorted, d.rec);
-    k_matvec_scatter<T, kMvTpp><<<nb(N * kMvTpp, 128), 128, 0, s>>>(N, args, g, d.rec, d.nbr_count, d.nbr, d.table,
+    k_matvec_scatter<T, kMvTpp><<<nb(N * kMvTpp, 128), 128, 0, s>>>(N, nbr_k(N, d.nbr_cap), args, g, d.rec,
+                                                                     d.nbr_count, d.nbr, d.table,
                                                                     d.pos_sorted);
 }
 
@@ -526,6 +622,10 @@ void launch_matvec_caller(int64_t N, const SampleArgs<T> *args, Geom<T> g, const
     template void launch_lz_matvec<T>(int64_t, Geom<T>, const Dev<T> &, cudaStream_t);                       \
     template void launch_lz_update<T>(int64_t, int, const Dev<T> &, cudaStream_t);                           \
     template void launch_lz_final<T>(int64_t, const SampleArgs<T> *, const Dev<T> &, bool, cudaStream_t);    \
+    template void launch_lz_final_forces<T>(int64_t, const SampleArgs<T> *, const Dev<T> &, cudaStream_t);   \
+    template void launch_det_final<T>(int64_t, const SampleArgs<T> *, const Dev<T> &, cudaStream_t);         \
+    template void launch_gather_vec<T>(int64_t, const SampleArgs<T> *, const Dev<T> &, cudaStream_t);        \
+    template void launch_matvec_sorted<T>(int64_t, Geom<T>, const Dev<T> &, cudaStream_t);                   \
     template void launch_matvec_caller<T>(int64_t, const SampleArgs<T> *, Geom<T>, const Dev<T> &, cudaStream_t);
 PSE_INST(float)
 PSE_INST(double)

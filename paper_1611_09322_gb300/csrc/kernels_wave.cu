@@ -31,11 +31,63 @@ template <typename T> __device__ __forceinline__ T sqrt_t(T x) {
     else return sqrt(x);
 }
 
-// One thread per half-spectrum mode (ix, iy, iz), iz in [0, M/2].  The noise
-// of a {k, -k} pair is keyed by its representative (nz > 0, or nz = 0 and
-// (ny > 0 or (ny = 0 and nx > 0))), id q = (ix*M + iy)*Mh1 + iz, Philox
-// blocks 2q and 2q+1; a thread holding the partner draws the same numbers
-// and conjugates them, so the kz = 0 plane is exactly Hermitian.  k = 0 and
+// Mode (ix, iy, iz) of the half spectrum, iz in [0, M/2]: signed indices,
+// and whether it carries noise (k != 0, no Nyquist index).
+struct ModeIdx {
+    int ix, iy, iz, nx, ny, nz;
+    bool live;
+};
+__device__ __forceinline__ ModeIdx mode_of(int64_t t, int M, int Mh1) {
+    ModeIdx m;
+    m.iz = (int)(t % Mh1);
+    m.iy = (int)((t / Mh1) % M);
+    m.ix = (int)(t / ((int64_t)Mh1 * M));
+    const int half = M / 2;
+    m.nx = m.ix <= half ? m.ix : m.ix - M;
+    m.ny = m.iy <= half ? m.iy : m.iy - M;
+    m.nz = m.iz;
+    const bool nyq = (M % 2) == 0 && (m.ix == half || m.iy == half || m.iz == half);
+    m.live = !nyq && (m.nx | m.ny | m.nz) != 0;
+    return m;
+}
+
+// dW2 of a live mode: the noise of a {k, -k} pair is keyed by its
+// representative (nz > 0, or nz = 0 and (ny > 0 or (ny = 0 and nx > 0))),
+// id q = (ix*M + iy)*Mh1 + iz, Philox blocks 2q and 2q+1; a mode holding the
+// partner draws the same numbers and conjugates them, so the kz = 0 plane is
+// exactly Hermitian.
+template <typename T>
+__device__ __forceinline__ void mode_noise(const ModeIdx &m, int M, int Mh1, uint32_t strm, uint64_t seed,
+                                           uint64_t sample, T wr[3], T wi[3]) {
+    int rx = m.ix, ry = m.iy;
+    bool conj = false;
+    if (m.nz == 0 && !(m.ny > 0 || (m.ny == 0 && m.nx > 0))) {
+        rx = (M - m.ix) % M;
+        ry = (M - m.iy) % M;
+        conj = true;
+    }
+    const uint32_t q = (uint32_t)(((int64_t)rx * M + ry) * Mh1 + m.iz);
+    const Normals4<T> a = normals4<T>(2u * q, strm, seed, sample);
+    const Normals4<T> b = normals4<T>(2u * q + 1u, strm, seed, sample);
+    const T s2 = T(0.70710678118654752440);
+    wr[0] = a.v[0] * s2; wr[1] = a.v[2] * s2; wr[2] = b.v[0] * s2;
+    wi[0] = a.v[1] * s2; wi[1] = a.v[3] * s2; wi[2] = b.v[1] * s2;
+    if (conj) { wi[0] = -wi[0]; wi[1] = -wi[1]; wi[2] = -wi[2]; }
+}
+
+// Unit wave vector and the noise scale
+//   sc(k) = V^{-1/2} sinc(ka)/k sqrt(1 + k^2/4xi^2) exp(-(1 - eta) k^2 / 8xi^2)
+// of a live mode.
+template <typename T>
+__device__ __forceinline__ T mode_scale(const ModeIdx &m, const WaveGeom<T> &w, T &hx, T &hy, T &hz) {
+    const T kx = w.kscale * m.nx, ky = w.kscale * m.ny, kz = w.kscale * m.nz;
+    const T k2 = kx * kx + ky * ky + kz * kz;
+    const T k = sqrt_t(k2);
+    hx = kx / k; hy = ky / k; hz = kz / k;
+    return w.inv_sqrtV * sinc_over_k(k, w.a) * sqrt_t(T(1) + k2 * w.inv4xi2) * exp_t(-w.decay * k2);
+}
+
+// One thread per half-spectrum mode: vhat = sc(k) (I - kk) dW2(k); k = 0 and
 // Nyquist modes are zero.
 template <typename T>
 __global__ void k_wave_noise(WaveGeom<T> w, const SampleArgs<T> *args, int system, typename Cplx<T>::type *spec,
@@ -44,40 +96,16 @@ __global__ void k_wave_noise(WaveGeom<T> w, const SampleArgs<T> *args, int syste
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nmodes = (int64_t)w.M * w.M * w.Mh1;
     if (t >= nmodes) return;
-    const int iz = (int)(t % w.Mh1);
-    const int iy = (int)((t / w.Mh1) % w.M);
-    const int ix = (int)(t / ((int64_t)w.Mh1 * w.M));
-    const int M = w.M, half = M / 2;
-    const int nx = ix <= half ? ix : ix - M;
-    const int ny = iy <= half ? iy : iy - M;
-    const int nz = iz;
-    const bool even = (M % 2) == 0;
-    const bool nyq = even && (ix == half || iy == half || iz == half);
+    const ModeIdx m = mode_of(t, w.M, w.Mh1);
     C o0, o1, o2;
     o0.x = o0.y = o1.x = o1.y = o2.x = o2.y = T(0);
-    if (!nyq && (nx | ny | nz) != 0) {
-        int rx = ix, ry = iy;
-        bool conj = false;
-        if (nz == 0 && !(ny > 0 || (ny == 0 && nx > 0))) {
-            rx = (M - ix) % M;
-            ry = (M - iy) % M;
-            conj = true;
-        }
-        const uint32_t q = (uint32_t)(((int64_t)rx * M + ry) * w.Mh1 + iz);
-        const uint32_t strm = 2u * system + 1u;
-        const Normals4<T> a = normals4<T>(2u * q, strm, args->seed, args->sample);
-        const Normals4<T> b = normals4<T>(2u * q + 1u, strm, args->seed, args->sample);
-        const T s2 = T(0.70710678118654752440);
-        T wr[3] = {a.v[0] * s2, a.v[2] * s2, b.v[0] * s2};
-        T wi[3] = {a.v[1] * s2, a.v[3] * s2, b.v[1] * s2};
-        if (conj) { wi[0] = -wi[0]; wi[1] = -wi[1]; wi[2] = -wi[2]; }
-        const T kx = w.kscale * nx, ky = w.kscale * ny, kz = w.kscale * nz;
-        const T k2 = kx * kx + ky * ky + kz * kz;
-        const T k = sqrt_t(k2);
-        const T hx = kx / k, hy = ky / k, hz = kz / k;
+    if (m.live) {
+        T wr[3], wi[3];
+        mode_noise<T>(m, w.M, w.Mh1, 2u * system + 1u, args->seed, args->sample, wr, wi);
+        T hx, hy, hz;
+        const T sc = mode_scale<T>(m, w, hx, hy, hz);
         const T dr = hx * wr[0] + hy * wr[1] + hz * wr[2];
         const T di = hx * wi[0] + hy * wi[1] + hz * wi[2];
-        const T sc = w.inv_sqrtV * sinc_over_k(k, w.a) * sqrt_t(T(1) + k2 * w.inv4xi2) * exp_t(-w.decay * k2);
         o0.x = sc * (wr[0] - hx * dr); o0.y = sc * (wi[0] - hx * di);
         o1.x = sc * (wr[1] - hy * dr); o1.y = sc * (wi[1] - hy * di);
         o2.x = sc * (wr[2] - hz * dr); o2.y = sc * (wi[2] - hz * di);
@@ -85,6 +113,73 @@ __global__ void k_wave_noise(WaveGeom<T> w, const SampleArgs<T> *args, int syste
     spec[t] = o0;
     spec[plane + t] = o1;
     spec[2 * plane + t] = o2;
+}
+
+// Mode factor applied in place to a forward (R2C) spectrum, one thread per
+// half-spectrum mode, k = 0 and Nyquist set to zero:
+//   WAVE_MODE_DET:       vhat = c_det norm sc^2 (I - kk) Fhat  [+ c_noise sc (I - kk) dW2]
+//     Fhat = DFT of the unnormalised spread grid sum_i w_x w_y w_z F_i; with the
+//     Gaussian's constant norm = (2xi^2/(pi eta))^{3/2} h^3 this is
+//     h^3 B(k)/V (I - kk) DFT(S F), the deterministic wave product, and the
+//     optional k-space noise term fuses the Brownian wave part into the same
+//     inverse FFT (Sec. III);
+//   WAVE_MODE_GRIDNOISE: vhat = c_noise sc M^{-3/2} (I - kk) What, What the DFT of white
+//     grid noise, which on every live mode pair has the law of dW2.
+template <typename T>
+__global__ void k_wave_apply(WaveGeom<T> w, const SampleArgs<T> *args, int system, typename Cplx<T>::type *spec,
+                             int64_t plane, int mode, int with_noise) {
+    using C = typename Cplx<T>::type;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nmodes = (int64_t)w.M * w.M * w.Mh1;
+    if (t >= nmodes) return;
+    const ModeIdx m = mode_of(t, w.M, w.Mh1);
+    C o[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o[c].x = o[c].y = T(0);
+    if (m.live) {
+        T hx, hy, hz;
+        const T sc = mode_scale<T>(m, w, hx, hy, hz);
+        const C i0 = spec[t], i1 = spec[plane + t], i2 = spec[2 * plane + t];
+        T f;
+        if (mode == WAVE_MODE_DET) f = (T)args->c_det * w.norm * sc * sc;
+        else f = (T)args->c_noise * sc * w.inv_M15;
+        T vr[3] = {i0.x, i1.x, i2.x}, vi[3] = {i0.y, i1.y, i2.y};
+        const T dr = hx * vr[0] + hy * vr[1] + hz * vr[2];
+        const T di = hx * vi[0] + hy * vi[1] + hz * vi[2];
+        const T hh[3] = {hx, hy, hz};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            o[c].x = f * (vr[c] - hh[c] * dr);
+            o[c].y = f * (vi[c] - hh[c] * di);
+        }
+        if (mode == WAVE_MODE_DET && with_noise) {
+            T wr[3], wi[3];
+            mode_noise<T>(m, w.M, w.Mh1, 2u * system + 1u, args->seed, args->sample, wr, wi);
+            const T g = (T)args->c_noise * sc;
+            const T er = hx * wr[0] + hy * wr[1] + hz * wr[2];
+            const T ei = hx * wi[0] + hy * wi[1] + hz * wi[2];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                o[c].x += g * (wr[c] - hh[c] * er);
+                o[c].y += g * (wi[c] - hh[c] * ei);
+            }
+        }
+    }
+    spec[t] = o[0];
+    spec[plane + t] = o[1];
+    spec[2 * plane + t] = o[2];
+}
+
+// White noise on the grid: node g = (ix*M + iy)*M + iz keys one Philox block
+// on the wave stream; its first three normals are the x, y, z components.
+template <typename T>
+__global__ void k_grid_noise(int64_t M3, const SampleArgs<T> *args, int system, T *grid) {
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= M3) return;
+    const Normals4<T> n = normals4<T>((uint32_t)g, 2u * system + 1u, args->seed, args->sample);
+    grid[g] = n.v[0];
+    grid[M3 + g] = n.v[1];
+    grid[2 * M3 + g] = n.v[2];
 }
 
 // Support start and fractional offset of one coordinate: s = x M / L as a
@@ -120,6 +215,206 @@ __device__ __forceinline__ int wrap_grid(int i, int M) {  // valid for i in [-M,
     return i >= M ? i - M : i;
 }
 
+// ------------------------------------------------------------------ spreading
+// Grid force density (unnormalised): grid_c(x_g) += sum_i w_x w_y w_z F_i,c over
+// each particle's P^3 support, w = exp(-ch2 (u - p)^2) per axis as in the
+// interpolation (the Gaussian's constant is applied in the mode factor).
+//
+// One CTA per tile of G^3 cells.  The tile's particles (cell-sorted, so each
+// cell is a contiguous run) are spread into a padded E^3 node block in shared
+// memory with shared-memory atomics, CP components per pass.  The block
+// starts at the node orig[t] of each axis (host-computed: the support start of
+// the tile's lower corner less one node) and E bounds the support of every
+// particle of the tile with one node of margin on each side.  Two ways out:
+//   scratch != null: the block is stored to scratch[tile][component] (plain
+//     coalesced stores); k_spread_gather then sums, for every grid node, the
+//     blocks that cover it (no global atomics);
+//   scratch == null: the block is added to the grid with one coalesced float
+//     atomic per nonzero node.
+// A particle whose support still falls outside the block (not expected, kept
+// for safety) adds straight into the global grid, which is cleared first.
+#define PSE_SPREAD_THREADS 1024  // threads per CTA (occupancy while the shared atomics wait)
+#define PSE_SPREAD_CHUNK 256     // particles staged per pass
+
+__device__ __forceinline__ int pmod(int i, int M) {
+    const int r = i % M;
+    return r < 0 ? r + M : r;
+}
+
+template <typename T> __device__ __forceinline__ int64_t caller_of(T w) {
+    if constexpr (sizeof(T) == 4) return (int64_t)__float_as_int(w);
+    else return (int64_t)__double_as_longlong(w);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PSE_SPREAD_THREADS)
+    k_spread(WaveGeom<T> w, Geom<T> g, SpreadTile st, const int *__restrict__ orig, const V4<T> *__restrict__ pos_sorted,
+             const int *__restrict__ cell_start, const SampleArgs<T> *args, T *grid, T *scratch) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int E = st.E, E2 = E * E, E3 = E2 * E, P = w.P, CP = st.CP, G = st.G, M = w.M;
+    const int64_t M3 = (int64_t)M * M * M;
+    T *tile = (T *)smem_raw;                                // CP * E^3
+    T *wts = tile + CP * E3;                                // CHUNK * 3P
+    T *fv = wts + PSE_SPREAD_CHUNK * 3 * P;                 // CHUNK * 3
+    int *base = (int *)(fv + PSE_SPREAD_CHUNK * 3);         // CHUNK
+    int *cst = base + PSE_SPREAD_CHUNK;                     // 64: first sorted index of each cell
+    int *coff = cst + 64;                                   // 65: prefix of the cells' counts
+    __shared__ int s_ncell;
+
+    const int t = blockIdx.x;
+    const int tz = t % st.ntx, ty = (t / st.ntx) % st.ntx, tx = t / (st.ntx * st.ntx);
+    const int c0x = tx * G, c0y = ty * G, c0z = tz * G;
+    const int ox = orig[tx], oy = orig[ty], oz = orig[tz];
+    // cells of the tile and their particle runs
+    const int G3 = G * G * G;
+    if (threadIdx.x < G3) {
+        const int a = threadIdx.x / (G * G), b = (threadIdx.x / G) % G, c = threadIdx.x % G;
+        const int cx = c0x + a, cy = c0y + b, cz = c0z + c;
+        int s0 = 0, n = 0;
+        if (cx < g.nc && cy < g.nc && cz < g.nc) {
+            const int id = cell_id(cx, cy, cz, g.nb);
+            s0 = cell_start[id];
+            n = cell_start[id + 1] - s0;
+        }
+        cst[threadIdx.x] = s0;
+        coff[threadIdx.x + 1] = n;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        coff[0] = 0;
+        for (int j = 1; j <= G3; ++j) coff[j] += coff[j - 1];
+        s_ncell = G3;
+    }
+    __syncthreads();
+    const int ntile = coff[s_ncell];
+    T *out = scratch ? scratch + (int64_t)t * 3 * E3 : nullptr;
+    if (ntile == 0) {
+        if (out)
+            for (int i = threadIdx.x; i < 3 * E3; i += blockDim.x) out[i] = T(0);
+        return;
+    }
+    const int PP = P * P;
+
+    for (int cp0 = 0; cp0 < 3; cp0 += CP) {
+        for (int i = threadIdx.x; i < CP * E3; i += blockDim.x) tile[i] = T(0);
+        __syncthreads();
+        for (int p0 = 0; p0 < ntile; p0 += PSE_SPREAD_CHUNK) {
+            const int np = min(PSE_SPREAD_CHUNK, ntile - p0);
+            if (threadIdx.x < np) {
+                const int k = p0 + threadIdx.x;
+                int lo = 0, hi = s_ncell - 1;  // last cell j with coff[j] <= k
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (coff[mid] <= k) lo = mid;
+                    else hi = mid - 1;
+                }
+                const V4<T> p = pos_sorted[cst[lo] + (k - coff[lo])];
+                const T *F = args->vin + 3 * caller_of(p.w);
+                int i0x, i0y, i0z;
+                T ux, uy, uz;
+                support(p.x, w, i0x, ux);
+                support(p.y, w, i0y, uy);
+                support(p.z, w, i0z, uz);
+                T *wv = wts + threadIdx.x * 3 * P;
+                for (int q = 0; q < P; ++q) {
+                    const T dx = ux - T(q), dy = uy - T(q), dz = uz - T(q);
+                    wv[q] = exp_t(-w.ch2 * dx * dx);
+                    wv[P + q] = exp_t(-w.ch2 * dy * dy);
+                    wv[2 * P + q] = exp_t(-w.ch2 * dz * dz);
+                }
+                T *f = fv + threadIdx.x * 3;
+                f[0] = F[0]; f[1] = F[1]; f[2] = F[2];
+                const int lx = i0x - ox, ly = i0y - oy, lz = i0z - oz;
+                const bool inside = lx >= 0 && ly >= 0 && lz >= 0 && lx + P <= E && ly + P <= E && lz + P <= E;
+                base[threadIdx.x] = inside ? (lx * E + ly) * E + lz : -1;
+                if (!inside) {
+                    for (int a = 0; a < P; ++a)
+                        for (int b = 0; b < P; ++b)
+                            for (int c = 0; c < P; ++c) {
+                                const T wt = wv[a] * wv[P + b] * wv[2 * P + c];
+                                const int64_t gi =
+                                    ((int64_t)pmod(i0x + a, M) * M + pmod(i0y + b, M)) * M + pmod(i0z + c, M);
+                                for (int cc = 0; cc < CP; ++cc) atomicAdd(grid + (cp0 + cc) * M3 + gi, wt * f[cp0 + cc]);
+                            }
+                }
+            }
+            __syncthreads();
+            // thread t owns the (y, z) node pair q = t mod P^2 of particles
+            // t / P^2, t / P^2 + stride, ...: no divisions in the loop
+            const int stride = blockDim.x / PP;
+            if (threadIdx.x < stride * PP) {
+                const int q = threadIdx.x % PP, b = q / P, c = q - b * P;
+                for (int pp = threadIdx.x / PP; pp < np; pp += stride) {
+                    const int b0 = base[pp];
+                    if (b0 < 0) continue;
+                    const T *wv = wts + pp * 3 * P;
+                    const T *f = fv + pp * 3 + cp0;
+                    const T wyz = wv[P + b] * wv[2 * P + c];
+                    const int row = b0 + b * E + c;
+                    for (int a = 0; a < P; ++a) {
+                        const T wt = wv[a] * wyz;
+                        for (int cc = 0; cc < CP; ++cc) atomicAdd(tile + cc * E3 + row + a * E2, wt * f[cc]);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (out) {
+            for (int i = threadIdx.x; i < CP * E3; i += blockDim.x) out[cp0 * E3 + i] = tile[i];
+        } else {
+            for (int i = threadIdx.x; i < E3; i += blockDim.x) {
+                const int lz = i % E, ly = (i / E) % E, lx = i / E2;
+                const int64_t gi = ((int64_t)pmod(ox + lx, M) * M + pmod(oy + ly, M)) * M + pmod(oz + lz, M);
+                for (int cc = 0; cc < CP; ++cc) {
+                    const T v = tile[cc * E3 + i];
+                    if (v != T(0)) atomicAdd(grid + (cp0 + cc) * M3 + gi, v);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Second phase of the two-phase spreading: one thread per grid node (z
+// fastest, so the reads of one block row are coalesced) adds the values the
+// covering tile blocks hold for it.  cover[x * PSE_COVER + k] = (tile index
+// along the axis, node offset in that tile's block) for the cnt[x] blocks
+// covering node x along one axis (the same on the three axes of a cube).
+template <typename T>
+__global__ void __launch_bounds__(256) k_spread_gather(int M, int E, int ntx, const int2 *__restrict__ cover,
+                                                       const int *__restrict__ cnt, const T *__restrict__ scratch,
+                                                       T *grid) {
+    const int64_t M3 = (int64_t)M * M * M;
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= M3) return;
+    const int z = (int)(g % M), y = (int)((g / M) % M), x = (int)(g / ((int64_t)M * M));
+    const int E3 = E * E * E;
+    const int nx = cnt[x], ny = cnt[y], nz = cnt[z];
+    T a0 = 0, a1 = 0, a2 = 0;
+    for (int i = 0; i < nx; ++i) {
+        const int2 cx = cover[x * PSE_COVER + i];
+        for (int j = 0; j < ny; ++j) {
+            const int2 cy = cover[y * PSE_COVER + j];
+            for (int k = 0; k < nz; ++k) {
+                const int2 cz = cover[z * PSE_COVER + k];
+                const int64_t tb = ((int64_t)(cx.x * ntx + cy.x) * ntx + cz.x) * 3 * E3;
+                const int off = (cx.y * E + cy.y) * E + cz.y;
+                a0 += scratch[tb + off];
+                a1 += scratch[tb + E3 + off];
+                a2 += scratch[tb + 2 * E3 + off];
+            }
+        }
+    }
+    grid[g] += a0;
+    grid[M3 + g] += a1;
+    grid[2 * M3 + g] += a2;
+}
+
+size_t spread_smem_bytes(SpreadTile st, int P, size_t elem) {
+    return elem * ((size_t)st.CP * st.E * st.E * st.E + (size_t)PSE_SPREAD_CHUNK * (3 * P + 3)) +
+           sizeof(int) * (PSE_SPREAD_CHUNK + 64 + 65);
+}
+
 // G lanes per sorted particle (G = 8, 16 or 32 divides the warp):
 // u_w = norm * sum_{P^3} g_x g_y g_z v(node), separable weights
 // exp(-ch2 (u - p)^2) per axis, periodic node indices.  Lane g of the group
@@ -128,13 +423,9 @@ __device__ __forceinline__ int wrap_grid(int i, int M) {  // valid for i in [-M,
 // first P lanes of the group evaluate the 3P one-dimensional weights, shared
 // by shuffles inside the group.
 template <typename T, int G>
-__global__ void __launch_bounds__(128) k_interp(int64_t N, WaveGeom<T> w, const V4<T> *__restrict__ pos_sorted,
-                                                const T *__restrict__ grid, V4<T> *uwave) {
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t s = tid / G;
-    const int lg = threadIdx.x % G;
-    const int gbase = (threadIdx.x & 31) - lg;  // first lane of this group in the warp
-    const bool active = s < N;
+__device__ __forceinline__ void interp_particle(int64_t s, bool active, int lg, int gbase, const WaveGeom<T> &w,
+                                                const V4<T> *__restrict__ pos_sorted, const T *__restrict__ grid,
+                                                V4<T> *uwave) {
     const V4<T> p = pos_sorted[active ? s : 0];
     const int M = w.M, P = w.P;
     const int64_t M3 = (int64_t)M * M * M;
@@ -186,6 +477,15 @@ __global__ void __launch_bounds__(128) k_interp(int64_t N, WaveGeom<T> w, const 
     }
 }
 
+// One lane group per particle, one launch-wide pass.
+template <typename T, int G>
+__global__ void __launch_bounds__(128) k_interp(int64_t N, WaveGeom<T> w, const V4<T> *__restrict__ pos_sorted,
+                                                const T *__restrict__ grid, V4<T> *uwave) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lg = threadIdx.x % G;
+    interp_particle<T, G>(tid / G, tid / G < N, lg, (threadIdx.x & 31) - lg, w, pos_sorted, grid, uwave);
+}
+
 static inline unsigned nbw(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 template <typename T>
@@ -201,9 +501,60 @@ template <typename T> void launch_interp(int64_t N, WaveGeom<T> w, Geom<T> g, co
     else k_interp<T, 32><<<nbw(N * 32, 128), 128, 0, s>>>(N, w, d.pos_sorted, d.grid, d.uwave);
 }
 
+template <typename T>
+void launch_wave_apply(WaveGeom<T> w, const SampleArgs<T> *args, int system, void *spec, int mode, int with_noise,
+                       cudaStream_t s) {
+    const int64_t plane = (int64_t)w.M * w.M * w.Mh1;
+    k_wave_apply<T><<<nbw(plane, 256), 256, 0, s>>>(w, args, system, (typename Cplx<T>::type *)spec, plane, mode,
+                                                    with_noise);
+}
+template <typename T> void launch_grid_noise(WaveGeom<T> w, const SampleArgs<T> *args, int system, T *grid,
+                                             cudaStream_t s) {
+    const int64_t M3 = (int64_t)w.M * w.M * w.M;
+    k_grid_noise<T><<<nbw(M3, 256), 256, 0, s>>>(M3, args, system, grid);
+}
+// Opt the spreading kernel in to all the dynamic shared memory a block may
+// have on this device (the opt-in limit less the kernel's static shared
+// memory); returns that size.  Called once, outside any stream capture.
+template <typename T> cudaError_t spread_prepare(size_t *max_dynamic) {
+    *max_dynamic = 0;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_spread<T>);
+    if (e != cudaSuccess) return e;
+    const size_t avail = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    e = cudaFuncSetAttribute(k_spread<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)avail);
+    if (e == cudaSuccess) *max_dynamic = avail;
+    return e;
+}
+// Spread into d.grid (cleared by the caller).  With a cover table the tile
+// blocks go through scratch and the gather kernel; otherwise they are added
+// with atomics.
+template <typename T>
+cudaError_t launch_spread(WaveGeom<T> w, Geom<T> g, SpreadTile st, const int *orig, const int2 *cover,
+                          const int *cover_cnt, T *scratch, const Dev<T> &d, cudaStream_t s) {
+    const size_t smem = spread_smem_bytes(st, w.P, sizeof(T));
+    const unsigned tiles = (unsigned)st.ntx * st.ntx * st.ntx;
+    const bool two_phase = scratch && cover && cover_cnt;
+    k_spread<T><<<tiles, PSE_SPREAD_THREADS, smem, s>>>(w, g, st, orig, d.pos_sorted, d.cell_start, d.args, d.grid,
+                                                         two_phase ? scratch : nullptr);
+    if (two_phase) {
+        const int64_t M3 = (int64_t)w.M * w.M * w.M;
+        k_spread_gather<T><<<nbw(M3, 256), 256, 0, s>>>(w.M, st.E, st.ntx, cover, cover_cnt, scratch, d.grid);
+    }
+    return cudaGetLastError();
+}
+
 #define PSE_INST(T)                                                                                      \
     template void launch_wave_noise<T>(WaveGeom<T>, const SampleArgs<T> *, int, void *, cudaStream_t); \
-    template void launch_interp<T>(int64_t, WaveGeom<T>, Geom<T>, const Dev<T> &, cudaStream_t);
+    template void launch_interp<T>(int64_t, WaveGeom<T>, Geom<T>, const Dev<T> &, cudaStream_t);       \
+    template void launch_wave_apply<T>(WaveGeom<T>, const SampleArgs<T> *, int, void *, int, int, cudaStream_t); \
+    template void launch_grid_noise<T>(WaveGeom<T>, const SampleArgs<T> *, int, T *, cudaStream_t);   \
+    template cudaError_t launch_spread<T>(WaveGeom<T>, Geom<T>, SpreadTile, const int *, const int2 *, const int *, \
+                                          T *, const Dev<T> &, cudaStream_t);                                      \
+    template cudaError_t spread_prepare<T>(size_t *);
 PSE_INST(float)
 PSE_INST(double)
 #undef PSE_INST

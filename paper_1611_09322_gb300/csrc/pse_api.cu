@@ -4,7 +4,10 @@
 // One sample is one graph launch.  The graph forks after the cell sort:
 //   real branch:  neighbour list -> WHILE { matvec -> update  ||  eig(T_{j-1}) }
 //   wave branch:  k-space noise -> cuFFT C2R (x3) -> interpolation
-// and joins in the final combination kernel.  The Lanczos loop runs on the
+// and joins in the final combination kernel.  The forces path (c_det M F +
+// c_noise M^{1/2} z) adds M_r F on the real branch before the loop, and its
+// wave branch spreads F, runs cuFFT R2C, applies the deterministic mode
+// factor with the k-space noise fused in, then C2R and interpolation.  The Lanczos loop runs on the
 // device: the eigen kernel of iteration j-1 (FP64, one warp) runs beside the
 // matvec of iteration j and sets the WHILE node's condition, so the host
 // never waits inside a sample.  Per-call arguments (pointers, seed, sample
@@ -37,9 +40,21 @@ struct pse_ctx {
     bool fft_made = false;
     cudaStream_t s_main = nullptr, s_wave = nullptr, s_body = nullptr, s_body2 = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaGraphConditionalHandle cond = 0;
+    cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};  // per graph mode (GM_*)
+    cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+    cudaGraphConditionalHandle cond[3] = {0, 0, 0};
+    cufftHandle fft_r2c = 0;                            // forward FFT (spreading / grid noise)
+    bool r2c_made = false;
+    SpreadTile spread{};                                // spreading tile shape
+    bool spread_ready = false, spread_tuned = false;
+    size_t spread_smem_max = 0;                         // dynamic shared memory the spreading may use
+    int *sp_orig = nullptr;                             // block origin of each tile index (ncell + 1)
+    int2 *sp_cover = nullptr;                           // M * PSE_COVER (tile, offset) pairs
+    int *sp_cnt = nullptr;                              // M: blocks covering each node
+    void *sp_scratch = nullptr;                         // tile blocks of the two-phase spreading
+    size_t sp_scratch_bytes = 0;
+    bool sp_two_phase = false;
+    bool mv_tuned = false;                              // matvec launch shape timed
     cudaStream_t last_stream = nullptr;
     void *stage_pos = nullptr, *stage_out = nullptr;  // device staging for the host-buffer call
     std::vector<void *> per_n;                          // buffers freed when N changes
@@ -99,11 +114,16 @@ void free_list(std::vector<void *> &list) {
     list.clear();
 }
 
+// Graph modes: a plain sample, the forces path with noise, without noise.
+enum { GM_SAMPLE = 0, GM_FORCES_NOISE = 1, GM_FORCES = 2 };
+
 void drop_graph(pse_ctx *c) {
-    if (c->exec) cudaGraphExecDestroy(c->exec);
-    if (c->graph) cudaGraphDestroy(c->graph);
-    c->exec = nullptr;
-    c->graph = nullptr;
+    for (int m = 0; m < 3; ++m) {
+        if (c->exec[m]) cudaGraphExecDestroy(c->exec[m]);
+        if (c->graph[m]) cudaGraphDestroy(c->graph[m]);
+        c->exec[m] = nullptr;
+        c->graph[m] = nullptr;
+    }
 }
 
 template <typename T> void fill_geom(pse_ctx *c) {
@@ -121,6 +141,7 @@ template <typename T> void fill_geom(pse_ctx *c) {
     g.xi = (T)p.xi;
     g.nc = p.ncell;
     g.nb = bricks_per_side(p.ncell);
+    g.mv = c->params.matvec_shape > 0 ? c->params.matvec_shape - 1 : 0;
     geom<T>(c) = g;
     WaveGeom<T> w{};
     w.M = p.M;
@@ -136,6 +157,7 @@ template <typename T> void fill_geom(pse_ctx *c) {
     w.gl_lo = (T)(gl - (double)(T)gl);
     w.ch2 = (T)(2 * p.xi * p.xi * p.h * p.h / p.eta);
     w.norm = (T)(pow(2 * p.xi * p.xi / (M_PI * p.eta), 1.5) * p.h * p.h * p.h);
+    w.inv_M15 = (T)pow((double)p.M, -1.5);
     w.interp_lanes = 16;
     wgeom<T>(c) = w;
 }
@@ -185,6 +207,120 @@ template <typename T> pse_status init_ctx(pse_ctx *c) {
     return PSE_OK;
 }
 
+// Forward (R2C, batch 3) plan: grid -> spectrum, same layouts as the C2R plan.
+template <typename T> pse_status ensure_r2c(pse_ctx *c) {
+    if (c->r2c_made) return PSE_OK;
+    const int M = c->plan.M;
+    const int64_t plane = (int64_t)M * M * (M / 2 + 1);
+    int n[3] = {M, M, M};
+    CKF(cufftPlanMany(&c->fft_r2c, 3, n, nullptr, 1, M * M * M, nullptr, 1, (int)plane,
+                      sizeof(T) == 4 ? CUFFT_R2C : CUFFT_D2Z, 3));
+    c->r2c_made = true;
+    return PSE_OK;
+}
+
+// Spreading tile: G^3 cells per CTA spread into a padded E^3 node block,
+// E = ceil(G cs / h) + P + 2 (support of any particle of the tile, one node
+// of margin each side), CP components per pass; the block must fit the
+// dynamic shared memory a CTA may use (smem_max).
+static bool spread_tile(const pse_plan_info &p, int G, int CP, size_t elem, size_t smem_max, SpreadTile *st) {
+    const double cs = p.L / p.ncell;
+    SpreadTile t;
+    t.G = G;
+    t.CP = CP;
+    t.E = (int)ceil(G * cs / p.h) + p.P + 2;
+    t.ntx = (p.ncell + G - 1) / G;
+    if (spread_smem_bytes(t, p.P, elem) > smem_max) return false;
+    *st = t;
+    return true;
+}
+
+// Make tile t current: block origins of each tile index, the table of blocks
+// covering each grid node and the scratch for the two-phase spreading (used
+// when every node is covered by at most PSE_COVER blocks per axis and the
+// scratch stays within 6 grids; otherwise the blocks are added with atomics).
+template <typename T> pse_status set_spread_tile(pse_ctx *c, const SpreadTile &t) {
+    const pse_plan_info &p = c->plan;
+    const int M = p.M, ntx = t.ntx, E = t.E;
+    const double cs = p.L / p.ncell;
+    std::vector<int> orig(ntx);
+    for (int k = 0; k < ntx; ++k) orig[k] = (int)floor(k * t.G * cs * M / p.L - 0.5 * p.P) + 1 - 1;
+    std::vector<int2> cover((size_t)M * PSE_COVER, int2{0, 0});
+    std::vector<int> cnt(M, 0);
+    bool fits = true;
+    for (int x = 0; x < M && fits; ++x)
+        for (int k = 0; k < ntx && fits; ++k) {
+            int l = (x - orig[k]) % M;
+            if (l < 0) l += M;
+            for (; l < E; l += M) {
+                if (cnt[x] == PSE_COVER) { fits = false; break; }
+                cover[(size_t)x * PSE_COVER + cnt[x]++] = int2{k, l};
+            }
+        }
+    pse_status st;
+    if (!c->sp_orig) {
+        if ((st = alloc(c->per_ctx, (void **)&c->sp_orig, sizeof(int) * (p.ncell + 1))) != PSE_OK) return st;
+        if ((st = alloc(c->per_ctx, (void **)&c->sp_cover, sizeof(int2) * M * PSE_COVER)) != PSE_OK) return st;
+        if ((st = alloc(c->per_ctx, (void **)&c->sp_cnt, sizeof(int) * M)) != PSE_OK) return st;
+    }
+    CK(cudaMemcpy(c->sp_orig, orig.data(), sizeof(int) * ntx, cudaMemcpyHostToDevice));
+    const size_t need = sizeof(T) * 3 * (size_t)ntx * ntx * ntx * (size_t)E * E * E;
+    const size_t grid_bytes = sizeof(T) * 3 * (size_t)M * M * M;
+    c->sp_two_phase = fits && need <= 6 * grid_bytes;
+    if (c->sp_two_phase) {
+        CK(cudaMemcpy(c->sp_cover, cover.data(), sizeof(int2) * M * PSE_COVER, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->sp_cnt, cnt.data(), sizeof(int) * M, cudaMemcpyHostToDevice));
+        if (need > c->sp_scratch_bytes) {
+            if (c->sp_scratch) {
+                cudaDeviceSynchronize();
+                cudaFree(c->sp_scratch);
+            }
+            c->sp_scratch = nullptr;
+            c->sp_scratch_bytes = 0;
+            if (cudaMalloc(&c->sp_scratch, need) != cudaSuccess) {
+                cudaGetLastError();
+                c->sp_scratch = nullptr;
+                c->sp_two_phase = false;
+            } else {
+                c->sp_scratch_bytes = need;
+            }
+        }
+    }
+    c->spread = t;
+    drop_graph(c);
+    return PSE_OK;
+}
+
+template <typename T> cudaError_t run_spread(pse_ctx *c, const SpreadTile &t, cudaStream_t s) {
+    Dev<T> &d = dev<T>(c);
+    const bool tp = c->sp_two_phase;
+    return launch_spread<T>(wgeom<T>(c), geom<T>(c), t, c->sp_orig, tp ? c->sp_cover : nullptr,
+                            tp ? c->sp_cnt : nullptr, tp ? (T *)c->sp_scratch : nullptr, d, s);
+}
+
+// Default: the largest tile that holds all three components, else the
+// largest holding one; spread_tile = 1, 2, 4 forces that many cells per side.
+template <typename T> pse_status choose_spread(pse_ctx *c) {
+    if (c->spread_ready) return PSE_OK;
+    CK(spread_prepare<T>(&c->spread_smem_max));
+    const int Gs[3] = {4, 2, 1};
+    const int want = c->params.spread_tile;
+    bool ok = false;
+    for (int CP : {3, 1}) {
+        for (int G : Gs)
+            if ((want == 0 || want == G) && spread_tile(c->plan, G, CP, sizeof(T), c->spread_smem_max, &c->spread)) {
+                ok = true;
+                break;
+            }
+        if (ok) break;
+    }
+    if (!ok) return PSE_ENOTSUPPORTED;
+    pse_status st = set_spread_tile<T>(c, c->spread);
+    if (st != PSE_OK) return st;
+    c->spread_ready = true;
+    return PSE_OK;
+}
+
 // Per-N buffers.
 template <typename T> pse_status ensure(pse_ctx *c, int64_t N) {
     if (N == c->N) return PSE_OK;
@@ -222,6 +358,7 @@ template <typename T> pse_status ensure(pse_ctx *c, int64_t N) {
     A(d.pc, sizeof(float) * 16 * N);
     d.pc_on = c->pc_enabled ? d.pc : nullptr;
     A(d.uwave, sizeof(V4<T>) * N);
+    A(d.udet, sizeof(V4<T>) * N);
     A(d.partials, sizeof(double) * (2 * num_sms() * 16 + 64));
     A(c->stage_pos, sizeof(T) * 3 * N);
     A(c->stage_out, sizeof(T) * 3 * N);
@@ -249,16 +386,39 @@ template <typename T> void real_setup(pse_ctx *c, int64_t N, cudaStream_t s) {
     launch_lz_init<T>(N, d.args, c->params.system, d, s);
 }
 
-template <typename T> pse_status wave_branch(pse_ctx *c, int64_t N, cudaStream_t s) {
+template <typename T> void interp(pse_ctx *c, int64_t N, cudaStream_t s) {
+    launch_interp<T>(N, wgeom<T>(c), geom<T>(c), dev<T>(c), s);
+}
+
+template <typename T> pse_status wave_branch(pse_ctx *c, int64_t N, cudaStream_t s, int mode) {
     Dev<T> &d = dev<T>(c);
-    launch_wave_noise<T>(wgeom<T>(c), d.args, c->params.system, d.spec, s);
+    const WaveGeom<T> &w = wgeom<T>(c);
+    if (mode == GM_SAMPLE && c->params.wave_noise == 0) {
+        launch_wave_noise<T>(w, d.args, c->params.system, d.spec, s);
+    } else {
+        const int64_t M3 = (int64_t)w.M * w.M * w.M;
+        if (mode == GM_SAMPLE) {
+            launch_grid_noise<T>(w, d.args, c->params.system, d.grid, s);
+        } else {
+            CK(cudaMemsetAsync(d.grid, 0, sizeof(T) * 3 * M3, s));
+            CK(run_spread<T>(c, c->spread, s));
+        }
+        CKF(cufftSetStream(c->fft_r2c, s));
+        if constexpr (sizeof(T) == 4) {
+            CKF(cufftExecR2C(c->fft_r2c, (cufftReal *)d.grid, (cufftComplex *)d.spec));
+        } else {
+            CKF(cufftExecD2Z(c->fft_r2c, (cufftDoubleReal *)d.grid, (cufftDoubleComplex *)d.spec));
+        }
+        launch_wave_apply<T>(w, d.args, c->params.system, d.spec,
+                             mode == GM_SAMPLE ? WAVE_MODE_GRIDNOISE : WAVE_MODE_DET, mode == GM_FORCES_NOISE, s);
+    }
     CKF(cufftSetStream(c->fft, s));
     if constexpr (sizeof(T) == 4) {
         CKF(cufftExecC2R(c->fft, (cufftComplex *)d.spec, (cufftReal *)d.grid));
     } else {
         CKF(cufftExecZ2D(c->fft, (cufftDoubleComplex *)d.spec, (cufftDoubleReal *)d.grid));
     }
-    launch_interp<T>(N, wgeom<T>(c), geom<T>(c), d, s);
+    interp<T>(c, N, s);
     return PSE_OK;
 }
 
@@ -267,17 +427,21 @@ template <typename T> pse_status wave_branch(pse_ctx *c, int64_t N, cudaStream_t
 // list, preconditioner blocks and q_1.  The loop body is one Lanczos step
 // (matvec -> update on `sa`, eigen-solve of the previous T on `sb`).  The
 // epilogue joins the wave branch and writes the output.
-template <typename T> pse_status capture_pre(pse_ctx *c) {
+template <typename T> pse_status capture_pre(pse_ctx *c, int mode) {
     const int64_t N = c->N;
     Dev<T> &d = dev<T>(c);
     cudaStream_t s = c->s_main;
     pre<T>(c, N, s);
     cudaEventRecord(c->ev[0], s);
     cudaStreamWaitEvent(c->s_wave, c->ev[0], 0);
-    const pse_status wst = wave_branch<T>(c, N, c->s_wave);
+    const pse_status wst = wave_branch<T>(c, N, c->s_wave, mode);
     cudaEventRecord(c->ev[1], c->s_wave);
     launch_nbr<T>(N, geom<T>(c), d, s);
-    real_setup<T>(c, N, s);
+    if (mode != GM_SAMPLE) {  // M_r F into udet (the records are overwritten by q_1 next)
+        launch_gather_vec<T>(N, d.args, d, s);
+        launch_matvec_sorted<T>(N, geom<T>(c), d, s);
+    }
+    if (mode != GM_FORCES) real_setup<T>(c, N, s);
     return wst;
 }
 
@@ -290,10 +454,12 @@ void capture_body(pse_ctx *c, cudaStream_t sa, cudaStream_t sb, cudaGraphConditi
     launch_lz_eig(d.lz, c->max_iter, c->params.fixed_iter, ltol, h, sb);
 }
 
-template <typename T> void capture_post(pse_ctx *c) {
+template <typename T> void capture_post(pse_ctx *c, int mode) {
     Dev<T> &d = dev<T>(c);
     cudaStreamWaitEvent(c->s_main, c->ev[1], 0);
-    launch_lz_final<T>(c->N, d.args, d, true, c->s_main);
+    if (mode == GM_SAMPLE) launch_lz_final<T>(c->N, d.args, d, true, c->s_main);
+    else if (mode == GM_FORCES_NOISE) launch_lz_final_forces<T>(c->N, d.args, d, c->s_main);
+    else launch_det_final<T>(c->N, d.args, d, c->s_main);
 }
 
 // Insert a WHILE node (default condition 1) at the capture point of `s`;
@@ -322,31 +488,35 @@ static cudaError_t add_while(cudaStream_t s, cudaGraphConditionalHandle *h, cuda
 // One whole sample on c->s_main (capturing): prologue, a WHILE node whose
 // body is one Lanczos step with the eigen kernel setting the condition, and
 // the epilogue.
-template <typename T> pse_status capture_sample(pse_ctx *c) {
-    const pse_status wst = capture_pre<T>(c);
+template <typename T> pse_status capture_sample(pse_ctx *c, int mode) {
+    const pse_status wst = capture_pre<T>(c, mode);
+    if (mode == GM_FORCES) {
+        capture_post<T>(c, mode);
+        return wst;
+    }
     cudaGraph_t body = nullptr;
-    cudaError_t e = add_while(c->s_main, &c->cond, &body);
+    cudaError_t e = add_while(c->s_main, &c->cond[mode], &body);
     if (e == cudaSuccess) {
         e = cudaStreamBeginCaptureToGraph(c->s_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaEventRecord(c->ev[2], c->s_body);
             cudaStreamWaitEvent(c->s_body2, c->ev[2], 0);
-            capture_body<T>(c, c->s_body, c->s_body2, c->cond);
+            capture_body<T>(c, c->s_body, c->s_body2, c->cond[mode]);
             cudaEventRecord(c->ev[3], c->s_body2);
             cudaStreamWaitEvent(c->s_body, c->ev[3], 0);
             cudaGraph_t body_out = nullptr;
             e = cudaStreamEndCapture(c->s_body, &body_out);
         }
     }
-    capture_post<T>(c);
+    capture_post<T>(c, mode);
     if (wst != PSE_OK) return wst;
     return e == cudaSuccess ? PSE_OK : PSE_ECUDA;
 }
 
-template <typename T> pse_status build_graph(pse_ctx *c) {
+template <typename T> pse_status build_graph(pse_ctx *c, int mode) {
     cudaStream_t s = c->s_main;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    const pse_status st = capture_sample<T>(c);
+    const pse_status st = capture_sample<T>(c, mode);
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
     if (st != PSE_OK || e2 != cudaSuccess) {
@@ -354,8 +524,8 @@ template <typename T> pse_status build_graph(pse_ctx *c) {
         cudaGetLastError();
         return st != PSE_OK ? st : PSE_ECUDA;
     }
-    c->graph = graph;
-    if (cudaGraphInstantiate(&c->exec, graph, 0) != cudaSuccess) {
+    c->graph[mode] = graph;
+    if (cudaGraphInstantiate(&c->exec[mode], graph, 0) != cudaSuccess) {
         cudaGetLastError();
         drop_graph(c);
         return PSE_ECUDA;
@@ -365,14 +535,22 @@ template <typename T> pse_status build_graph(pse_ctx *c) {
 
 // Same kernels, launched directly with a host-side Lanczos loop (one
 // synchronisation per iteration).  Used when use_graph = -1.
-template <typename T> pse_status run_plain(pse_ctx *c, cudaStream_t s) {
+template <typename T> pse_status run_plain(pse_ctx *c, cudaStream_t s, int mode) {
     const int64_t N = c->N;
     Dev<T> &d = dev<T>(c);
     const double ltol = c->params.lanczos_tol > 0 ? c->params.lanczos_tol : c->plan.tol;
     pre<T>(c, N, s);
-    pse_status st = wave_branch<T>(c, N, s);
+    pse_status st = wave_branch<T>(c, N, s, mode);
     if (st != PSE_OK) return st;
     launch_nbr<T>(N, geom<T>(c), d, s);
+    if (mode != GM_SAMPLE) {
+        launch_gather_vec<T>(N, d.args, d, s);
+        launch_matvec_sorted<T>(N, geom<T>(c), d, s);
+    }
+    if (mode == GM_FORCES) {
+        launch_det_final<T>(N, d.args, d, s);
+        return PSE_OK;
+    }
     real_setup<T>(c, N, s);
     for (int it = 0; it < c->max_iter + 2; ++it) {
         launch_lz_matvec<T>(N, geom<T>(c), d, s);
@@ -383,7 +561,46 @@ template <typename T> pse_status run_plain(pse_ctx *c, cudaStream_t s) {
         CK(cudaStreamSynchronize(s));
         if (!cont) break;
     }
-    launch_lz_final<T>(N, d.args, d, true, s);
+    if (mode == GM_SAMPLE) launch_lz_final<T>(N, d.args, d, true, s);
+    else launch_lz_final_forces<T>(N, d.args, d, s);
+    return PSE_OK;
+}
+
+// Time each matvec launch shape (3 launches after one warm-up) on the
+// current call's neighbour list and keep the fastest.  Needs d.args set.
+template <typename T> pse_status tune_matvec(pse_ctx *c, cudaStream_t s) {
+    const int64_t N = c->N;
+    Dev<T> &d = dev<T>(c);
+    pre<T>(c, N, s);
+    launch_nbr<T>(N, geom<T>(c), d, s);
+    real_setup<T>(c, N, s);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int keep = 0;
+    Geom<T> g = geom<T>(c);
+    for (int v = 0; v < PSE_MV_VARIANTS; ++v) {
+        g.mv = v;
+        for (int rep = 0; rep < 4; ++rep) {
+            if (rep == 1) cudaEventRecord(e0, s);
+            launch_lz_matvec<T>(N, g, d, s);
+        }
+        cudaEventRecord(e1, s);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess) continue;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            keep = v;
+        }
+    }
+    geom<T>(c).mv = keep;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->mv_tuned = true;
+    drop_graph(c);
+    CK(cudaGetLastError());
     return PSE_OK;
 }
 
@@ -395,9 +612,10 @@ pse_status sample_impl(pse_ctx *c, int64_t N, const T *pos, uint64_t seed, uint6
     DeviceGuard guard(c->device);
     pse_status st = ensure<T>(c, N);
     if (st != PSE_OK) return st;
+    if (c->params.wave_noise == 1 && (st = ensure_r2c<T>(c)) != PSE_OK) return st;
     const bool use_graph = c->params.use_graph >= 0;
-    if (use_graph && !c->exec) {
-        st = build_graph<T>(c);
+    if (use_graph && !c->exec[GM_SAMPLE]) {
+        st = build_graph<T>(c, GM_SAMPLE);
         if (st != PSE_OK) return st;
     }
     SampleArgs<T> a{};
@@ -408,11 +626,95 @@ pse_status sample_impl(pse_ctx *c, int64_t N, const T *pos, uint64_t seed, uint6
     a.vin = nullptr;
     a.seed = seed;
     a.sample = sample;
+    a.c_det = 0.0;
+    a.c_noise = 1.0;
     CK(cudaMemcpyAsync(dev<T>(c).args, &a, sizeof(a), cudaMemcpyHostToDevice, s));
+    if ((c->params.autotune & 4) && c->params.matvec_shape == 0 && !c->mv_tuned) {
+        if ((st = tune_matvec<T>(c, s)) != PSE_OK) return st;
+        if (use_graph && (st = build_graph<T>(c, GM_SAMPLE)) != PSE_OK) return st;
+    }
     if (use_graph) {
-        CK(cudaGraphLaunch(c->exec, s));
+        CK(cudaGraphLaunch(c->exec[GM_SAMPLE], s));
     } else {
-        st = run_plain<T>(c, s);
+        st = run_plain<T>(c, s, GM_SAMPLE);
+        if (st != PSE_OK) return st;
+    }
+    c->last_stream = s;
+    CK(cudaGetLastError());
+    return PSE_OK;
+}
+
+// Time every tile shape that fits (3 spreads each after one warm-up) on the
+// cell list of the current call and keep the fastest.
+template <typename T> pse_status tune_spread(pse_ctx *c, cudaStream_t s) {
+    Dev<T> &d = dev<T>(c);
+    const int64_t M3 = (int64_t)c->plan.M * c->plan.M * c->plan.M;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    SpreadTile keep = c->spread;
+    for (int CP : {3, 1})
+        for (int G : {4, 2, 1}) {
+            SpreadTile t;
+            if (!spread_tile(c->plan, G, CP, sizeof(T), c->spread_smem_max, &t)) continue;
+            if (set_spread_tile<T>(c, t) != PSE_OK) continue;
+            float ms = 0.f;
+            bool ok = true;
+            for (int rep = 0; rep < 4 && ok; ++rep) {
+                if (rep == 1) cudaEventRecord(e0, s);
+                ok = cudaMemsetAsync(d.grid, 0, sizeof(T) * 3 * M3, s) == cudaSuccess &&
+                     run_spread<T>(c, t, s) == cudaSuccess;
+            }
+            cudaEventRecord(e1, s);
+            if (!ok || cudaEventSynchronize(e1) != cudaSuccess) continue;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                keep = t;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    c->spread_tuned = true;
+    return set_spread_tile<T>(c, keep);
+}
+
+template <typename T>
+pse_status forces_impl(pse_ctx *c, int64_t N, const T *pos, const T *force, uint64_t seed, uint64_t sample,
+                       double c_det, double c_noise, T *out, cudaStream_t s) {
+    if (!pos || !force || !out || N < 1) return PSE_EINVAL;
+    if (!(c_det == c_det) || !(c_noise == c_noise)) return PSE_EINVAL;
+    if (c_noise != 0.0 && c->params.wave_noise == 1) return PSE_ENOTSUPPORTED;
+    DeviceGuard guard(c->device);
+    pse_status st = ensure<T>(c, N);
+    if (st != PSE_OK) return st;
+    if ((st = ensure_r2c<T>(c)) != PSE_OK) return st;
+    if ((st = choose_spread<T>(c)) != PSE_OK) return st;
+    const int mode = c_noise != 0.0 ? GM_FORCES_NOISE : GM_FORCES;
+    SampleArgs<T> a{};
+    a.pos = pos;
+    a.out = out;
+    a.vin = force;
+    a.seed = seed;
+    a.sample = sample;
+    a.c_det = c_det;
+    a.c_noise = c_noise;
+    CK(cudaMemcpyAsync(dev<T>(c).args, &a, sizeof(a), cudaMemcpyHostToDevice, s));
+    if ((c->params.autotune & 2) && c->params.spread_tile == 0 && !c->spread_tuned) {
+        pre<T>(c, N, s);
+        if ((st = tune_spread<T>(c, s)) != PSE_OK) return st;
+    }
+    const bool use_graph = c->params.use_graph >= 0;
+    if (use_graph && !c->exec[mode]) {
+        st = build_graph<T>(c, mode);
+        if (st != PSE_OK) return st;
+    }
+    if (use_graph) {
+        CK(cudaGraphLaunch(c->exec[mode], s));
+    } else {
+        st = run_plain<T>(c, s, mode);
         if (st != PSE_OK) return st;
     }
     c->last_stream = s;
@@ -500,6 +802,12 @@ pse_status create_impl(pse_ctx **out, double L, double a, const pse_params *p) {
     c->max_iter = p->max_iter > 0 ? p->max_iter : PSE_MAXIT;
     if (c->params.fixed_iter > c->max_iter) c->max_iter = c->params.fixed_iter;
     if (cudaGetDevice(&c->device) != cudaSuccess) { cudaGetLastError(); delete c; return PSE_ECUDA; }
+    if (p->wave_noise < 0 || p->wave_noise > 1 ||
+        !(p->spread_tile == 0 || p->spread_tile == 1 || p->spread_tile == 2 || p->spread_tile == 4) ||
+        p->matvec_shape < 0 || p->matvec_shape > PSE_MV_VARIANTS) {
+        delete c;
+        return PSE_EINVAL;
+    }
     st = (p->precision == PSE_FP64) ? init_ctx<double>(c) : init_ctx<float>(c);
     if (st != PSE_OK) { pse_destroy(c); return st; }
     *out = c;
@@ -529,6 +837,8 @@ void pse_destroy(pse_ctx *c) {
     cudaDeviceSynchronize();
     drop_graph(c);
     if (c->fft_made) cufftDestroy(c->fft);
+    if (c->r2c_made) cufftDestroy(c->fft_r2c);
+    if (c->sp_scratch) cudaFree(c->sp_scratch);
     free_list(c->per_n);
     free_list(c->per_ctx);
     cudaStream_t ss[4] = {c->s_main, c->s_wave, c->s_body, c->s_body2};
@@ -560,6 +870,25 @@ pse_status pse_sample_f64(pse_ctx *c, int64_t N, const double *d_pos, uint64_t s
                           double *d_out, double *d_real, double *d_wave, void *stream) {
     if (!c || c->plan.precision != PSE_FP64) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
     return sample_impl<double>(c, N, d_pos, seed, sample_index, d_out, d_real, d_wave, (cudaStream_t)stream);
+}
+
+pse_status pse_sample_with_forces(pse_ctx *c, int64_t N, const float *d_pos, const float *d_force, uint64_t seed,
+                                  uint64_t sample_index, double c_det, double c_noise, float *d_out, void *stream) {
+    if (!c || c->plan.precision != PSE_FP32) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
+    return forces_impl<float>(c, N, d_pos, d_force, seed, sample_index, c_det, c_noise, d_out, (cudaStream_t)stream);
+}
+
+pse_status pse_sample_with_forces_f64(pse_ctx *c, int64_t N, const double *d_pos, const double *d_force,
+                                      uint64_t seed, uint64_t sample_index, double c_det, double c_noise,
+                                      double *d_out, void *stream) {
+    if (!c || c->plan.precision != PSE_FP64) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
+    return forces_impl<double>(c, N, d_pos, d_force, seed, sample_index, c_det, c_noise, d_out,
+                               (cudaStream_t)stream);
+}
+
+pse_status pse_mobility_apply(pse_ctx *c, int64_t N, const float *d_pos, const float *d_force, float *d_out,
+                              void *stream) {
+    return pse_sample_with_forces(c, N, d_pos, d_force, 0, 0, 1.0, 0.0, d_out, stream);
 }
 
 pse_status pse_sample_host(pse_ctx *c, int64_t N, const float *h_pos, uint64_t seed, uint64_t sample_index,
@@ -616,7 +945,9 @@ pse_status pse_profile_stages(pse_ctx *c, int64_t N, const float *d_pos, uint64_
     a.out = d_out;
     a.seed = seed;
     a.sample = sample_index;
+    a.c_noise = 1.0;
     CK(cudaMemcpyAsync(d.args, &a, sizeof(a), cudaMemcpyHostToDevice, s));
+    if (c->params.wave_noise == 1 && (st = ensure_r2c<float>(c)) != PSE_OK) return st;
     const double ltol = c->params.lanczos_tol > 0 ? c->params.lanczos_tol : c->plan.tol;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -643,12 +974,21 @@ pse_status pse_profile_stages(pse_ctx *c, int64_t N, const float *d_pos, uint64_
         cudaMemsetAsync(&d.lz->overflow, 0, sizeof(int), s);
         cudaMemsetAsync(&d.lz->n_pairs, 0, sizeof(unsigned long long), s);
         return PSE_OK; });
-    if (r == PSE_OK) r = timed(PSE_STAGE_WAVE_NOISE, 1, [&] { launch_wave_noise<float>(c->wf, d.args, c->params.system, d.spec, s); return PSE_OK; });
+    if (r == PSE_OK) r = timed(PSE_STAGE_WAVE_NOISE, c->params.wave_noise ? 2 : 1, [&] {
+        if (c->params.wave_noise == 0) {
+            launch_wave_noise<float>(c->wf, d.args, c->params.system, d.spec, s);
+            return PSE_OK;
+        }
+        launch_grid_noise<float>(c->wf, d.args, c->params.system, d.grid, s);
+        CKF(cufftSetStream(c->fft_r2c, s));
+        CKF(cufftExecR2C(c->fft_r2c, (cufftReal *)d.grid, (cufftComplex *)d.spec));
+        launch_wave_apply<float>(c->wf, d.args, c->params.system, d.spec, WAVE_MODE_GRIDNOISE, 0, s);
+        return PSE_OK; });
     if (r == PSE_OK) r = timed(PSE_STAGE_FFT, 0, [&] {
         CKF(cufftSetStream(c->fft, s));
         CKF(cufftExecC2R(c->fft, (cufftComplex *)d.spec, (cufftReal *)d.grid));
         return PSE_OK; });
-    if (r == PSE_OK) r = timed(PSE_STAGE_INTERP, 1, [&] { launch_interp<float>(N, c->wf, c->gf, d, s); return PSE_OK; });
+    if (r == PSE_OK) r = timed(PSE_STAGE_INTERP, 1, [&] { interp<float>(c, N, s); return PSE_OK; });
     if (r == PSE_OK) r = timed(PSE_STAGE_NEIGHBOURS, 1, [&] {
         launch_nbr<float>(N, c->gf, d, s);
         return PSE_OK; });
@@ -757,6 +1097,7 @@ pse_status pse_get_stats(pse_ctx *c, pse_stats *out) {
     out->lanczos_rel_change = lz.rel;
     out->n_pairs = np;
     out->overflow = lz.overflow;
+    out->matvec_shape = (c->plan.precision == PSE_FP64 ? c->gd.mv : c->gf.mv) + 1;
     if (lz.overflow) return PSE_ENOMEM;
     if (!lz.converged && lz.J > 0) return PSE_ENOTCONVERGED;
     return PSE_OK;
@@ -878,6 +1219,7 @@ extern "C" pse_status pse_batch_sample(pse_batch *b, const int64_t *offsets, con
         if (N != b->built_N[k]) rebuild = true;
         pse_status st = ensure<float>(b->sys[k], N);
         if (st != PSE_OK) return st;
+        if (b->sys[k]->params.wave_noise == 1 && (st = ensure_r2c<float>(b->sys[k])) != PSE_OK) return st;
         b->sys[k]->df.args = b->d_args + k;  // kept across re-allocation
     }
     if (rebuild) {
@@ -890,7 +1232,7 @@ extern "C" pse_status pse_batch_sample(pse_batch *b, const int64_t *offsets, con
         for (int k = 0; k < S; ++k) {
             pse_ctx *c = b->sys[k];
             cudaStreamWaitEvent(c->s_main, b->ev_fork, 0);
-            const pse_status sk = capture_pre<float>(c);
+            const pse_status sk = capture_pre<float>(c, GM_SAMPLE);
             if (sk != PSE_OK && st == PSE_OK) st = sk;
             cudaEventRecord(b->ev_pre[k], c->s_main);
             cudaStreamWaitEvent(b->root, b->ev_pre[k], 0);
@@ -920,7 +1262,7 @@ extern "C" pse_status pse_batch_sample(pse_batch *b, const int64_t *offsets, con
         for (int k = 0; k < S; ++k) {
             pse_ctx *c = b->sys[k];
             cudaStreamWaitEvent(c->s_main, b->ev_after, 0);
-            capture_post<float>(c);
+            capture_post<float>(c, GM_SAMPLE);
             cudaEventRecord(b->ev_join[k], c->s_main);
             cudaStreamWaitEvent(b->root, b->ev_join[k], 0);
         }
@@ -948,6 +1290,8 @@ extern "C" pse_status pse_batch_sample(pse_batch *b, const int64_t *offsets, con
         a.vin = nullptr;
         a.seed = seed;
         a.sample = sample_index;
+        a.c_det = 0.0;
+        a.c_noise = 1.0;
     }
     CK(cudaMemcpyAsync(b->d_args, b->h_args.data(), sizeof(SampleArgs<float>) * S, cudaMemcpyHostToDevice, s));
     CK(cudaGraphLaunch(b->exec, s));

@@ -62,7 +62,9 @@ template <typename T> struct Geom {
     T xi;         // splitting parameter
     int nc;       // cells per side
     int nb;       // bricks per side (4x4x4 cells each)
+    int mv;       // matvec launch shape (0: 4 threads x 4 gathers per particle, 1: 8 x 2, 2: 16 x 1, 3: 4 x 2)
 };
+#define PSE_MV_VARIANTS 4
 
 // Wave-space parameters of one system.
 template <typename T> struct WaveGeom {
@@ -75,6 +77,7 @@ template <typename T> struct WaveGeom {
     T gl_hi, gl_lo;      // M / L split in two (compensated product x * M / L)
     T ch2;               // 2 xi^2 h^2 / eta: Gaussian exponent per squared grid unit
     T norm;              // (2 xi^2 / (pi eta))^{3/2} h^3
+    T inv_M15;           // M^{-3/2}: white grid noise -> dW2 normalisation
     int interp_lanes;    // lanes per particle in the interpolation (8, 16, 32; 0 = pick)
 };
 
@@ -85,9 +88,17 @@ template <typename T> struct SampleArgs {
     T *out;         // 3N or null
     T *real;        // 3N or null
     T *wave;        // 3N or null
-    const T *vin;   // 3N caller vector for the matvec path, or null
+    const T *vin;   // 3N caller vector (matvec input, or forces), or null
     uint64_t seed;
     uint64_t sample;
+    double c_det;   // weight of M F (forces path)
+    double c_noise; // weight of M^{1/2} z (1 for a plain sample)
+};
+
+// Tiling of the spreading kernel: tiles of G^3 cells, each spread into a
+// padded E^3 node block in shared memory, CP of the 3 components per pass.
+struct SpreadTile {
+    int G, E, CP, ntx;  // ntx = tiles per side
 };
 
 // Device-side state of the Lanczos iteration (one system).
@@ -287,6 +298,7 @@ template <typename T> struct Dev {
     float *pc_theta;     // network parameters (PSE_PRECOND_NPARAM)
     V4<T> *u;            // matvec output
     V4<T> *uwave;        // wave part at sorted particles
+    V4<T> *udet;         // M_r F at sorted particles (forces path)
     double *partials;    // per-block partial sums
     LzState *lz;
     V4<T> *table;        // PSE_TABLE_N: (F, G - F, dF, d(G-F)) / (6 pi a)
@@ -332,6 +344,23 @@ template <typename T> void launch_matvec_caller(int64_t N, const SampleArgs<T> *
 template <typename T> void launch_wave_noise(WaveGeom<T> w, const SampleArgs<T> *args, int system, void *spec,
                                              cudaStream_t s);
 template <typename T> void launch_interp(int64_t N, WaveGeom<T> w, Geom<T> g, const Dev<T> &d, cudaStream_t s);
+enum { WAVE_MODE_DET = 0, WAVE_MODE_GRIDNOISE = 1 };
+template <typename T>
+void launch_wave_apply(WaveGeom<T> w, const SampleArgs<T> *args, int system, void *spec, int mode, int with_noise,
+                       cudaStream_t s);
+template <typename T>
+void launch_grid_noise(WaveGeom<T> w, const SampleArgs<T> *args, int system, T *grid, cudaStream_t s);
+size_t spread_smem_bytes(SpreadTile st, int P, size_t elem);
+#define PSE_COVER 8  // tile blocks that may cover one grid node along one axis
+template <typename T>
+cudaError_t launch_spread(WaveGeom<T> w, Geom<T> g, SpreadTile st, const int *orig, const int2 *cover,
+                          const int *cover_cnt, T *scratch, const Dev<T> &d, cudaStream_t s);
+template <typename T> cudaError_t spread_prepare(size_t *max_dynamic);
+template <typename T> void launch_matvec_sorted(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s);
+template <typename T> void launch_gather_vec(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, cudaStream_t s);
+template <typename T> void launch_det_final(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, cudaStream_t s);
+template <typename T>
+void launch_lz_final_forces(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, cudaStream_t s);
 
 // learned preconditioner (float contexts)
 void launch_pc_infer(int64_t N, Geom<float> g, const Dev<float> &d, const float *theta, float s0, float *pc,

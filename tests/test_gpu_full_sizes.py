@@ -1,0 +1,115 @@
+"""The workloads at their full sizes, through the C ABI, in the FP32 launch
+configuration the benchmark times (one CUDA graph per sample, tuned kernels):
+
+  * N = 1e5 hard spheres at phi = 0.2 and 0.4, tol 1e-3: 100 consecutive
+    samples converge; one sample against the FP64 oracle's full sample at the
+    same Lanczos J (relative error reported and bounded by 1e-4);
+  * N = 2.5e5 fractal gels at phi = 0.05 and 0.1: near-field rows at sampled
+    particles against the oracle, convergence;
+  * N = 4e6 hard spheres at phi = 0.3, tol 1e-3 and 1e-5: near-field rows at
+    sampled particles against the oracle (row by row), the wave part at
+    sampled particles against the oracle's gridded sample (tol 1e-3), and
+    convergence of the Lanczos test.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+SEED = 13579
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.fail("GPU test run without a CUDA device")
+    from paper_1611_09322_gb300 import build
+    build.build_all()
+    return t
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _maxrel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def _rows_check(torch, s, pos, plan, n_rows=200, seed=1):
+    """pse_real_matvec at full size vs the oracle's row-by-row M_r v."""
+    from oracle import pse
+    N = pos.shape[0]
+    v = np.random.default_rng(seed).standard_normal((N, 3)).astype(np.float32)
+    got = s.real_matvec(torch.from_numpy(pos).cuda(), torch.from_numpy(v).cuda()).cpu().numpy()
+    rows = np.random.default_rng(seed + 1).choice(N, n_rows, replace=False)
+    ref = pse.real_rows(pos.astype(np.float64), plan, rows, v.astype(np.float64))
+    return _maxrel(got[rows], ref)
+
+
+@pytest.mark.parametrize("phi", [0.2, 0.4])
+def test_hard_spheres_1e5(torch, phi):
+    from oracle import ewald, pse
+    from paper_1611_09322_gb300 import Sampler, workloads
+    N = 100_000
+    pos, L, _ = workloads.hard_spheres(N, phi, 2)
+    s = Sampler(L, 1.0, xi=0.5, tol=1e-3, autotune=5)
+    plan = ewald.plan(L, 1.0, 0.5, 1e-3, M=s.plan["M"])  # the grid the FFT-size tuner kept
+    d = torch.from_numpy(pos).cuda()
+    out = torch.empty_like(d)
+    for i in range(100):
+        s.sample(d, SEED, i, out=out)
+        if i % 25 == 0:
+            st = s.stats()
+            assert st["converged"] == 1 and st["overflow"] == 0
+    assert torch.isfinite(out).all()
+    u, ur, uw = s.sample(d, SEED, 7, parts=True)
+    J = s.stats()["lanczos_iters"]
+    p64 = pos.astype(np.float64)
+    ref_r, j, _ = pse.real_sample(p64, plan, SEED, 7, n_iter=J)
+    ref_w = pse.wave_sample_grid(p64, plan, SEED, 7)
+    err = _rel(u.cpu().numpy(), ref_r + ref_w)
+    print(f"N=1e5 phi={phi}: J={J}, relative error of the FP32 sample vs the FP64 oracle {err:.2e}")
+    assert err < 1e-4 and _maxrel(ur.cpu().numpy(), ref_r) < 1e-4 and _maxrel(uw.cpu().numpy(), ref_w) < 1e-4
+    assert _rows_check(torch, s, pos, plan) < 1e-5
+    s.close()
+
+
+@pytest.mark.parametrize("phi", [0.05, 0.1])
+def test_gels_2p5e5(torch, phi):
+    from oracle import ewald
+    from paper_1611_09322_gb300 import Sampler, workloads
+    N = 250_000
+    pos, L, _ = workloads.gel(N, phi, 3)
+    s = Sampler(L, 1.0, xi=0.5, tol=1e-3, autotune=5)
+    plan = ewald.plan(L, 1.0, 0.5, 1e-3, M=s.plan["M"])
+    d = torch.from_numpy(pos).cuda()
+    u = s.sample(d, SEED, 1)
+    st = s.stats()
+    assert st["converged"] == 1 and st["overflow"] == 0 and torch.isfinite(u).all()
+    assert _rows_check(torch, s, pos, plan) < 1e-5
+    s.close()
+
+
+@pytest.mark.parametrize("tol", [1e-3, 1e-5])
+def test_hard_spheres_4e6(torch, tol):
+    from oracle import ewald, pse
+    from paper_1611_09322_gb300 import Sampler, workloads
+    N = 4_000_000
+    pos, L, _ = workloads.hard_spheres(N, 0.3, 4)
+    s = Sampler(L, 1.0, xi=0.5, tol=tol, autotune=5)
+    plan = ewald.plan(L, 1.0, 0.5, tol, M=s.plan["M"])
+    assert s.plan["P"] == plan.P and s.plan["M"] >= ewald.plan(L, 1.0, 0.5, tol).M
+    d = torch.from_numpy(pos).cuda()
+    u, ur, uw = s.sample(d, SEED, 2, parts=True)
+    st = s.stats()
+    assert st["converged"] == 1 and st["overflow"] == 0 and torch.isfinite(u).all()
+    assert st["lanczos_rel_change"] < tol
+    assert _rows_check(torch, s, pos, plan, n_rows=100) < 1e-5
+    if tol == 1e-3:
+        rows = np.random.default_rng(5).choice(N, 300, replace=False)
+        v, _ = pse.wave_grid_velocity(plan, SEED, 2)
+        ref = pse.interpolate(v, pos[rows].astype(np.float64), plan)
+        assert _maxrel(uw.cpu().numpy()[rows], ref) < 1e-4
+    s.close()

@@ -74,6 +74,20 @@ def test_wave_part(torch, N, phi, xi, tol):
     s.close()
 
 
+@pytest.mark.parametrize("N,phi", [(3001, 0.2), (6000, 0.4), (64, 0.1)])
+def test_interpolation_dense_and_tiny(torch, N, phi):
+    """The wave sample for a dense packing and a box of a few grid nodes."""
+    from oracle import ewald, pse
+    pos, L, _ = _hs(N, phi, 16)
+    plan = ewald.plan(L, 1.0, 0.5, 1e-3)
+    s = _sampler(L, xi=0.5, tol=1e-3, fixed_iter=2)
+    _, _, w = s.sample(torch.from_numpy(pos).cuda(), SEED, 6, parts=True)
+    got = w.cpu().numpy()
+    ref = pse.wave_sample_grid(pos.astype(np.float64), plan, SEED, 6)
+    assert _rel(got, ref) < 1e-4 and _maxrel(got, ref) < 1e-4, (_rel(got, ref), _maxrel(got, ref))
+    s.close()
+
+
 @pytest.mark.parametrize("N,phi,J", [(1000, 0.1, 6), (1000, 0.1, 1), (1500, 0.3, 12), (130, 0.2, 30)])
 def test_real_part_fixed_iterations(torch, N, phi, J):
     """Real sample after exactly J Lanczos steps = the oracle's J-step Lanczos."""
@@ -86,6 +100,26 @@ def test_real_part_fixed_iterations(torch, N, phi, J):
     st = s.stats()
     assert st["lanczos_iters"] == J
     ref, j, _ = pse.real_sample(pos.astype(np.float64), plan, SEED, 9, n_iter=J)
+    assert _rel(got, ref) < 1e-4 and _maxrel(got, ref) < 1e-4, (_rel(got, ref), _maxrel(got, ref))
+    s.close()
+
+
+@pytest.mark.parametrize("shape", [1, 2, 3, 4, 0])
+def test_matvec_launch_shapes(torch, shape):
+    """Every near-field matvec launch shape (threads x gathers per particle),
+    and the timed choice (shape 0 with autotune bit 2), gives the oracle's
+    J-step real part; dense packing so that some lists exceed one gather round."""
+    from oracle import ewald, pse
+    N, J = 1500, 6
+    pos, L, _ = _hs(N, 0.35, 15)
+    plan = ewald.plan(L, 1.0, 0.5, 1e-3)
+    s = _sampler(L, xi=0.5, tol=1e-3, fixed_iter=J, matvec_shape=shape, autotune=4 if shape == 0 else 0)
+    _, r, _ = s.sample(torch.from_numpy(pos).cuda(), SEED, 9, parts=True)
+    got = r.cpu().numpy()
+    st = s.stats()
+    assert st["lanczos_iters"] == J
+    assert st["matvec_shape"] == shape if shape else 1 <= st["matvec_shape"] <= 4
+    ref, _, _ = pse.real_sample(pos.astype(np.float64), plan, SEED, 9, n_iter=J)
     assert _rel(got, ref) < 1e-4 and _maxrel(got, ref) < 1e-4, (_rel(got, ref), _maxrel(got, ref))
     s.close()
 

@@ -130,3 +130,16 @@ def test_sample_covariance_is_the_mobility():
     assert abs(white.mean() - 1) < 4 * math.sqrt(2 / (3 * N * n))
     ratio = proj.var(axis=0) / qMq
     assert np.all(np.abs(ratio - 1) < 4 * math.sqrt(2 / n))
+
+
+def test_real_rows_match_the_dense_real_mobility():
+    """Row-at-a-time M_r v (for sampled particles of large systems) = rows of the
+    dense eq. Mreal matrix (all images)."""
+    pos, L = _hs(200, 0.3, 8)
+    plan = ewald.plan(L, 1.0, 0.5, 1e-3)
+    Mr = ewald.mobility_real_dense(pos, L, 1.0, 0.5, plan.r_cut)
+    v = np.random.default_rng(3).standard_normal((200, 3))
+    rows = np.array([0, 7, 50, 199])
+    got = pse.real_rows(pos, plan, rows, v)
+    ref = (Mr @ v.ravel()).reshape(200, 3)[rows]
+    assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
