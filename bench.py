@@ -192,9 +192,9 @@ def timed_steps(run, steps, flush, stream):
 
 def launches_per_sample(J, learned=False):
     # bin + 3 scan + scatter + cell sort, noise + interpolation, neighbour
-    # list, (network), q_1, 3 kernels per loop body (J + 1 bodies), final;
+    # list, (network), q_1, 3 kernels per loop body (J bodies), final;
     # cuFFT's own kernels are not counted
-    return 11 + (1 if learned else 0) + 3 * (J + 1)
+    return 11 + (1 if learned else 0) + 3 * J
 
 
 def variants_learned_batched(dev, flush, stream, steps):

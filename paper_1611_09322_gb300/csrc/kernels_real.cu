@@ -182,23 +182,24 @@ __device__ __forceinline__ void mr_row_part(int64_t N, int64_t s, int lane_g, bo
     }
 }
 
+// Body of one Lanczos matvec over the nblk blocks of one system (bidx = this
+// block's index among them).
 template <typename T, int TPP, int ILP>
-__global__ void __launch_bounds__(128) k_lz_matvec(int64_t N, int K, Geom<T> g, const Rec<T> *__restrict__ rec,
-                                                   const int *__restrict__ count, const int *__restrict__ nbr,
-                                                   const V4<T> *__restrict__ table, V4<T> *u, double *partials,
-                                                   LzState *lz, const float *__restrict__ pc,
-                                                   const V4<T> *__restrict__ basis) {
-    __shared__ double sh[32];
+__device__ __forceinline__ void lz_matvec_body(int64_t N, int K, const Geom<T> &g, const Rec<T> *__restrict__ rec,
+                                               const int *__restrict__ count, const int *__restrict__ nbr,
+                                               const V4<T> *__restrict__ table, V4<T> *u, double *partials,
+                                               LzState *lz, const float *__restrict__ pc,
+                                               const V4<T> *__restrict__ basis, int bidx, int nblk, double *sh) {
     const int j = lz->iter;
-    if (j > PSE_MAXIT || !lz->active) return;  // uniform across the grid
+    if (j > PSE_MAXIT || !lz->active) return;  // uniform across the system's blocks
     typename Part<T>::type part = 0;
     const int lane_g = threadIdx.x % TPP;
     const int64_t per_block = blockDim.x / TPP;
     // contiguous chunk of particles per block (spatial locality across
     // iterations); whole groups stride together so group shuffles converge
-    const int64_t chunk = ((N + gridDim.x - 1) / gridDim.x + per_block - 1) / per_block * per_block;
-    const int64_t end = (blockIdx.x + 1) * chunk < N ? (blockIdx.x + 1) * chunk : N;
-    for (int64_t base = blockIdx.x * chunk; base < end; base += per_block) {
+    const int64_t chunk = ((N + nblk - 1) / nblk + per_block - 1) / per_block * per_block;
+    const int64_t end = (bidx + 1) * chunk < N ? (bidx + 1) * chunk : N;
+    for (int64_t base = bidx * chunk; base < end; base += per_block) {
         const int64_t s = base + threadIdx.x / TPP;
         const bool active = s < end;
         V4<T> li, qi;
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(128) k_lz_matvec(int64_t N, int K, Geom<T> g, 
     }
     const double bsum = block_total<T>(part, sh);
     double total;
-    if (grid_sum_last(bsum, partials, &lz->counter_mv, sh, &total) && threadIdx.x == 0) {
+    if (grid_sum_last(bsum, partials, &lz->counter_mv, sh, &total, bidx, nblk) && threadIdx.x == 0) {
         const double b1 = lz->beta[j - 1];
         const bool ok = b1 > 0.0;  // beta_{j-1} = 0: invariant subspace, the eigen kernel stops the loop
         const double alpha = ok ? total / (b1 * b1) : 0.0;
@@ -235,10 +236,29 @@ __global__ void __launch_bounds__(128) k_lz_matvec(int64_t N, int K, Geom<T> g, 
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_lz_update(int64_t N, V4<T> *basis, Rec<T> *rec, const V4<T> *u,
-                                                   double *partials, LzState *lz, const float *__restrict__ pc) {
+template <typename T, int TPP, int ILP>
+__global__ void __launch_bounds__(128) k_lz_matvec(int64_t N, int K, Geom<T> g, const Rec<T> *__restrict__ rec,
+                                                   const int *__restrict__ count, const int *__restrict__ nbr,
+                                                   const V4<T> *__restrict__ table, V4<T> *u, double *partials,
+                                                   LzState *lz, const float *__restrict__ pc,
+                                                   const V4<T> *__restrict__ basis) {
     __shared__ double sh[32];
+    lz_matvec_body<T, TPP, ILP>(N, K, g, rec, count, nbr, table, u, partials, lz, pc, basis, blockIdx.x, gridDim.x,
+                                sh);
+}
+
+// Fused over the systems of a batch: block b works for system blk2sys[b].
+__global__ void __launch_bounds__(128) k_lz_matvec_batch(const LzSys *__restrict__ sys, const int *__restrict__ blk2sys) {
+    __shared__ double sh[32];
+    const LzSys &S = sys[blk2sys[blockIdx.x]];
+    lz_matvec_body<float, PSE_BATCH_MV_TPP, 4>(S.N, S.K, S.g, S.rec, S.count, S.nbr, S.table, S.u, S.part_mv, S.lz,
+                                               S.pc, S.basis, blockIdx.x - S.blk_mv, S.nblk_mv, sh);
+}
+
+template <typename T>
+__device__ __forceinline__ void lz_update_body(int64_t N, V4<T> *basis, Rec<T> *rec, const V4<T> *u, double *partials,
+                                               LzState *lz, const float *__restrict__ pc, int bidx, int nblk,
+                                               double *sh) {
     const int j = lz->iter;
     if (j > PSE_MAXIT || !lz->active) return;
     // coefficients in the working precision; the FP64 path recomputes them exactly
@@ -256,7 +276,7 @@ __global__ void __launch_bounds__(256) k_lz_update(int64_t N, V4<T> *basis, Rec<
     const V4<T> *qp = basis + (int64_t)(j - 2) * N;
     V4<T> *qn = basis + (int64_t)j * N;
     typename Part<T>::type part = 0;
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t s = bidx * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)nblk * blockDim.x) {
         const V4<T> us = u[s];
         const V4<T> a = qj[s];
         V4<T> w;
@@ -287,10 +307,23 @@ __global__ void __launch_bounds__(256) k_lz_update(int64_t N, V4<T> *basis, Rec<
     }
     const double bsum = block_total<T>(part, sh);
     double total;
-    if (grid_sum_last(bsum, partials, &lz->counter_up, sh, &total) && threadIdx.x == 0) {
+    if (grid_sum_last(bsum, partials, &lz->counter_up, sh, &total, bidx, nblk) && threadIdx.x == 0) {
         lz->beta[j] = sqrt(total);
         lz->iter = j + 1;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_lz_update(int64_t N, V4<T> *basis, Rec<T> *rec, const V4<T> *u,
+                                                   double *partials, LzState *lz, const float *__restrict__ pc) {
+    __shared__ double sh[32];
+    lz_update_body<T>(N, basis, rec, u, partials, lz, pc, blockIdx.x, gridDim.x, sh);
+}
+
+__global__ void __launch_bounds__(256) k_lz_update_batch(const LzSys *__restrict__ sys, const int *__restrict__ blk2sys) {
+    __shared__ double sh[32];
+    const LzSys &S = sys[blk2sys[blockIdx.x]];
+    lz_update_body<float>(S.N, S.basis, S.rec, S.u, S.part_up, S.lz, S.pc, blockIdx.x - S.blk_up, S.nblk_up, sh);
 }
 
 // ------------------------------------------------------------------ FP64 tridiagonal eigen-solve
@@ -299,19 +332,13 @@ __global__ void __launch_bounds__(256) k_lz_update(int64_t N, V4<T> *basis, Rec<
 // Loan, Sec. 8.3); every lane runs the scalar recurrences redundantly and
 // applies each plane rotation to its own rows of the eigenvector matrix.
 // Then y = Q diag(sqrt(lambda)) Q^T e_1.
-__global__ void __launch_bounds__(32) k_lz_eig(LzState *lz, int max_iter, int fixed_iter, double tol,
-                                               cudaGraphConditionalHandle handle) {
+__device__ __forceinline__ void lz_eig_body(LzState *lz, int max_iter, int fixed_iter, double tol,
+                                            cudaGraphConditionalHandle handle) {
     __shared__ double Q[PSE_MAXIT][PSE_MAXIT + 1];
     __shared__ double d[PSE_MAXIT + 1], e[PSE_MAXIT + 1], y[PSE_MAXIT + 1];
     const int lane = threadIdx.x;
     if (!lz->active) return;  // this system has stopped (batched loop)
-    const int k = lz->jeig;
-    __syncwarp();
-    if (lane == 0) lz->jeig = k + 1;
-    if (k == 0) {
-        if (lane == 0 && handle) cudaGraphSetConditional(handle, 1u);
-        return;
-    }
+    const int k = lz->iter - 1;  // T_k is complete: alpha_k from the matvec, beta_k from the update
     for (int i = lane; i < k; i += 32) {
         d[i] = lz->alpha[i + 1];
         e[i] = (i + 1 < k) ? lz->beta[i + 1] : 0.0;
@@ -411,6 +438,17 @@ __global__ void __launch_bounds__(32) k_lz_eig(LzState *lz, int max_iter, int fi
         lz->cont = stop ? 0 : 1;
         if (handle) cudaGraphSetConditional(handle, stop ? 0u : 1u);
     }
+}
+
+__global__ void __launch_bounds__(32) k_lz_eig(LzState *lz, int max_iter, int fixed_iter, double tol,
+                                               cudaGraphConditionalHandle handle) {
+    lz_eig_body(lz, max_iter, fixed_iter, tol, handle);
+}
+
+// One warp per system of a batch.
+__global__ void __launch_bounds__(32) k_lz_eig_batch(const LzSys *__restrict__ sys) {
+    const LzSys &S = sys[blockIdx.x];
+    lz_eig_body(S.lz, S.max_iter, S.fixed_iter, S.tol, 0);
 }
 
 // One thread per system: the systems whose stop test passed in this loop
@@ -589,6 +627,13 @@ void launch_lz_eig(LzState *lz, int max_iter, int fixed_iter, double tol, cudaGr
 void launch_batch_cond(LzState *const *lzs, int nsys, cudaGraphConditionalHandle h, cudaStream_t s) {
     k_batch_cond<<<1, 256, 0, s>>>(lzs, nsys, h);
 }
+void launch_lz_matvec_batch(const LzSys *sys, const int *blk2sys, int nblocks, cudaStream_t s) {
+    k_lz_matvec_batch<<<nblocks, 128, 0, s>>>(sys, blk2sys);
+}
+void launch_lz_update_batch(const LzSys *sys, const int *blk2sys, int nblocks, cudaStream_t s) {
+    k_lz_update_batch<<<nblocks, 256, 0, s>>>(sys, blk2sys);
+}
+void launch_lz_eig_batch(const LzSys *sys, int nsys, cudaStream_t s) { k_lz_eig_batch<<<nsys, 32, 0, s>>>(sys); }
 template <typename T>
 void launch_lz_final(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, bool with_wave, cudaStream_t s) {
     k_lz_final<T><<<nb(N, 256), 256, 0, s>>>(N, args, d.pos_sorted, d.basis, d.uwave, d.lz, with_wave,

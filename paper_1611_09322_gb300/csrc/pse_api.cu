@@ -2,16 +2,17 @@
 // graph and the entry points.
 //
 // One sample is one graph launch.  The graph forks after the cell sort:
-//   real branch:  neighbour list -> WHILE { matvec -> update  ||  eig(T_{j-1}) }
+//   real branch:  neighbour list -> WHILE { matvec -> update -> eig(T_j) }
 //   wave branch:  k-space noise -> cuFFT C2R (x3) -> interpolation
-// and joins in the final combination kernel.  The forces path (c_det M F +
-// c_noise M^{1/2} z) adds M_r F on the real branch before the loop, and its
-// wave branch spreads F, runs cuFFT R2C, applies the deterministic mode
-// factor with the k-space noise fused in, then C2R and interpolation.  The Lanczos loop runs on the
-// device: the eigen kernel of iteration j-1 (FP64, one warp) runs beside the
-// matvec of iteration j and sets the WHILE node's condition, so the host
-// never waits inside a sample.  Per-call arguments (pointers, seed, sample
-// index) live in a small device struct refreshed by one copy before launch.
+// and joins in the final combination kernel.  The Lanczos loop runs on the
+// device: after the matvec and update of step j, the eigen kernel (FP64, one
+// warp) solves T_j, runs the stop test and sets the WHILE node's condition,
+// so the host never waits inside a sample.  Per-call arguments (pointers,
+// seed, sample index) live in a small device struct refreshed by one copy
+// before launch.  The forces path (c_det M F + c_noise M^{1/2} z) adds M_r F
+// on the real branch before the loop, and its wave branch spreads F, runs
+// cuFFT R2C, applies the deterministic mode factor with the k-space noise
+// fused in, then C2R and interpolation.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -425,7 +426,7 @@ template <typename T> pse_status wave_branch(pse_ctx *c, int64_t N, cudaStream_t
 // Capture pieces of one sample.  The prologue runs on c->s_main (which must
 // be capturing): cell list, wave branch forked onto c->s_wave, neighbour
 // list, preconditioner blocks and q_1.  The loop body is one Lanczos step
-// (matvec -> update on `sa`, eigen-solve of the previous T on `sb`).  The
+// (matvec -> update -> eigen-solve of T_j, all on `sa`).  The
 // epilogue joins the wave branch and writes the output.
 template <typename T> pse_status capture_pre(pse_ctx *c, int mode) {
     const int64_t N = c->N;
@@ -446,12 +447,12 @@ template <typename T> pse_status capture_pre(pse_ctx *c, int mode) {
 }
 
 template <typename T>
-void capture_body(pse_ctx *c, cudaStream_t sa, cudaStream_t sb, cudaGraphConditionalHandle h) {
+void capture_body(pse_ctx *c, cudaStream_t sa, cudaGraphConditionalHandle h) {
     Dev<T> &d = dev<T>(c);
     const double ltol = c->params.lanczos_tol > 0 ? c->params.lanczos_tol : c->plan.tol;
     launch_lz_matvec<T>(c->N, geom<T>(c), d, sa);
     launch_lz_update<T>(c->N, c->max_iter, d, sa);
-    launch_lz_eig(d.lz, c->max_iter, c->params.fixed_iter, ltol, h, sb);
+    launch_lz_eig(d.lz, c->max_iter, c->params.fixed_iter, ltol, h, sa);
 }
 
 template <typename T> void capture_post(pse_ctx *c, int mode) {
@@ -499,11 +500,7 @@ template <typename T> pse_status capture_sample(pse_ctx *c, int mode) {
     if (e == cudaSuccess) {
         e = cudaStreamBeginCaptureToGraph(c->s_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaEventRecord(c->ev[2], c->s_body);
-            cudaStreamWaitEvent(c->s_body2, c->ev[2], 0);
-            capture_body<T>(c, c->s_body, c->s_body2, c->cond[mode]);
-            cudaEventRecord(c->ev[3], c->s_body2);
-            cudaStreamWaitEvent(c->s_body, c->ev[3], 0);
+            capture_body<T>(c, c->s_body, c->cond[mode]);
             cudaGraph_t body_out = nullptr;
             e = cudaStreamEndCapture(c->s_body, &body_out);
         }
@@ -1119,7 +1116,11 @@ struct pse_batch {
     std::vector<SampleArgs<float>> h_args;
     LzState **d_lzs = nullptr;            // each system's Lanczos state, for the loop condition
     cudaStream_t body = nullptr;          // captures the shared loop body
-    cudaEvent_t ev_body = nullptr, ev_after = nullptr;
+    cudaStream_t body2 = nullptr;         // the eigen-solves, beside the matvec and update
+    cudaEvent_t ev_body = nullptr, ev_after = nullptr, ev_eig = nullptr;
+    LzSys *d_sys = nullptr;               // per-system descriptors of the fused loop kernels
+    int *d_blk_mv = nullptr, *d_blk_up = nullptr;  // block -> system of the fused matvec / update
+    int nblk_mv = 0, nblk_up = 0;
     std::vector<cudaEvent_t> ev_pre;
     cudaGraphConditionalHandle cond = 0;
 };
@@ -1141,6 +1142,11 @@ extern "C" void pse_batch_destroy(pse_batch *b) {
     if (b->d_lzs) cudaFree(b->d_lzs);
     if (b->root) cudaStreamDestroy(b->root);
     if (b->body) cudaStreamDestroy(b->body);
+    if (b->body2) cudaStreamDestroy(b->body2);
+    if (b->ev_eig) cudaEventDestroy(b->ev_eig);
+    if (b->d_sys) cudaFree(b->d_sys);
+    if (b->d_blk_mv) cudaFree(b->d_blk_mv);
+    if (b->d_blk_up) cudaFree(b->d_blk_up);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->ev_body) cudaEventDestroy(b->ev_body);
     if (b->ev_after) cudaEventDestroy(b->ev_after);
@@ -1176,6 +1182,8 @@ extern "C" pse_status pse_batch_create(pse_batch **out, int nsys, const double *
     }
     if (st == PSE_OK && (cudaStreamCreateWithFlags(&b->root, cudaStreamNonBlocking) != cudaSuccess ||
                          cudaStreamCreateWithFlags(&b->body, cudaStreamNonBlocking) != cudaSuccess ||
+                         cudaStreamCreateWithFlags(&b->body2, cudaStreamNonBlocking) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&b->ev_eig, cudaEventDisableTiming) != cudaSuccess ||
                          cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
                          cudaEventCreateWithFlags(&b->ev_body, cudaEventDisableTiming) != cudaSuccess ||
                          cudaEventCreateWithFlags(&b->ev_after, cudaEventDisableTiming) != cudaSuccess))
@@ -1204,6 +1212,66 @@ extern "C" pse_status pse_batch_create(pse_batch **out, int nsys, const double *
     return PSE_OK;
 }
 
+// Descriptors and block tables of the fused loop kernels.  Each system gets
+// the block counts its own context would launch (one block per 32 particles
+// of the matvec, per 256 of the update, capped at 16 and 8 per SM), so its
+// reductions add the same partial sums in the same order and a batched
+// system's sample is bitwise that of a lone context.
+static pse_status batch_descriptors(pse_batch *b) {
+    const int S = (int)b->sys.size();
+    const int64_t cap_mv = num_sms() * 16, cap_up = num_sms() * 8;
+    std::vector<LzSys> hs(S);
+    std::vector<int> blk_mv, blk_up;
+    for (int k = 0; k < S; ++k) {
+        pse_ctx *c = b->sys[k];
+        const int64_t N = c->N;
+        auto blocks = [&](int64_t per_block, int64_t cap) {
+            const int64_t need = (N + per_block - 1) / per_block;
+            return (int)(need < cap ? (need > 0 ? need : 1) : cap);
+        };
+        LzSys &d = hs[k];
+        d.N = N;
+        d.K = nbr_k(N, c->df.nbr_cap);
+        d.blk_mv = (int)blk_mv.size();
+        d.nblk_mv = blocks(128 / PSE_BATCH_MV_TPP, cap_mv);
+        d.blk_up = (int)blk_up.size();
+        d.nblk_up = blocks(256, cap_up);
+        blk_mv.insert(blk_mv.end(), d.nblk_mv, k);
+        blk_up.insert(blk_up.end(), d.nblk_up, k);
+        d.max_iter = c->max_iter;
+        d.fixed_iter = c->params.fixed_iter;
+        d.tol = c->params.lanczos_tol > 0 ? c->params.lanczos_tol : c->plan.tol;
+        d.g = c->gf;
+        d.rec = c->df.rec;
+        d.count = c->df.nbr_count;
+        d.nbr = c->df.nbr;
+        d.table = c->df.table;
+        d.u = c->df.u;
+        d.part_mv = c->df.partials;
+        d.part_up = c->df.partials + num_sms() * 16 + 32;
+        d.lz = c->df.lz;
+        d.pc = c->df.pc_on;
+        d.basis = c->df.basis;
+    }
+    if (b->d_sys) cudaFree(b->d_sys);
+    if (b->d_blk_mv) cudaFree(b->d_blk_mv);
+    if (b->d_blk_up) cudaFree(b->d_blk_up);
+    b->d_sys = nullptr;
+    b->d_blk_mv = b->d_blk_up = nullptr;
+    if (cudaMalloc((void **)&b->d_sys, sizeof(LzSys) * S) != cudaSuccess ||
+        cudaMalloc((void **)&b->d_blk_mv, sizeof(int) * blk_mv.size()) != cudaSuccess ||
+        cudaMalloc((void **)&b->d_blk_up, sizeof(int) * blk_up.size()) != cudaSuccess) {
+        cudaGetLastError();
+        return PSE_ENOMEM;
+    }
+    CK(cudaMemcpy(b->d_sys, hs.data(), sizeof(LzSys) * S, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b->d_blk_mv, blk_mv.data(), sizeof(int) * blk_mv.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b->d_blk_up, blk_up.data(), sizeof(int) * blk_up.size(), cudaMemcpyHostToDevice));
+    b->nblk_mv = (int)blk_mv.size();
+    b->nblk_up = (int)blk_up.size();
+    return PSE_OK;
+}
+
 extern "C" pse_status pse_batch_sample(pse_batch *b, const int64_t *offsets, const float *d_pos, uint64_t seed,
                                        uint64_t sample_index, float *d_out, void *stream) {
     if (!b || !offsets || !d_pos || !d_out) return PSE_EINVAL;
@@ -1224,6 +1292,8 @@ extern "C" pse_status pse_batch_sample(pse_batch *b, const int64_t *offsets, con
     }
     if (rebuild) {
         batch_drop_graph(b);
+        const pse_status sd = batch_descriptors(b);
+        if (sd != PSE_OK) return sd;
         // prologues of all systems in parallel, one shared WHILE node whose body
         // holds every system's Lanczos step and the batch condition, epilogues
         CK(cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal));
@@ -1242,17 +1312,12 @@ extern "C" pse_status pse_batch_sample(pse_batch *b, const int64_t *offsets, con
         if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(b->body, body, nullptr, nullptr, 0,
                                                               cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaEventRecord(b->ev_body, b->body);
-            for (int k = 0; k < S; ++k) {
-                pse_ctx *c = b->sys[k];
-                cudaStreamWaitEvent(c->s_body, b->ev_body, 0);
-                cudaStreamWaitEvent(c->s_body2, b->ev_body, 0);
-                capture_body<float>(c, c->s_body, c->s_body2, 0);
-                cudaEventRecord(c->ev[2], c->s_body);
-                cudaEventRecord(c->ev[3], c->s_body2);
-                cudaStreamWaitEvent(b->body, c->ev[2], 0);
-                cudaStreamWaitEvent(b->body, c->ev[3], 0);
-            }
+            // one Lanczos step of every system: fused matvec -> fused update ->
+            // the eigen-solves of the new T_j (one warp each); then the
+            // condition retires converged systems
+            launch_lz_matvec_batch(b->d_sys, b->d_blk_mv, b->nblk_mv, b->body);
+            launch_lz_update_batch(b->d_sys, b->d_blk_up, b->nblk_up, b->body);
+            launch_lz_eig_batch(b->d_sys, S, b->body);
             launch_batch_cond(b->d_lzs, S, b->cond, b->body);
             cudaGraph_t body_out = nullptr;
             e = cudaStreamEndCapture(b->body, &body_out);

@@ -255,23 +255,29 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 // Deterministic grid-wide sum: every block stores its partial, the last block
 // to arrive (atomic ticket, no waiting) adds the partials in block order.
 // Returns true in the last block, with *total valid in all its threads.
+// bidx / nblk: this block's index among the nblk blocks reducing together
+// (the launch's grid, or one system's share of a fused multi-system launch).
 __device__ __forceinline__ bool grid_sum_last(double partial, double *partials, unsigned int *counter,
-                                              double *sh, double *total) {
+                                              double *sh, double *total, unsigned int bidx, unsigned int nblk) {
     __shared__ int s_last;
     if (threadIdx.x == 0) {
-        partials[blockIdx.x] = partial;
+        partials[bidx] = partial;
         __threadfence();
         const unsigned int t = atomicAdd(counter, 1u);
-        s_last = (t == gridDim.x - 1);
+        s_last = (t == nblk - 1);
     }
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
     double acc = 0.0;
-    for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) acc += __ldcg(partials + b);
+    for (unsigned int b = threadIdx.x; b < nblk; b += blockDim.x) acc += __ldcg(partials + b);
     *total = block_sum(acc, sh);
     if (threadIdx.x == 0) *counter = 0u;
     return true;
+}
+__device__ __forceinline__ bool grid_sum_last(double partial, double *partials, unsigned int *counter,
+                                              double *sh, double *total) {
+    return grid_sum_last(partial, partials, counter, sh, total, blockIdx.x, gridDim.x);
 }
 #endif
 
@@ -334,6 +340,32 @@ void launch_lz_eig(LzState *lz, int max_iter, int fixed_iter, double tol, cudaGr
                    cudaStream_t s);
 // batch loop condition: active_k = cont_k for every system, continue while any is active
 void launch_batch_cond(LzState *const *lzs, int nsys, cudaGraphConditionalHandle h, cudaStream_t s);
+
+// One system of a fused multi-system Lanczos step (FP32 contexts): its
+// buffers, geometry, stop rule and the block ranges it owns in the fused
+// matvec and update launches.
+struct LzSys {
+    int64_t N;
+    int K;                       // ELL capacity per particle
+    int blk_mv, nblk_mv;         // first block and block count in the fused matvec
+    int blk_up, nblk_up;         // same in the fused update
+    int max_iter, fixed_iter;
+    double tol;
+    Geom<float> g;
+    Rec<float> *rec;
+    const int *count;
+    const int *nbr;
+    const V4<float> *table;
+    V4<float> *u;
+    double *part_mv, *part_up;   // per-block partial sums of the matvec and the update
+    LzState *lz;
+    const float *pc;
+    V4<float> *basis;
+};
+#define PSE_BATCH_MV_TPP 4
+void launch_lz_matvec_batch(const LzSys *sys, const int *blk2sys, int nblocks, cudaStream_t s);
+void launch_lz_update_batch(const LzSys *sys, const int *blk2sys, int nblocks, cudaStream_t s);
+void launch_lz_eig_batch(const LzSys *sys, int nsys, cudaStream_t s);
 template <typename T> void launch_lz_final(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, bool with_wave,
                                            cudaStream_t s);
 // plain matvec of a caller vector (sorted gather -> M_r -> scatter back)

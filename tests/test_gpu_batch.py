@@ -28,6 +28,10 @@ def _systems():
 
 
 def test_batch_equals_lone_contexts(torch):
+    """Each system of a batch (fused multi-system Lanczos kernels) gives the
+    sample a lone context gives with the same Philox streams: same Lanczos J,
+    same values to float rounding (the fused kernels are other compilations
+    of the same arithmetic), and repeated launches are bitwise reproducible."""
     from paper_1611_09322_gb300 import BatchSampler, Sampler
     systems = _systems()
     Ls = [L for _, L, _ in systems]
@@ -37,10 +41,13 @@ def test_batch_equals_lone_contexts(torch):
     pos_all = torch.from_numpy(np.concatenate([p for p, _, _ in systems])).cuda()
     for sample in (3, 4):  # two launches of the same graph
         out = b.sample(pos_all, offsets, SEED, sample).cpu().numpy()
+        again = b.sample(pos_all, offsets, SEED, sample).cpu().numpy()
+        assert np.array_equal(out, again)
         for k, (pos, L, xi) in enumerate(systems):
             s = Sampler(L, 1.0, xi=xi, tol=1e-3, system=k)
             ref = s.sample(torch.from_numpy(pos).cuda(), SEED, sample).cpu().numpy()
-            assert np.array_equal(out[offsets[k]:offsets[k + 1]], ref), k
+            got = out[offsets[k]:offsets[k + 1]]
+            assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max(), k
             assert b.stats(k)["lanczos_iters"] == s.stats()["lanczos_iters"]
             assert b.stats(k)["converged"] == 1
             s.close()
@@ -68,6 +75,6 @@ def test_batch_rebuilds_when_sizes_change(torch):
     out = b.sample(torch.from_numpy(np.concatenate([p1, q2])).cuda(), [0, 1200, 1900], SEED, 1).cpu().numpy()
     s = Sampler(L2, 1.0, xi=0.5, tol=1e-3, system=1)
     ref = s.sample(torch.from_numpy(q2).cuda(), SEED, 1).cpu().numpy()
-    assert np.array_equal(out[1200:], ref)
+    assert np.abs(out[1200:] - ref).max() <= 1e-5 * np.abs(ref).max()
     s.close()
     b.close()
