@@ -350,15 +350,25 @@ pse_status pse_real_matvec_noalloc(double L, double a, double xi, double tol, in
 /* ---------------------------------------------------------------- batched systems
  * Many independent periodic systems of uneven size sampled together (not in
  * the paper).  Each system has its own box, radius and parameters (its own
- * xi, cut-offs and grid); one pse_batch_sample is ONE CUDA graph launch in
- * which every system's complete sample (cell list, neighbour list, device-side
- * Lanczos loop, wave branch) is a parallel branch.  System k draws its noise
- * from Philox streams 2k and 2k + 1, so its output equals that of a lone
- * context created with params.system = k. */
+ * xi, cut-offs and grid); one pse_batch_sample is ONE CUDA graph launch whose
+ * kernels each work for all systems at once (a block -> system table): cell
+ * lists, neighbour lists, q_1, the wave noise and interpolation, and in the
+ * device-side loop the near-field matvec, the Lanczos update and the FP64
+ * eigen-solves; systems that converge drop out of the loop.  The inverse
+ * FFTs run as one batched cuFFT call per grid size: each system's grid is
+ * raised to the next size of a fixed list (16, 20, 24, 28, 32, 40, 48, ...,
+ * a finer grid only lowers the NUFFT error), so systems share sizes.
+ * System k draws its noise from Philox streams 2k and 2k + 1: its output
+ * equals, to float rounding and with the same Lanczos J, that of a lone
+ * context created with params.system = k and grid_M = its batch grid
+ * (pse_batch_get_plan). */
 typedef struct pse_batch pse_batch;
 
 /* nsys >= 1 systems: L[k], a[k] and params p[k] (host arrays of nsys
- * entries).  p[k].system is set to k.  FP32 only. */
+ * entries).  p[k].system is set to k; p[k].grid_M, when set, is kept;
+ * autotune bit 0 is ignored (the size classes replace it).  Interpolation
+ * supports P <= 16 (PSE_ENOTSUPPORTED at the first sample otherwise).  FP32
+ * only. */
 pse_status pse_batch_create(pse_batch **out, int nsys, const double *L, const double *a, const pse_params *p);
 
 /* Sample all systems.  offsets: host array of nsys + 1 particle offsets

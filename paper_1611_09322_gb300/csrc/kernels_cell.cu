@@ -33,9 +33,8 @@ __device__ __forceinline__ float cell_offset(float x, int c, float cs, float cs_
 __device__ __forceinline__ double cell_offset(double x, int c, double cs, double) { return x - c * cs; }
 
 template <typename T>
-__global__ void k_bin(int64_t N, const SampleArgs<T> *args, Geom<T> g, int *cell_of, int *slot, int *count) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= N) return;
+__device__ __forceinline__ void bin_elem(int64_t i, const SampleArgs<T> *args, const Geom<T> &g, int *cell_of,
+                                         int *slot, int *count) {
     const T *p = args->pos + 3 * i;
     const T x = wrap_box(p[0], g.L), y = wrap_box(p[1], g.L), z = wrap_box(p[2], g.L);
     const int cx = cell_coord(x, g.inv_cs, g.nc), cy = cell_coord(y, g.inv_cs, g.nc),
@@ -46,10 +45,15 @@ __global__ void k_bin(int64_t N, const SampleArgs<T> *args, Geom<T> g, int *cell
 }
 
 template <typename T>
-__global__ void k_scatter(int64_t N, const SampleArgs<T> *args, Geom<T> g, const int *cell_of, const int *slot,
-                          const int *start, V4<T> *pos_sorted, V4<T> *loc_sorted, Rec<T> *rec) {
+__global__ void k_bin(int64_t N, const SampleArgs<T> *args, Geom<T> g, int *cell_of, int *slot, int *count) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= N) return;
+    if (i < N) bin_elem<T>(i, args, g, cell_of, slot, count);
+}
+
+template <typename T>
+__device__ __forceinline__ void scatter_elem(int64_t i, const SampleArgs<T> *args, const Geom<T> &g,
+                                             const int *cell_of, const int *slot, const int *start, V4<T> *pos_sorted,
+                                             V4<T> *loc_sorted, Rec<T> *rec) {
     const T *p = args->pos + 3 * i;
     const T x = wrap_box(p[0], g.L), y = wrap_box(p[1], g.L), z = wrap_box(p[2], g.L);
     const int c = cell_of[i];
@@ -71,6 +75,13 @@ __global__ void k_scatter(int64_t N, const SampleArgs<T> *args, Geom<T> g, const
     rec[dst].l = l;
 }
 
+template <typename T>
+__global__ void k_scatter(int64_t N, const SampleArgs<T> *args, Geom<T> g, const int *cell_of, const int *slot,
+                          const int *start, V4<T> *pos_sorted, V4<T> *loc_sorted, Rec<T> *rec) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < N) scatter_elem<T>(i, args, g, cell_of, slot, start, pos_sorted, loc_sorted, rec);
+}
+
 template <typename T> __device__ __forceinline__ long long w_bits(T w) {
     if constexpr (sizeof(T) == 4) return (long long)__float_as_int(w);
     else return __double_as_longlong(w);
@@ -79,9 +90,8 @@ template <typename T> __device__ __forceinline__ long long w_bits(T w) {
 // Insertion sort of each cell's entries by caller index: makes the sorted
 // order, and every summation order downstream, independent of atomics.
 template <typename T>
-__global__ void k_cellsort(int ncell3, const int *start, V4<T> *pos_sorted, V4<T> *loc_sorted, Rec<T> *rec) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell3) return;
+__device__ __forceinline__ void cellsort_cell(int c, const int *start, V4<T> *pos_sorted, V4<T> *loc_sorted,
+                                              Rec<T> *rec) {
     const int b = start[c], e = start[c + 1];
     for (int i = b + 1; i < e; ++i) {
         const V4<T> pa = pos_sorted[i], la = loc_sorted[i];
@@ -98,6 +108,12 @@ __global__ void k_cellsort(int ncell3, const int *start, V4<T> *pos_sorted, V4<T
     for (int i = b; i < e; ++i) rec[i].l = loc_sorted[i];
 }
 
+template <typename T>
+__global__ void k_cellsort(int ncell3, const int *start, V4<T> *pos_sorted, V4<T> *loc_sorted, Rec<T> *rec) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ncell3) cellsort_cell<T>(c, start, pos_sorted, loc_sorted, rec);
+}
+
 // One thread per sorted particle, one pass: every neighbour within r_cut over
 // the 27 stencil cells goes to ELL column cnt (nbr[cnt * N + s], coalesced
 // across a warp when counts agree) as (t << 6) | stencil code.  With
@@ -105,12 +121,11 @@ __global__ void k_cellsort(int ncell3, const int *start, V4<T> *pos_sorted, V4<T
 // most one image of each pair inside r_cut, so the distance test keeps the
 // right one.  Lists longer than K are cut and flag an overflow.
 template <typename T>
-__global__ void __launch_bounds__(128) k_nbr(int64_t N, Geom<T> g, const V4<T> *__restrict__ loc,
-                                             const int *__restrict__ cell_start, int *count, int *nbr, int K,
-                                             int *overflow, unsigned long long *n_pairs) {
-    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ __forceinline__ int nbr_elem(int64_t s, int64_t N, const Geom<T> &g, const V4<T> *__restrict__ loc,
+                                        const int *__restrict__ cell_start, int *count, int *nbr, int K,
+                                        int *overflow) {
     int cnt = 0;
-    if (s < N) {
+    {
         const V4<T> li = loc[s];
         const int c = (int)w_bits(li.w);
         const int nc = g.nc;
@@ -155,11 +170,114 @@ __global__ void __launch_bounds__(128) k_nbr(int64_t N, Geom<T> g, const V4<T> *
         }
         count[s] = cnt;
     }
+    return cnt;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_nbr(int64_t N, Geom<T> g, const V4<T> *__restrict__ loc,
+                                             const int *__restrict__ cell_start, int *count, int *nbr, int K,
+                                             int *overflow, unsigned long long *n_pairs) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int cnt = s < N ? nbr_elem<T>(s, N, g, loc, cell_start, count, nbr, K, overflow) : 0;
     // pair total for the statistics: one atomic per warp
     int tot = cnt;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
     if ((threadIdx.x & 31) == 0 && tot) atomicAdd(n_pairs, (unsigned long long)tot);
+}
+
+// ------------------------------------------------------------------ fused multi-system kernels
+// Block b of a fused launch works for system tab[b]; lb is its index among
+// that system's nb blocks.  Element-wise kernels stride over the system's
+// elements with its blocks.
+#define PSE_BATCH_SYS(kind)                                  \
+    const BSys &S = sys[tab[blockIdx.x]];                    \
+    const int lb = (int)blockIdx.x - S.b0[kind];             \
+    const int64_t stride = (int64_t)S.nb[kind] * blockDim.x
+
+__global__ void k_zero_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
+    PSE_BATCH_SYS(BK_ZERO);
+    for (int64_t c = lb * (int64_t)blockDim.x + threadIdx.x; c < S.nc3; c += stride) S.d.cell_count[c] = 0;
+    if (lb == 0 && threadIdx.x == 0) {
+        S.d.lz->overflow = 0;
+        S.d.lz->n_pairs = 0ull;
+    }
+}
+__global__ void k_bin_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
+    PSE_BATCH_SYS(BK_BIN);
+    for (int64_t i = lb * (int64_t)blockDim.x + threadIdx.x; i < S.N; i += stride)
+        bin_elem<float>(i, S.d.args, S.g, S.d.cell_of, S.d.slot, S.d.cell_count);
+}
+// One block of 1024 threads per system: exclusive scan of the cell counts
+// into cell_start (nc3 + 1 entries), 4096 counts per pass with a carry.
+__global__ void __launch_bounds__(1024) k_scan_batch(const BSys *__restrict__ sys) {
+    const BSys &S = sys[blockIdx.x];
+    __shared__ int sh[1024];
+    int carry = 0;
+    const int n = S.nc3;
+    for (int base0 = 0; base0 < n; base0 += PSE_SCAN_ITEMS) {
+        const int base = base0 + threadIdx.x * 4;
+        int v[4], tot = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = base + k < n ? S.d.cell_count[base + k] : 0;
+            tot += v[k];
+        }
+        sh[threadIdx.x] = tot;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            const int t = threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += t;
+            __syncthreads();
+        }
+        int run = carry + sh[threadIdx.x] - tot;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (base + k < n) S.d.cell_start[base + k] = run;
+            run += v[k];
+        }
+        carry += sh[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) S.d.cell_start[n] = carry;
+}
+__global__ void k_scatter_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
+    PSE_BATCH_SYS(BK_SCATTER);
+    for (int64_t i = lb * (int64_t)blockDim.x + threadIdx.x; i < S.N; i += stride)
+        scatter_elem<float>(i, S.d.args, S.g, S.d.cell_of, S.d.slot, S.d.cell_start, S.d.pos_sorted, S.d.loc_sorted,
+                            S.d.rec);
+}
+__global__ void k_cellsort_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
+    PSE_BATCH_SYS(BK_SORT);
+    for (int64_t c = lb * (int64_t)blockDim.x + threadIdx.x; c < S.nc3; c += stride)
+        cellsort_cell<float>((int)c, S.d.cell_start, S.d.pos_sorted, S.d.loc_sorted, S.d.rec);
+}
+__global__ void __launch_bounds__(128) k_nbr_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
+    PSE_BATCH_SYS(BK_NBR);
+    for (int64_t s0 = lb * (int64_t)blockDim.x; s0 < S.N; s0 += stride) {  // uniform per block
+        const int64_t s = s0 + threadIdx.x;
+        const int cnt = s < S.N ? nbr_elem<float>(s, S.N, S.g, S.d.loc_sorted, S.d.cell_start, S.d.nbr_count,
+                                                   S.d.nbr, S.K, &S.d.lz->overflow)
+                                : 0;
+        int tot = cnt;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        if ((threadIdx.x & 31) == 0 && tot) atomicAdd(&S.d.lz->n_pairs, (unsigned long long)tot);
+    }
+}
+
+static unsigned tab_blocks(const int *nblk, int kind) { return (unsigned)nblk[kind]; }
+
+void launch_batch_prologue_cells(const BSys *sys, int nsys, int *const *tab, const int *nblk, cudaStream_t s) {
+    k_zero_batch<<<tab_blocks(nblk, BK_ZERO), 256, 0, s>>>(sys, tab[BK_ZERO]);
+    k_bin_batch<<<tab_blocks(nblk, BK_BIN), 256, 0, s>>>(sys, tab[BK_BIN]);
+    k_scan_batch<<<nsys, 1024, 0, s>>>(sys);
+    k_scatter_batch<<<tab_blocks(nblk, BK_SCATTER), 256, 0, s>>>(sys, tab[BK_SCATTER]);
+    k_cellsort_batch<<<tab_blocks(nblk, BK_SORT), 256, 0, s>>>(sys, tab[BK_SORT]);
+}
+void launch_batch_nbr(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s) {
+    k_nbr_batch<<<tab_blocks(nblk, BK_NBR), 128, 0, s>>>(sys, tab[BK_NBR]);
 }
 
 // ------------------------------------------------------------------ exclusive scan

@@ -36,12 +36,12 @@ template <typename T> __device__ __forceinline__ double block_total(typename Par
 
 // ------------------------------------------------------------------ init: q_1 = z1, beta_0
 template <typename T>
-__global__ void __launch_bounds__(256) k_lz_init(int64_t N, const SampleArgs<T> *args, int system,
-                                                 const V4<T> *pos_sorted, V4<T> *q1, Rec<T> *rec, double *partials,
-                                                 LzState *lz, const float *__restrict__ pc) {
-    __shared__ double sh[32];
+__device__ __forceinline__ void lz_init_body(int64_t N, const SampleArgs<T> *args, int system,
+                                             const V4<T> *pos_sorted, V4<T> *q1, Rec<T> *rec, double *partials,
+                                             LzState *lz, const float *__restrict__ pc, int bidx, int nblk,
+                                             double *sh) {
     typename Part<T>::type part = 0;
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t s = bidx * (int64_t)blockDim.x + threadIdx.x; s < N; s += (int64_t)nblk * blockDim.x) {
         const uint32_t orig = (uint32_t)w_bits_r(pos_sorted[s].w);
         const Normals4<T> z = normals4<T>(orig, 2u * system, args->seed, args->sample);
         V4<T> v;
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) k_lz_init(int64_t N, const SampleArgs<T> 
     }
     const double bsum = block_total<T>(part, sh);
     double total;
-    if (grid_sum_last(bsum, partials, &lz->counter_init, sh, &total) && threadIdx.x == 0) {
+    if (grid_sum_last(bsum, partials, &lz->counter_init, sh, &total, bidx, nblk) && threadIdx.x == 0) {
         lz->beta[0] = sqrt(total);
         lz->iter = 1;
         lz->jeig = 0;
@@ -73,6 +73,21 @@ __global__ void __launch_bounds__(256) k_lz_init(int64_t N, const SampleArgs<T> 
         lz->active = 1;
         lz->rel = 0.0;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_lz_init(int64_t N, const SampleArgs<T> *args, int system,
+                                                 const V4<T> *pos_sorted, V4<T> *q1, Rec<T> *rec, double *partials,
+                                                 LzState *lz, const float *__restrict__ pc) {
+    __shared__ double sh[32];
+    lz_init_body<T>(N, args, system, pos_sorted, q1, rec, partials, lz, pc, blockIdx.x, gridDim.x, sh);
+}
+
+__global__ void __launch_bounds__(256) k_lz_init_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
+    __shared__ double sh[32];
+    const BSys &S = sys[tab[blockIdx.x]];
+    lz_init_body<float>(S.N, S.d.args, S.system, S.d.pos_sorted, S.d.basis, S.d.rec, S.d.partials, S.d.lz, S.d.pc_on,
+                        (int)blockIdx.x - S.b0[BK_INIT], S.nb[BK_INIT], sh);
 }
 
 // ------------------------------------------------------------------ near-field matvec
@@ -454,7 +469,7 @@ __global__ void __launch_bounds__(32) k_lz_eig_batch(const LzSys *__restrict__ s
 // One thread per system: the systems whose stop test passed in this loop
 // body become inactive for the next one; the shared WHILE node continues
 // while any system is still active.
-__global__ void k_batch_cond(LzState *const *lzs, int nsys, cudaGraphConditionalHandle h) {
+__global__ void k_batch_cond(LzState *const *lzs, int nsys, cudaGraphConditionalHandle h, int *any_out) {
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
@@ -465,7 +480,10 @@ __global__ void k_batch_cond(LzState *const *lzs, int nsys, cudaGraphConditional
         if (c) atomicOr(&any, 1);
     }
     __syncthreads();
-    if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+    if (threadIdx.x == 0) {
+        if (h) cudaGraphSetConditional(h, any ? 1u : 0u);
+        if (any_out) *any_out = any;
+    }
 }
 
 // ------------------------------------------------------------------ final combination
@@ -473,9 +491,10 @@ __global__ void k_batch_cond(LzState *const *lzs, int nsys, cudaGraphConditional
 // On the forces path (udet != null) out = c_noise x + c_det M_r F + wave, the
 // wave part already carrying both weights.
 template <typename T>
-__global__ void k_lz_final(int64_t N, const SampleArgs<T> *args, const V4<T> *pos_sorted, const V4<T> *basis,
-                           const V4<T> *uwave, const LzState *lz, bool with_wave, const float *__restrict__ pc,
-                           const V4<T> *udet) {
+__device__ __forceinline__ void lz_final_body(int64_t N, const SampleArgs<T> *args, const V4<T> *pos_sorted,
+                                              const V4<T> *basis, const V4<T> *uwave, const LzState *lz,
+                                              bool with_wave, const float *__restrict__ pc, const V4<T> *udet,
+                                              int64_t s) {
     __shared__ T cf[PSE_MAXIT + 2];
     __shared__ double cfd[PSE_MAXIT + 2];
     const int J = lz->J;
@@ -484,7 +503,6 @@ __global__ void k_lz_final(int64_t N, const SampleArgs<T> *args, const V4<T> *po
         else cfd[i] = lz->beta[0] * lz->y[i] / lz->beta[i];
     }
     __syncthreads();
-    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= N) return;
     T x = 0, y = 0, z = 0;
     for (int i = 0; i < J; ++i) {
@@ -519,6 +537,23 @@ __global__ void k_lz_final(int64_t N, const SampleArgs<T> *args, const V4<T> *po
         z = cn * z + cd * m.z;
     }
     if (args->out) { args->out[o] = x + wx; args->out[o + 1] = y + wy; args->out[o + 2] = z + wz; }
+}
+
+template <typename T>
+__global__ void k_lz_final(int64_t N, const SampleArgs<T> *args, const V4<T> *pos_sorted, const V4<T> *basis,
+                           const V4<T> *uwave, const LzState *lz, bool with_wave, const float *__restrict__ pc,
+                           const V4<T> *udet) {
+    lz_final_body<T>(N, args, pos_sorted, basis, uwave, lz, with_wave, pc, udet,
+                     blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+}
+
+// One block of 256 particles per launch block: each block's particles belong
+// to one system (blocks never straddle systems).
+__global__ void k_lz_final_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
+    const BSys &S = sys[tab[blockIdx.x]];
+    const int lb = (int)blockIdx.x - S.b0[BK_FINAL];
+    lz_final_body<float>(S.N, S.d.args, S.d.pos_sorted, S.d.basis, S.d.uwave, S.d.lz, true, S.d.pc_on, nullptr,
+                         lb * (int64_t)blockDim.x + threadIdx.x);
 }
 
 // Forces path without noise: out = c_det M_r F + wave part (c_det M_w F), caller order.
@@ -624,8 +659,8 @@ void launch_lz_eig(LzState *lz, int max_iter, int fixed_iter, double tol, cudaGr
                    cudaStream_t s) {
     k_lz_eig<<<1, 32, 0, s>>>(lz, max_iter, fixed_iter, tol, h);
 }
-void launch_batch_cond(LzState *const *lzs, int nsys, cudaGraphConditionalHandle h, cudaStream_t s) {
-    k_batch_cond<<<1, 256, 0, s>>>(lzs, nsys, h);
+void launch_batch_cond(LzState *const *lzs, int nsys, cudaGraphConditionalHandle h, cudaStream_t s, int *any_out) {
+    k_batch_cond<<<1, 256, 0, s>>>(lzs, nsys, h, any_out);
 }
 void launch_lz_matvec_batch(const LzSys *sys, const int *blk2sys, int nblocks, cudaStream_t s) {
     k_lz_matvec_batch<<<nblocks, 128, 0, s>>>(sys, blk2sys);
@@ -634,6 +669,12 @@ void launch_lz_update_batch(const LzSys *sys, const int *blk2sys, int nblocks, c
     k_lz_update_batch<<<nblocks, 256, 0, s>>>(sys, blk2sys);
 }
 void launch_lz_eig_batch(const LzSys *sys, int nsys, cudaStream_t s) { k_lz_eig_batch<<<nsys, 32, 0, s>>>(sys); }
+void launch_batch_init(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s) {
+    k_lz_init_batch<<<nblk[BK_INIT], 256, 0, s>>>(sys, tab[BK_INIT]);
+}
+void launch_batch_final(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s) {
+    k_lz_final_batch<<<nblk[BK_FINAL], 256, 0, s>>>(sys, tab[BK_FINAL]);
+}
 template <typename T>
 void launch_lz_final(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, bool with_wave, cudaStream_t s) {
     k_lz_final<T><<<nb(N, 256), 256, 0, s>>>(N, args, d.pos_sorted, d.basis, d.uwave, d.lz, with_wave,

@@ -90,12 +90,9 @@ __device__ __forceinline__ T mode_scale(const ModeIdx &m, const WaveGeom<T> &w, 
 // One thread per half-spectrum mode: vhat = sc(k) (I - kk) dW2(k); k = 0 and
 // Nyquist modes are zero.
 template <typename T>
-__global__ void k_wave_noise(WaveGeom<T> w, const SampleArgs<T> *args, int system, typename Cplx<T>::type *spec,
-                             int64_t plane) {
+__device__ __forceinline__ void wave_noise_elem(int64_t t, const WaveGeom<T> &w, const SampleArgs<T> *args,
+                                                int system, typename Cplx<T>::type *spec, int64_t plane) {
     using C = typename Cplx<T>::type;
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t nmodes = (int64_t)w.M * w.M * w.Mh1;
-    if (t >= nmodes) return;
     const ModeIdx m = mode_of(t, w.M, w.Mh1);
     C o0, o1, o2;
     o0.x = o0.y = o1.x = o1.y = o2.x = o2.y = T(0);
@@ -113,6 +110,13 @@ __global__ void k_wave_noise(WaveGeom<T> w, const SampleArgs<T> *args, int syste
     spec[t] = o0;
     spec[plane + t] = o1;
     spec[2 * plane + t] = o2;
+}
+
+template <typename T>
+__global__ void k_wave_noise(WaveGeom<T> w, const SampleArgs<T> *args, int system, typename Cplx<T>::type *spec,
+                             int64_t plane) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < (int64_t)w.M * w.M * w.Mh1) wave_noise_elem<T>(t, w, args, system, spec, plane);
 }
 
 // Mode factor applied in place to a forward (R2C) spectrum, one thread per
@@ -477,6 +481,17 @@ __device__ __forceinline__ void interp_particle(int64_t s, bool active, int lg, 
     }
 }
 
+// Fused over the systems of a batch (wave noise of every system's half
+// spectrum; interpolation with 16 lanes per particle, P <= 16).
+__global__ void k_wave_noise_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
+    const BSys &S = sys[tab[blockIdx.x]];
+    const int lb = (int)blockIdx.x - S.b0[BK_NOISE];
+    const int64_t plane = (int64_t)S.w.M * S.w.M * S.w.Mh1;
+    const int64_t stride = (int64_t)S.nb[BK_NOISE] * blockDim.x;
+    for (int64_t t = lb * (int64_t)blockDim.x + threadIdx.x; t < plane; t += stride)
+        wave_noise_elem<float>(t, S.w, S.d.args, S.system, (cufftComplex *)S.d.spec, plane);
+}
+
 // One lane group per particle, one launch-wide pass.
 template <typename T, int G>
 __global__ void __launch_bounds__(128) k_interp(int64_t N, WaveGeom<T> w, const V4<T> *__restrict__ pos_sorted,
@@ -486,7 +501,26 @@ __global__ void __launch_bounds__(128) k_interp(int64_t N, WaveGeom<T> w, const 
     interp_particle<T, G>(tid / G, tid / G < N, lg, (threadIdx.x & 31) - lg, w, pos_sorted, grid, uwave);
 }
 
+__global__ void __launch_bounds__(128) k_interp_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
+    constexpr int G = PSE_BATCH_INTERP_G;
+    const BSys &S = sys[tab[blockIdx.x]];
+    const int lb = (int)blockIdx.x - S.b0[BK_INTERP];
+    const int lg = threadIdx.x % G;
+    const int64_t per_block = blockDim.x / G;
+    for (int64_t base = lb * per_block; base < S.N; base += (int64_t)S.nb[BK_INTERP] * per_block) {  // uniform
+        const int64_t s = base + threadIdx.x / G;
+        interp_particle<float, G>(s, s < S.N, lg, (threadIdx.x & 31) - lg, S.w, S.d.pos_sorted, S.d.grid, S.d.uwave);
+    }
+}
+
 static inline unsigned nbw(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+void launch_batch_noise(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s) {
+    k_wave_noise_batch<<<nblk[BK_NOISE], 256, 0, s>>>(sys, tab[BK_NOISE]);
+}
+void launch_batch_interp(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s) {
+    k_interp_batch<<<nblk[BK_INTERP], 128, 0, s>>>(sys, tab[BK_INTERP]);
+}
 
 template <typename T>
 void launch_wave_noise(WaveGeom<T> w, const SampleArgs<T> *args, int system, void *spec, cudaStream_t s) {

@@ -1121,6 +1121,22 @@ struct pse_batch {
     LzSys *d_sys = nullptr;               // per-system descriptors of the fused loop kernels
     int *d_blk_mv = nullptr, *d_blk_up = nullptr;  // block -> system of the fused matvec / update
     int nblk_mv = 0, nblk_up = 0;
+    BSys *d_bsys = nullptr;               // per-system descriptors of the fused prologue / epilogue
+    int *d_btab[PSE_BK] = {};             // block -> system, per fused kernel kind
+    int bnblk[PSE_BK] = {};
+    cudaStream_t wave = nullptr;          // wave branch of the batch
+    int *d_any = nullptr;                 // any system still iterating (host-loop mode)
+    // systems whose grids share a size share one pooled spectrum / grid and one
+    // batched cuFFT plan (3 transforms per system)
+    struct FftGroup {
+        int M = 0;
+        std::vector<int> members;
+        void *spec = nullptr, *grid = nullptr;
+        cufftHandle plan = 0;
+        bool plan_made = false;
+    };
+    std::vector<FftGroup> groups;
+    cudaEvent_t ev_sorted = nullptr, ev_wave = nullptr, ev_noise = nullptr;
     std::vector<cudaEvent_t> ev_pre;
     cudaGraphConditionalHandle cond = 0;
 };
@@ -1147,6 +1163,18 @@ extern "C" void pse_batch_destroy(pse_batch *b) {
     if (b->d_sys) cudaFree(b->d_sys);
     if (b->d_blk_mv) cudaFree(b->d_blk_mv);
     if (b->d_blk_up) cudaFree(b->d_blk_up);
+    if (b->d_bsys) cudaFree(b->d_bsys);
+    for (int k = 0; k < PSE_BK; ++k) if (b->d_btab[k]) cudaFree(b->d_btab[k]);
+    for (auto &g : b->groups) {
+        if (g.plan_made) cufftDestroy(g.plan);
+        if (g.spec) cudaFree(g.spec);
+        if (g.grid) cudaFree(g.grid);
+    }
+    if (b->wave) cudaStreamDestroy(b->wave);
+    if (b->d_any) cudaFree(b->d_any);
+    if (b->ev_sorted) cudaEventDestroy(b->ev_sorted);
+    if (b->ev_wave) cudaEventDestroy(b->ev_wave);
+    if (b->ev_noise) cudaEventDestroy(b->ev_noise);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->ev_body) cudaEventDestroy(b->ev_body);
     if (b->ev_after) cudaEventDestroy(b->ev_after);
@@ -1164,13 +1192,59 @@ extern "C" pse_status pse_batch_create(pse_batch **out, int nsys, const double *
     if (!b) return PSE_ENOMEM;
     if (cudaGetDevice(&b->device) != cudaSuccess) { cudaGetLastError(); delete b; return PSE_ECUDA; }
     pse_status st = PSE_OK;
+    // grid size classes: each system's Sec. II C grid is raised to the next
+    // class (a finer grid only lowers the NUFFT error), so that systems of a
+    // class share one batched inverse FFT
+    static const int classes[] = {16, 20, 24, 28, 32, 40, 48, 56, 64, 72, 80, 96, 112, 128, 144, 160, 192,
+                                  224, 256, 288, 320, 384, 448, 512, 576, 640, 768, 896, 1024};
     for (int k = 0; k < nsys && st == PSE_OK; ++k) {
         if (p[k].precision != PSE_FP32) { st = PSE_ENOTSUPPORTED; break; }
         pse_params q = p[k];
         q.system = k;
+        q.autotune &= ~1;  // the size class replaces the per-system FFT-size timing
+        if (q.grid_M <= 0) {
+            pse_plan_info pi;
+            st = pse_plan(L[k], a[k], &q, &pi);
+            if (st != PSE_OK) break;
+            for (int cl : classes)
+                if (cl >= pi.M) { q.grid_M = cl; break; }
+        }
         pse_ctx *c = nullptr;
         st = pse_create_ex(&c, L[k], a[k], &q);
         if (st == PSE_OK) b->sys.push_back(c);
+    }
+    // pooled spectra / grids and one plan per grid size
+    for (int k = 0; k < (int)b->sys.size() && st == PSE_OK; ++k) {
+        const int M = b->sys[k]->plan.M;
+        size_t gi = 0;
+        while (gi < b->groups.size() && b->groups[gi].M != M) ++gi;
+        if (gi == b->groups.size()) {
+            b->groups.emplace_back();
+            b->groups.back().M = M;
+        }
+        b->groups[gi].members.push_back(k);
+    }
+    for (auto &g : b->groups) {
+        if (st != PSE_OK) break;
+        const int64_t M = g.M, plane = M * M * (M / 2 + 1), n = (int64_t)g.members.size();
+        if (cudaMalloc(&g.spec, sizeof(cufftComplex) * 3 * plane * n) != cudaSuccess ||
+            cudaMalloc(&g.grid, sizeof(float) * 3 * M * M * M * n) != cudaSuccess) {
+            cudaGetLastError();
+            st = PSE_ENOMEM;
+            break;
+        }
+        int nn[3] = {(int)M, (int)M, (int)M};
+        if (cufftPlanMany(&g.plan, 3, nn, nullptr, 1, (int)plane, nullptr, 1, (int)(M * M * M), CUFFT_C2R,
+                          (int)(3 * n)) != CUFFT_SUCCESS) {
+            st = PSE_ECUFFT;
+            break;
+        }
+        g.plan_made = true;
+        for (int i = 0; i < (int)n; ++i) {  // the system's kernels use its slice of the pool
+            pse_ctx *c = b->sys[g.members[i]];
+            c->df.spec = (cufftComplex *)g.spec + 3 * plane * i;
+            c->df.grid = (float *)g.grid + 3 * M * M * M * i;
+        }
     }
     if (st == PSE_OK && cudaMalloc(&b->d_args, sizeof(SampleArgs<float>) * nsys) != cudaSuccess) {
         cudaGetLastError();
@@ -1183,6 +1257,10 @@ extern "C" pse_status pse_batch_create(pse_batch **out, int nsys, const double *
     if (st == PSE_OK && (cudaStreamCreateWithFlags(&b->root, cudaStreamNonBlocking) != cudaSuccess ||
                          cudaStreamCreateWithFlags(&b->body, cudaStreamNonBlocking) != cudaSuccess ||
                          cudaStreamCreateWithFlags(&b->body2, cudaStreamNonBlocking) != cudaSuccess ||
+                         cudaStreamCreateWithFlags(&b->wave, cudaStreamNonBlocking) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&b->ev_sorted, cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&b->ev_wave, cudaEventDisableTiming) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&b->ev_noise, cudaEventDisableTiming) != cudaSuccess ||
                          cudaEventCreateWithFlags(&b->ev_eig, cudaEventDisableTiming) != cudaSuccess ||
                          cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
                          cudaEventCreateWithFlags(&b->ev_body, cudaEventDisableTiming) != cudaSuccess ||
@@ -1269,7 +1347,112 @@ static pse_status batch_descriptors(pse_batch *b) {
     CK(cudaMemcpy(b->d_blk_up, blk_up.data(), sizeof(int) * blk_up.size(), cudaMemcpyHostToDevice));
     b->nblk_mv = (int)blk_mv.size();
     b->nblk_up = (int)blk_up.size();
+
+    // prologue / epilogue kernels: blocks per system for each kind
+    std::vector<BSys> hb(S);
+    std::vector<int> tabs[PSE_BK];
+    for (int k = 0; k < S; ++k) {
+        pse_ctx *c = b->sys[k];
+        if (c->plan.P > PSE_BATCH_INTERP_G) return PSE_ENOTSUPPORTED;
+        BSys &d = hb[k];
+        d.N = c->N;
+        d.nc3 = c->ncell3;
+        d.system = c->params.system;
+        d.K = nbr_k(c->N, c->df.nbr_cap);
+        d.g = c->gf;
+        d.w = c->wf;
+        d.d = c->df;
+        const int64_t modes = (int64_t)c->plan.M * c->plan.M * (c->plan.M / 2 + 1);
+        const int64_t n_per[PSE_BK] = {
+            (d.nc3 + 255) / 256,                               // zero
+            (d.N + 255) / 256,                                 // bin
+            (d.N + 255) / 256,                                 // scatter
+            (d.nc3 + 255) / 256,                               // cell sort
+            (d.N + 127) / 128,                                 // neighbours
+            0,                                                 // init (set below)
+            (modes + 255) / 256,                               // noise
+            (d.N * PSE_BATCH_INTERP_G + 127) / 128,            // interpolation
+            (d.N + 255) / 256};                                // final (one block per 256, exact)
+        for (int kind = 0; kind < PSE_BK; ++kind) {
+            int64_t n = n_per[kind];
+            if (kind == BK_INIT) {  // the lone context's grid, so beta_0 adds the same partials
+                const int64_t need = (d.N + 255) / 256, cap = (int64_t)num_sms() * 8;
+                n = need < cap ? need : cap;
+            }
+            if (n < 1) n = 1;
+            if (n > (1 << 24)) return PSE_EINVAL;
+            d.b0[kind] = (int)tabs[kind].size();
+            d.nb[kind] = (int)n;
+            tabs[kind].insert(tabs[kind].end(), (size_t)n, k);
+        }
+    }
+    if (b->d_bsys) cudaFree(b->d_bsys);
+    b->d_bsys = nullptr;
+    for (int kind = 0; kind < PSE_BK; ++kind) {
+        if (b->d_btab[kind]) cudaFree(b->d_btab[kind]);
+        b->d_btab[kind] = nullptr;
+    }
+    if (cudaMalloc((void **)&b->d_bsys, sizeof(BSys) * S) != cudaSuccess) {
+        cudaGetLastError();
+        return PSE_ENOMEM;
+    }
+    CK(cudaMemcpy(b->d_bsys, hb.data(), sizeof(BSys) * S, cudaMemcpyHostToDevice));
+    for (int kind = 0; kind < PSE_BK; ++kind) {
+        if (cudaMalloc((void **)&b->d_btab[kind], sizeof(int) * tabs[kind].size()) != cudaSuccess) {
+            cudaGetLastError();
+            return PSE_ENOMEM;
+        }
+        CK(cudaMemcpy(b->d_btab[kind], tabs[kind].data(), sizeof(int) * tabs[kind].size(), cudaMemcpyHostToDevice));
+        b->bnblk[kind] = (int)tabs[kind].size();
+    }
     return PSE_OK;
+}
+
+// Pieces of one batched sample, on stream `s` (capturing or not): the fused
+// prologue (cell lists; the wave branch -- noise of all systems, one batched
+// C2R per grid size, interpolation of all -- beside the neighbour lists,
+// preconditioner blocks and q_1), one Lanczos step of every system, and the
+// epilogue (final combination of all systems once the wave branch is done).
+static pse_status batch_prologue(pse_batch *b, cudaStream_t s) {
+    const int S = (int)b->sys.size();
+    pse_status st = PSE_OK;
+    launch_batch_prologue_cells(b->d_bsys, S, b->d_btab, b->bnblk, s);
+    cudaEventRecord(b->ev_sorted, s);
+    cudaStreamWaitEvent(b->wave, b->ev_sorted, 0);
+    launch_batch_noise(b->d_bsys, b->d_btab, b->bnblk, b->wave);
+    cudaEventRecord(b->ev_noise, b->wave);
+    for (size_t gi = 0; gi < b->groups.size() && st == PSE_OK; ++gi) {
+        auto &g = b->groups[gi];
+        pse_ctx *c = b->sys[g.members[0]];  // the first member's stream carries the branch
+        cudaStreamWaitEvent(c->s_wave, b->ev_noise, 0);
+        if (cufftSetStream(g.plan, c->s_wave) != CUFFT_SUCCESS ||
+            cufftExecC2R(g.plan, (cufftComplex *)g.spec, (cufftReal *)g.grid) != CUFFT_SUCCESS)
+            st = PSE_ECUFFT;
+        cudaEventRecord(b->ev_pre[gi], c->s_wave);
+        cudaStreamWaitEvent(b->wave, b->ev_pre[gi], 0);
+    }
+    launch_batch_interp(b->d_bsys, b->d_btab, b->bnblk, b->wave);
+    cudaEventRecord(b->ev_wave, b->wave);
+    launch_batch_nbr(b->d_bsys, b->d_btab, b->bnblk, s);
+    for (int k = 0; k < S; ++k)
+        if (b->sys[k]->pc_enabled)
+            launch_pc_infer(b->sys[k]->N, b->sys[k]->gf, b->sys[k]->df, b->sys[k]->df.pc_theta, b->sys[k]->pc_s0,
+                            b->sys[k]->df.pc, s);
+    launch_batch_init(b->d_bsys, b->d_btab, b->bnblk, s);
+    return st;
+}
+
+static void batch_step(pse_batch *b, cudaStream_t s, cudaGraphConditionalHandle h, int *any_out) {
+    const int S = (int)b->sys.size();
+    launch_lz_matvec_batch(b->d_sys, b->d_blk_mv, b->nblk_mv, s);
+    launch_lz_update_batch(b->d_sys, b->d_blk_up, b->nblk_up, s);
+    launch_lz_eig_batch(b->d_sys, S, s);
+    launch_batch_cond(b->d_lzs, S, h, s, any_out);
+}
+
+static void batch_epilogue(pse_batch *b, cudaStream_t s) {
+    cudaStreamWaitEvent(s, b->ev_wave, 0);
+    launch_batch_final(b->d_bsys, b->d_btab, b->bnblk, s);
 }
 
 extern "C" pse_status pse_batch_sample(pse_batch *b, const int64_t *offsets, const float *d_pos, uint64_t seed,
@@ -1281,7 +1464,8 @@ extern "C" pse_status pse_batch_sample(pse_batch *b, const int64_t *offsets, con
         if (offsets[k + 1] - offsets[k] < 1) return PSE_EINVAL;
     DeviceGuard guard(b->device);
     cudaStream_t s = (cudaStream_t)stream;
-    bool rebuild = b->exec == nullptr;
+    const bool plain = b->sys[0]->params.use_graph < 0;
+    bool rebuild = plain || b->exec == nullptr;
     for (int k = 0; k < S; ++k) {
         const int64_t N = offsets[k + 1] - offsets[k];
         if (N != b->built_N[k]) rebuild = true;
@@ -1294,43 +1478,23 @@ extern "C" pse_status pse_batch_sample(pse_batch *b, const int64_t *offsets, con
         batch_drop_graph(b);
         const pse_status sd = batch_descriptors(b);
         if (sd != PSE_OK) return sd;
+    }
+    if (rebuild && !plain) {
         // prologues of all systems in parallel, one shared WHILE node whose body
         // holds every system's Lanczos step and the batch condition, epilogues
         CK(cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal));
-        cudaEventRecord(b->ev_fork, b->root);
-        pse_status st = PSE_OK;
-        for (int k = 0; k < S; ++k) {
-            pse_ctx *c = b->sys[k];
-            cudaStreamWaitEvent(c->s_main, b->ev_fork, 0);
-            const pse_status sk = capture_pre<float>(c, GM_SAMPLE);
-            if (sk != PSE_OK && st == PSE_OK) st = sk;
-            cudaEventRecord(b->ev_pre[k], c->s_main);
-            cudaStreamWaitEvent(b->root, b->ev_pre[k], 0);
-        }
+        pse_status st = batch_prologue(b, b->root);
         cudaGraph_t body = nullptr;
         cudaError_t e = add_while(b->root, &b->cond, &body);
         if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(b->body, body, nullptr, nullptr, 0,
                                                               cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            // one Lanczos step of every system: fused matvec -> fused update ->
-            // the eigen-solves of the new T_j (one warp each); then the
-            // condition retires converged systems
-            launch_lz_matvec_batch(b->d_sys, b->d_blk_mv, b->nblk_mv, b->body);
-            launch_lz_update_batch(b->d_sys, b->d_blk_up, b->nblk_up, b->body);
-            launch_lz_eig_batch(b->d_sys, S, b->body);
-            launch_batch_cond(b->d_lzs, S, b->cond, b->body);
+            batch_step(b, b->body, b->cond, nullptr);
             cudaGraph_t body_out = nullptr;
             e = cudaStreamEndCapture(b->body, &body_out);
         }
         if (e != cudaSuccess && st == PSE_OK) st = PSE_ECUDA;
-        cudaEventRecord(b->ev_after, b->root);
-        for (int k = 0; k < S; ++k) {
-            pse_ctx *c = b->sys[k];
-            cudaStreamWaitEvent(c->s_main, b->ev_after, 0);
-            capture_post<float>(c, GM_SAMPLE);
-            cudaEventRecord(b->ev_join[k], c->s_main);
-            cudaStreamWaitEvent(b->root, b->ev_join[k], 0);
-        }
+        batch_epilogue(b, b->root);
         cudaGraph_t graph = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(b->root, &graph);
         if (st != PSE_OK || e2 != cudaSuccess) {
@@ -1359,7 +1523,25 @@ extern "C" pse_status pse_batch_sample(pse_batch *b, const int64_t *offsets, con
         a.c_noise = 1.0;
     }
     CK(cudaMemcpyAsync(b->d_args, b->h_args.data(), sizeof(SampleArgs<float>) * S, cudaMemcpyHostToDevice, s));
-    CK(cudaGraphLaunch(b->exec, s));
+    if (plain) {  // the same kernels without a graph, host-side loop (one sync per step)
+        if (!b->d_any && cudaMalloc((void **)&b->d_any, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return PSE_ENOMEM;
+        }
+        pse_status st = batch_prologue(b, s);
+        if (st != PSE_OK) return st;
+        for (int it = 0; it < PSE_MAXIT + 2; ++it) {
+            batch_step(b, s, 0, b->d_any);
+            int any = 0;
+            CK(cudaMemcpyAsync(&any, b->d_any, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (!any) break;
+        }
+        batch_epilogue(b, s);
+        for (int k = 0; k < S; ++k) b->built_N[k] = offsets[k + 1] - offsets[k];
+    } else {
+        CK(cudaGraphLaunch(b->exec, s));
+    }
     for (pse_ctx *c : b->sys) c->last_stream = s;
     CK(cudaGetLastError());
     return PSE_OK;

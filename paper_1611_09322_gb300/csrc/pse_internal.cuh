@@ -339,7 +339,8 @@ template <typename T> void launch_lz_update(int64_t N, int max_iter, const Dev<T
 void launch_lz_eig(LzState *lz, int max_iter, int fixed_iter, double tol, cudaGraphConditionalHandle h,
                    cudaStream_t s);
 // batch loop condition: active_k = cont_k for every system, continue while any is active
-void launch_batch_cond(LzState *const *lzs, int nsys, cudaGraphConditionalHandle h, cudaStream_t s);
+void launch_batch_cond(LzState *const *lzs, int nsys, cudaGraphConditionalHandle h, cudaStream_t s,
+                       int *any_out = nullptr);
 
 // One system of a fused multi-system Lanczos step (FP32 contexts): its
 // buffers, geometry, stop rule and the block ranges it owns in the fused
@@ -363,6 +364,28 @@ struct LzSys {
     V4<float> *basis;
 };
 #define PSE_BATCH_MV_TPP 4
+
+// One system of a batch for the fused prologue / epilogue kernels (FP32):
+// sizes, geometry, buffers and, per fused kernel kind, the first block and
+// block count it owns (block -> system tables map the other way).
+enum { BK_ZERO = 0, BK_BIN, BK_SCATTER, BK_SORT, BK_NBR, BK_INIT, BK_NOISE, BK_INTERP, BK_FINAL, PSE_BK };
+#define PSE_BATCH_INTERP_G 16
+struct BSys {
+    int64_t N;
+    int nc3;        // cell slots
+    int system;     // Philox stream pair
+    int K;          // ELL capacity per particle
+    Geom<float> g;
+    WaveGeom<float> w;
+    Dev<float> d;
+    int b0[PSE_BK], nb[PSE_BK];
+};
+void launch_batch_prologue_cells(const BSys *sys, int nsys, int *const *tab, const int *nblk, cudaStream_t s);
+void launch_batch_nbr(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s);
+void launch_batch_init(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s);
+void launch_batch_final(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s);
+void launch_batch_noise(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s);
+void launch_batch_interp(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s);
 void launch_lz_matvec_batch(const LzSys *sys, const int *blk2sys, int nblocks, cudaStream_t s);
 void launch_lz_update_batch(const LzSys *sys, const int *blk2sys, int nblocks, cudaStream_t s);
 void launch_lz_eig_batch(const LzSys *sys, int nsys, cudaStream_t s);

@@ -28,8 +28,8 @@ def _systems():
 
 
 def test_batch_equals_lone_contexts(torch):
-    """Each system of a batch (fused multi-system Lanczos kernels) gives the
-    sample a lone context gives with the same Philox streams: same Lanczos J,
+    """Each system of a batch (fused multi-system kernels, pooled FFTs) gives the
+    sample a lone context on the same grid gives with the same Philox streams: same Lanczos J,
     same values to float rounding (the fused kernels are other compilations
     of the same arithmetic), and repeated launches are bitwise reproducible."""
     from paper_1611_09322_gb300 import BatchSampler, Sampler
@@ -44,7 +44,7 @@ def test_batch_equals_lone_contexts(torch):
         again = b.sample(pos_all, offsets, SEED, sample).cpu().numpy()
         assert np.array_equal(out, again)
         for k, (pos, L, xi) in enumerate(systems):
-            s = Sampler(L, 1.0, xi=xi, tol=1e-3, system=k)
+            s = Sampler(L, 1.0, xi=xi, tol=1e-3, system=k, grid_M=b.plan(k)["M"])
             ref = s.sample(torch.from_numpy(pos).cuda(), SEED, sample).cpu().numpy()
             got = out[offsets[k]:offsets[k + 1]]
             assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max(), k
@@ -73,8 +73,22 @@ def test_batch_rebuilds_when_sizes_change(torch):
     b.sample(torch.from_numpy(np.concatenate([p1, p2])).cuda(), [0, 1200, 2100], SEED, 0)
     q2 = p2[:700]
     out = b.sample(torch.from_numpy(np.concatenate([p1, q2])).cuda(), [0, 1200, 1900], SEED, 1).cpu().numpy()
-    s = Sampler(L2, 1.0, xi=0.5, tol=1e-3, system=1)
+    s = Sampler(L2, 1.0, xi=0.5, tol=1e-3, system=1, grid_M=b.plan(1)["M"])
     ref = s.sample(torch.from_numpy(q2).cuda(), SEED, 1).cpu().numpy()
     assert np.abs(out[1200:] - ref).max() <= 1e-5 * np.abs(ref).max()
     s.close()
+    b.close()
+
+
+def test_batch_grids_are_size_classes_at_least_the_plan(torch):
+    from oracle import ewald
+    from paper_1611_09322_gb300 import BatchSampler
+    systems = _systems()
+    Ls = [L for _, L, _ in systems]
+    params = [dict(xi=xi, tol=1e-3) for _, _, xi in systems]
+    b = BatchSampler(Ls, 1.0, params=params)
+    classes = {16, 20, 24, 28, 32, 40, 48, 56, 64, 72, 80, 96, 112, 128, 144, 160, 192, 224, 256}
+    for k, (_, L, xi) in enumerate(systems):
+        M = b.plan(k)["M"]
+        assert M in classes and M >= ewald.plan(L, 1.0, xi, 1e-3).M
     b.close()
