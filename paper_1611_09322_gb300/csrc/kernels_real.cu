@@ -135,8 +135,22 @@ template <typename T> __device__ __forceinline__ Rec<T> load_rec(const Rec<T> *_
     }
 }
 
+// Compact-table lookup (two uniform segments, knot at min(2a, r_cut)); `tab`
+// is normally the block's shared-memory copy.
+template <typename T>
+__device__ __forceinline__ void pair_fg_c(T r, const Geom<T> &g, const V4<T> *tab, T &F, T &GmF) {
+    const T u = r < g.tc_split ? r * g.tc_invA : T(PSE_TABLEC_A) + (r - g.tc_split) * g.tc_invB;
+    int it = (int)u;
+    it = it > PSE_TABLEC_N - 2 ? PSE_TABLEC_N - 2 : it;
+    const T f = u - T(it);
+    const V4<T> tb = tab[it];
+    F = tb.x + f * tb.z;
+    GmF = tb.y + f * tb.w;
+}
+
 // Row s of M_r q without the self term, summed over the TPP-thread group.
-template <typename T, int TPP, int ILP>
+// CT: `table` is the compact table (pair_fg_c), else the uniform one.
+template <typename T, int TPP, int ILP, bool CT = false>
 __device__ __forceinline__ void mr_row_part(int64_t N, int64_t s, int lane_g, bool active, int K, const Geom<T> &g,
                                             const Rec<T> *__restrict__ rec, const int *__restrict__ count,
                                             const int *__restrict__ nbr, const V4<T> *__restrict__ table,
@@ -180,7 +194,8 @@ __device__ __forceinline__ void mr_row_part(int64_t N, int64_t s, int lane_g, bo
                 if constexpr (sizeof(T) == 4) rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
                 else rinv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
                 T F, GmF;
-                pair_fg(r2 * rinv, g, table, F, GmF);
+                if constexpr (CT) pair_fg_c(r2 * rinv, g, table, F, GmF);
+                else pair_fg(r2 * rinv, g, table, F, GmF);
                 const T hx = dx * rinv, hy = dy * rinv, hz = dz * rinv;
                 const T dot = GmF * (hx * rt[u].q.x + hy * rt[u].q.y + hz * rt[u].q.z);
                 ax += F * rt[u].q.x + dot * hx;
@@ -199,7 +214,7 @@ __device__ __forceinline__ void mr_row_part(int64_t N, int64_t s, int lane_g, bo
 
 // Body of one Lanczos matvec over the nblk blocks of one system (bidx = this
 // block's index among them).
-template <typename T, int TPP, int ILP>
+template <typename T, int TPP, int ILP, bool CT>
 __device__ __forceinline__ void lz_matvec_body(int64_t N, int K, const Geom<T> &g, const Rec<T> *__restrict__ rec,
                                                const int *__restrict__ count, const int *__restrict__ nbr,
                                                const V4<T> *__restrict__ table, V4<T> *u, double *partials,
@@ -219,7 +234,7 @@ __device__ __forceinline__ void lz_matvec_body(int64_t N, int K, const Geom<T> &
         const bool active = s < end;
         V4<T> li, qi;
         T ax, ay, az;
-        mr_row_part<T, TPP, ILP>(N, s, lane_g, active, K, g, rec, count, nbr, table, li, qi, ax, ay, az);
+        mr_row_part<T, TPP, ILP, CT>(N, s, lane_g, active, K, g, rec, count, nbr, table, li, qi, ax, ay, az);
         if (active && lane_g == 0) {
             V4<T> o;
             o.x = ax + g.self_m * qi.x;
@@ -251,23 +266,37 @@ __device__ __forceinline__ void lz_matvec_body(int64_t N, int K, const Geom<T> &
     }
 }
 
+// Float contexts stage the compact F, G table (16 KB) in shared memory:
+// table lookups then cost shared-memory wavefronts instead of scattered L1
+// lines.  The FP64 path uses the uniform table (r < 0.2a) and the closed form.
 template <typename T, int TPP, int ILP>
 __global__ void __launch_bounds__(128) k_lz_matvec(int64_t N, int K, Geom<T> g, const Rec<T> *__restrict__ rec,
                                                    const int *__restrict__ count, const int *__restrict__ nbr,
-                                                   const V4<T> *__restrict__ table, V4<T> *u, double *partials,
-                                                   LzState *lz, const float *__restrict__ pc,
-                                                   const V4<T> *__restrict__ basis) {
+                                                   const V4<T> *__restrict__ table, const V4<T> *__restrict__ table_c,
+                                                   V4<T> *u, double *partials, LzState *lz,
+                                                   const float *__restrict__ pc, const V4<T> *__restrict__ basis) {
     __shared__ double sh[32];
-    lz_matvec_body<T, TPP, ILP>(N, K, g, rec, count, nbr, table, u, partials, lz, pc, basis, blockIdx.x, gridDim.x,
-                                sh);
+    if constexpr (sizeof(T) == 4) {
+        __shared__ V4<float> tab_s[PSE_TABLEC_N];
+        for (int i = threadIdx.x; i < PSE_TABLEC_N; i += blockDim.x) tab_s[i] = table_c[i];
+        __syncthreads();
+        lz_matvec_body<T, TPP, ILP, true>(N, K, g, rec, count, nbr, tab_s, u, partials, lz, pc, basis, blockIdx.x,
+                                          gridDim.x, sh);
+    } else {
+        lz_matvec_body<T, TPP, ILP, false>(N, K, g, rec, count, nbr, table, u, partials, lz, pc, basis, blockIdx.x,
+                                           gridDim.x, sh);
+    }
 }
 
 // Fused over the systems of a batch: block b works for system blk2sys[b].
 __global__ void __launch_bounds__(128) k_lz_matvec_batch(const LzSys *__restrict__ sys, const int *__restrict__ blk2sys) {
     __shared__ double sh[32];
+    __shared__ V4<float> tab_s[PSE_TABLEC_N];
     const LzSys &S = sys[blk2sys[blockIdx.x]];
-    lz_matvec_body<float, PSE_BATCH_MV_TPP, 4>(S.N, S.K, S.g, S.rec, S.count, S.nbr, S.table, S.u, S.part_mv, S.lz,
-                                               S.pc, S.basis, blockIdx.x - S.blk_mv, S.nblk_mv, sh);
+    for (int i = threadIdx.x; i < PSE_TABLEC_N; i += blockDim.x) tab_s[i] = S.table_c[i];
+    __syncthreads();
+    lz_matvec_body<float, PSE_BATCH_MV_TPP, 4, true>(S.N, S.K, S.g, S.rec, S.count, S.nbr, tab_s, S.u, S.part_mv,
+                                                     S.lz, S.pc, S.basis, blockIdx.x - S.blk_mv, S.nblk_mv, sh);
 }
 
 template <typename T>
@@ -369,16 +398,17 @@ __device__ __forceinline__ void lz_eig_body(LzState *lz, int max_iter, int fixed
                 if (fabs(e[m]) <= eps * dd) break;
             }
             if (m == l) break;
-            // shift from the leading 2x2 block
+            // shift from the leading 2x2 block (entries are O(mobility), far
+            // from overflow, so plain square roots replace hypot)
             double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-            double r = hypot(g, 1.0);
+            double r = sqrt(fma(g, g, 1.0));
             g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
             double s = 1.0, c = 1.0, p = 0.0;
             int i = m - 1;
             bool deflated = false;
             for (; i >= l; --i) {
                 const double f = s * e[i], b = c * e[i];
-                r = hypot(f, g);
+                r = sqrt(fma(f, f, g * g));
                 __syncwarp();
                 if (lane == 0) e[i + 1] = r;
                 __syncwarp();
@@ -388,8 +418,9 @@ __device__ __forceinline__ void lz_eig_body(LzState *lz, int max_iter, int fixed
                     deflated = true;
                     break;
                 }
-                s = f / r;
-                c = g / r;
+                const double rinv = 1.0 / r;  // one division per rotation
+                s = f * rinv;
+                c = g * rinv;
                 g = d[i + 1] - p;
                 r = (d[i] - g) * s + 2.0 * c * b;
                 p = s * r;
@@ -640,7 +671,7 @@ void launch_lz_init(int64_t N, const SampleArgs<T> *args, int system, const Dev<
 // selected by Geom::mv; the sampler may time them all and keep the fastest.
 template <typename T, int TPP, int ILP> void mv_launch(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
     k_lz_matvec<T, TPP, ILP><<<pgrid(N, 128 / TPP, 16), 128, 0, s>>>(
-        N, nbr_k(N, d.nbr_cap), g, d.rec, d.nbr_count, d.nbr, d.table, d.u, d.partials, d.lz,
+        N, nbr_k(N, d.nbr_cap), g, d.rec, d.nbr_count, d.nbr, d.table, d.table_c, d.u, d.partials, d.lz,
         sizeof(T) == 4 ? d.pc_on : nullptr, d.basis);
 }
 template <typename T> void launch_lz_matvec(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {

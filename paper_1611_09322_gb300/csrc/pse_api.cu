@@ -137,6 +137,10 @@ template <typename T> void fill_geom(pse_ctx *c) {
     g.inv_cs = (T)(p.ncell / p.L);
     g.rc2 = (T)(p.r_cut * p.r_cut);
     g.tab_inv_dr = (T)((PSE_TABLE_N - 1) / p.r_cut);
+    const double split = 2 * p.a < p.r_cut ? 2 * p.a : p.r_cut;
+    g.tc_split = (T)split;
+    g.tc_invA = (T)(PSE_TABLEC_A / split);
+    g.tc_invB = (T)((PSE_TABLEC_N - 1 - PSE_TABLEC_A) / (p.r_cut - split > 0 ? p.r_cut - split : 1.0));
     g.self_m = (T)p.self_mobility;
     g.a = (T)p.a;
     g.xi = (T)p.xi;
@@ -186,6 +190,28 @@ template <typename T> pse_status init_ctx(pse_ctx *c) {
     pse_status st;
     if ((st = alloc(c->per_ctx, (void **)&d.table, sizeof(V4<T>) * PSE_TABLE_N)) != PSE_OK) return st;
     CK(cudaMemcpy(d.table, tab.data(), sizeof(V4<T>) * PSE_TABLE_N, cudaMemcpyHostToDevice));
+    {  // compact two-segment table for the shared-memory matvec
+        const double split = 2 * p.a < p.r_cut ? 2 * p.a : p.r_cut;
+        const double dA = split / PSE_TABLEC_A;
+        const double dB = (p.r_cut - split > 0 ? p.r_cut - split : 1.0) / (PSE_TABLEC_N - 1 - PSE_TABLEC_A);
+        std::vector<double> Fc(PSE_TABLEC_N), Gc(PSE_TABLEC_N);
+        for (int i = 0; i < PSE_TABLEC_N; ++i) {
+            const double r = i <= PSE_TABLEC_A ? i * dA : split + (i - PSE_TABLEC_A) * dB;
+            fg_at(r, p.xi, p.a, &Fc[i], &Gc[i]);
+        }
+        std::vector<V4<T>> tc(PSE_TABLEC_N);
+        for (int i = 0; i < PSE_TABLEC_N; ++i) {
+            const double f0 = Fc[i] * s, g0 = (Gc[i] - Fc[i]) * s;
+            const double f1 = (i + 1 < PSE_TABLEC_N) ? Fc[i + 1] * s : f0;
+            const double g1 = (i + 1 < PSE_TABLEC_N) ? (Gc[i + 1] - Fc[i + 1]) * s : g0;
+            tc[i].x = (T)f0;
+            tc[i].y = (T)g0;
+            tc[i].z = (T)(f1 - f0);
+            tc[i].w = (T)(g1 - g0);
+        }
+        if ((st = alloc(c->per_ctx, (void **)&d.table_c, sizeof(V4<T>) * PSE_TABLEC_N)) != PSE_OK) return st;
+        CK(cudaMemcpy(d.table_c, tc.data(), sizeof(V4<T>) * PSE_TABLEC_N, cudaMemcpyHostToDevice));
+    }
     const int64_t M = p.M, plane = M * M * (M / 2 + 1);
     const size_t csize = sizeof(T) * 2;
     if ((st = alloc(c->per_ctx, &d.spec, csize * 3 * plane)) != PSE_OK) return st;
@@ -1324,6 +1350,7 @@ static pse_status batch_descriptors(pse_batch *b) {
         d.count = c->df.nbr_count;
         d.nbr = c->df.nbr;
         d.table = c->df.table;
+        d.table_c = c->df.table_c;
         d.u = c->df.u;
         d.part_mv = c->df.partials;
         d.part_up = c->df.partials + num_sms() * 16 + 32;

@@ -10,6 +10,8 @@
 
 #define PSE_MAXIT 64          // Lanczos cap (basis holds PSE_MAXIT + 2 vectors)
 #define PSE_TABLE_N 4096      // entries of the F, G table on [0, r_cut]
+#define PSE_TABLEC_N 1024     // entries of the compact table the Lanczos matvec stages in shared memory
+#define PSE_TABLEC_A 256      // of which on [0, 2a): knots at 2a, where F and G have a kink
 #define PSE_SCAN_ITEMS 4096   // elements per block of the device scan
 #define PSE_MAX_SCAN (PSE_SCAN_ITEMS * PSE_SCAN_ITEMS)
 
@@ -63,6 +65,9 @@ template <typename T> struct Geom {
     int nc;       // cells per side
     int nb;       // bricks per side (4x4x4 cells each)
     int mv;       // matvec launch shape (0: 4 threads x 4 gathers per particle, 1: 8 x 2, 2: 16 x 1, 3: 4 x 2)
+    // compact table: PSE_TABLEC_A uniform knots on [0, tc_split), the rest
+    // uniform on [tc_split, r_cut]; tc_split = min(2a, r_cut)
+    T tc_split, tc_invA, tc_invB;
 };
 #define PSE_MV_VARIANTS 4
 
@@ -308,6 +313,7 @@ template <typename T> struct Dev {
     double *partials;    // per-block partial sums
     LzState *lz;
     V4<T> *table;        // PSE_TABLE_N: (F, G - F, dF, d(G-F)) / (6 pi a)
+    V4<T> *table_c;      // PSE_TABLEC_N, same columns, on the two-segment knots
     void *spec;          // 3 * M * M * Mh1 complex
     T *grid;             // 3 * M^3 real
     SampleArgs<T> *args;
@@ -357,6 +363,7 @@ struct LzSys {
     const int *count;
     const int *nbr;
     const V4<float> *table;
+    const V4<float> *table_c;    // compact table (staged in shared memory by the matvec)
     V4<float> *u;
     double *part_mv, *part_up;   // per-block partial sums of the matvec and the update
     LzState *lz;
@@ -436,6 +443,7 @@ __device__ __forceinline__ void sym3_apply(const float *M, float x, float y, flo
 
 // host-side setup (FP64 arithmetic)
 void build_fg_table(double r_cut, double xi, double a, int n, double *F, double *G);
+void fg_at(double r, double xi, double a, double *F, double *G);
 double self_real(double xi, double a);
 
 }  // namespace pse

@@ -54,6 +54,17 @@ static void fg_small(double r, double xi, double a, double *F, double *G) {
     *G = A + B - Gw;
 }
 
+// F, G at one separation (the same branches as the tables below).
+void fg_at(double r, double xi, double a, double *F, double *G) {
+    if (r <= 0.0) {
+        *F = *G = self_real(xi, a);
+    } else if (r < 0.2 * a) {
+        fg_small(r, xi, a, F, G);
+    } else {
+        fg_closed(r, xi, a, F, G);
+    }
+}
+
 void build_fg_table(double r_cut, double xi, double a, int n, double *F, double *G) {
     const double dr = r_cut / (n - 1);
     for (int i = 0; i < n; ++i) {
