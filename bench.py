@@ -97,8 +97,8 @@ def clocks_stop(p, f, device_index=0):
 # at this workload, valid only while the kernel's sources hash to the value
 # recorded with it (profiles/ holds the capture's summary).
 TRAFFIC = {
-    "k_lz_matvec": (112_879_616 + 9_083_392, ("csrc/kernels_real.cu", "csrc/pse_internal.cuh"),
-                    "248da13847137d584824edd3076095339af4aeb00aeb6fa79d6c3ce790aaeef6"),
+    "k_lz_matvec": (145_776_896 + 11_379_712, ("csrc/kernels_real.cu",),
+                    "084eb80f9487e96342d36ab78a6b2567faad9d37046d9d58a2bfd2063bc88ede"),
 }
 
 
@@ -209,7 +209,7 @@ def variants_learned_batched(dev, flush, stream, steps):
     d = torch.from_numpy(pos).to(dev)
     o = torch.empty_like(d)
     for name, th in (("plain_N1e6", None), ("learned_N1e6", theta)):
-        s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=5)
+        s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=1)
         if th is not None:
             s.precond_set_weights(th)
         for i in range(3):
@@ -224,7 +224,7 @@ def variants_learned_batched(dev, flush, stream, steps):
     # dt M F + sqrt(2 dt) M^{1/2} z (kT = 1, dt = 1e-3), and the plain sample
     # with the wave noise drawn on the grid
     F = torch.randn(d.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(3))
-    s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=7)
+    s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=3)
     runs = (("mobility_apply_N1e6", lambda i: s.sample_with_forces(d, F, 1, 400 + i, 1.0, 0.0, out=o)),
             ("euler_maruyama_N1e6", lambda i: s.sample_with_forces(d, F, 1, 500 + i, 1e-3, math.sqrt(2e-3), out=o)))
     for name, fn in runs:
@@ -234,7 +234,7 @@ def variants_learned_batched(dev, flush, stream, steps):
         out[name] = {"value": N_PART * steps / (sum(per) / 1e3), "ms_per_step": sum(per) / steps}
     out["euler_maruyama_N1e6"]["lanczos_iters"] = s.stats()["lanczos_iters"]
     s.close()
-    s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=5, wave_noise=1)
+    s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=1, wave_noise=1)
     for i in range(3):
         s.sample(d, 1, i, out=o)
     per = timed_steps(lambda i: s.sample(d, 1, 600 + i, out=o), steps, flush, stream)
@@ -278,6 +278,51 @@ def _lib_set(batch, k, theta):
                "pse_batch_set_precond")
 
 
+def run_only(args):
+    """One secondary workload alone (for profiling its kernels): the
+    deterministic product M F at N = 1e6 ("forces") or the 64-system batch
+    ("batch"); --no-graph launches the same kernels without a CUDA graph so
+    that a profiler sees every kernel.  Prints one JSON line."""
+    import numpy as np
+    import torch
+    from paper_1611_09322_gb300 import BatchSampler, Sampler, workloads
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    graph = not args.no_graph
+    if args.only == "forces":
+        pos, L, _ = workloads.hard_spheres(N_PART, PHI, SEED_POS)
+        d = torch.from_numpy(pos).to(dev)
+        F = torch.randn(d.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(3))
+        o = torch.empty_like(d)
+        s = Sampler(L, 1.0, xi=XI, tol=TOL, use_graph=graph, spread_tile=4)
+        for i in range(args.warmup):
+            s.mobility_apply(d, F, out=o)
+        per = timed_steps(lambda i: s.mobility_apply(d, F, out=o), args.steps, flush, stream)
+        n, variant = N_PART, "deterministic M F, N=1e6 hard spheres, phi=0.1, tiles of 4^3 cells"
+        s.close()
+    else:
+        spec = workloads.batch_spec()
+        pos_list, Ls = [], []
+        for sp in spec:
+            p, Lk, _ = workloads.make(sp["kind"], sp["N"], sp["phi"], sp["seed"])
+            pos_list.append(p)
+            Ls.append(Lk)
+        offsets = np.cumsum([0] + [p.shape[0] for p in pos_list])
+        pa = torch.from_numpy(np.concatenate(pos_list)).to(dev)
+        po = torch.empty_like(pa)
+        b = BatchSampler(Ls, 1.0, xi=XI, tol=TOL, use_graph=graph)
+        for i in range(args.warmup):
+            b.sample(pa, offsets, 1, i, out=po)
+        per = timed_steps(lambda i: b.sample(pa, offsets, 1, 100 + i, out=po), args.steps, flush, stream)
+        n, variant = int(offsets[-1]), "64-system batch (N log-uniform in [1e3, 5e4], phi in [0.05, 0.4], half gels)"
+        b.close()
+    print(json.dumps({"only": args.only, "variant": variant, "graph": graph, "steps": args.steps,
+                      "ms_per_step": sum(per) / args.steps, "value": n * args.steps / (sum(per) / 1e3),
+                      "unit": UNIT}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -286,11 +331,16 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--only", choices=["forces", "batch"], default=None,
+                    help="run one secondary workload alone (profiling aid)")
+    ap.add_argument("--no-graph", action="store_true", help="with --only: launch without CUDA graphs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
 
     import torch
     import torch.distributed as dist
@@ -304,7 +354,7 @@ def main():
     torch.cuda.set_device(dev)
 
     pos, L, _ = workloads.hard_spheres(N_PART, PHI, SEED_POS)
-    s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=5)
+    s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=1)
     d_pos = torch.from_numpy(pos).to(dev)
     out = torch.empty_like(d_pos)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)

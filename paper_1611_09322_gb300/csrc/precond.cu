@@ -416,6 +416,29 @@ void launch_pc_blocks_caller(int64_t N, const Dev<float> &d, float *S, cudaStrea
     k_pc_blocks_caller<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, d.pc, d.pos_sorted, S);
 }
 
+// Fused over the systems of a batch that have the network installed (only
+// those get blocks in the table).
+__global__ void __launch_bounds__(128) k_pc_infer_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
+    __shared__ float th[kPcNParam];
+    const BSys &S = sys[tab[blockIdx.x]];
+    for (int i = threadIdx.x; i < kPcNParam; i += blockDim.x) th[i] = S.d.pc_theta[i];
+    __syncthreads();
+    const int64_t s = ((int64_t)blockIdx.x - S.b0[BK_PC]) * blockDim.x + threadIdx.x;
+    if (s >= S.N) return;
+    float f[kPcIn], Tm[6], h1[kPcH], h2[kPcH], o[2], Sb[6], R[6];
+    pc_features(S.N, s, S.g, S.d.rec, S.d.nbr_count, S.d.nbr, f, Tm);
+    pc_mlp(th, f, h1, h2, o);
+    pc_block(S.pc_s0, o[0], o[1], Tm, Sb);
+    sym3_inv(Sb, R);
+    float *dst = S.d.pc + s * 16;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { dst[i] = Sb[i]; dst[8 + i] = R[i]; }
+    dst[6] = dst[7] = dst[14] = dst[15] = 0.f;
+}
+void launch_batch_pc_infer(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s) {
+    if (nblk[BK_PC] > 0) k_pc_infer_batch<<<nblk[BK_PC], 128, 0, s>>>(sys, tab[BK_PC]);
+}
+
 void launch_pc_infer(int64_t N, Geom<float> g, const Dev<float> &d, const float *theta, float s0, float *pc,
                      cudaStream_t s) {
     k_pc_infer<<<(unsigned)((N + 127) / 128), 128, 0, s>>>(N, g, d.rec, d.nbr_count, d.nbr, theta, s0, pc);

@@ -375,13 +375,14 @@ struct LzSys {
 // One system of a batch for the fused prologue / epilogue kernels (FP32):
 // sizes, geometry, buffers and, per fused kernel kind, the first block and
 // block count it owns (block -> system tables map the other way).
-enum { BK_ZERO = 0, BK_BIN, BK_SCATTER, BK_SORT, BK_NBR, BK_INIT, BK_NOISE, BK_INTERP, BK_FINAL, PSE_BK };
+enum { BK_ZERO = 0, BK_BIN, BK_SCATTER, BK_SORT, BK_NBR, BK_INIT, BK_NOISE, BK_INTERP, BK_FINAL, BK_PC, PSE_BK };
 #define PSE_BATCH_INTERP_G 16
 struct BSys {
     int64_t N;
     int nc3;        // cell slots
     int system;     // Philox stream pair
     int K;          // ELL capacity per particle
+    float pc_s0;    // self-mobility^{-1/2} (learned preconditioner)
     Geom<float> g;
     WaveGeom<float> w;
     Dev<float> d;
@@ -393,6 +394,7 @@ void launch_batch_init(const BSys *sys, int *const *tab, const int *nblk, cudaSt
 void launch_batch_final(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s);
 void launch_batch_noise(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s);
 void launch_batch_interp(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s);
+void launch_batch_pc_infer(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s);
 void launch_lz_matvec_batch(const LzSys *sys, const int *blk2sys, int nblocks, cudaStream_t s);
 void launch_lz_update_batch(const LzSys *sys, const int *blk2sys, int nblocks, cudaStream_t s);
 void launch_lz_eig_batch(const LzSys *sys, int nsys, cudaStream_t s);
