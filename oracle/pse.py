@@ -316,6 +316,36 @@ def sample_with_forces(pos, F, plan, seed, sample, c_det=1.0, c_noise=1.0, n_ite
     return out, j
 
 
+# ----------------------------------------------------------------------------- Brownian dynamics
+
+def repulsion_forces(pos, L, a, k_rep):
+    """Harmonic overlap repulsion F_i = k_rep sum_j (2a - r_ij) rhat_ij over the
+    pairs closer than 2a (minimum image), rhat_ij pointing from j to i."""
+    pos = np.asarray(pos, dtype=np.float64)
+    F = np.zeros_like(pos)
+    i, j, d = pair_list(pos, L, 2 * a * (1 - 1e-12))
+    if i.size:
+        r = np.linalg.norm(d, axis=1)
+        f = (k_rep * (2 * a - r) / r)[:, None] * d
+        np.add.at(F, i, f)
+        np.add.at(F, j, -f)
+    return F
+
+
+def bd_step(pos, plan, seed, step, dt, kT, k_rep, f_ext=None, n_iter=None, system=0):
+    """One Euler-Maruyama step of Brownian dynamics (Sec. II, eq. for dx):
+    x + dt M F + sqrt(2 kT dt) M^{1/2} z, F = overlap repulsion (+ f_ext), the
+    noise of (seed, step); the new positions are wrapped into [0, L).
+    Returns (new positions, displacement, j_lanczos)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    F = repulsion_forces(pos, plan.L, plan.a, k_rep)
+    if f_ext is not None:
+        F = F + np.asarray(f_ext, dtype=np.float64).reshape(-1, 3)
+    dx, j = sample_with_forces(pos, F, plan, seed, step, c_det=dt, c_noise=math.sqrt(2 * kT * dt),
+                               n_iter=n_iter, system=system)
+    return np.mod(pos + dx, plan.L), dx, j
+
+
 # ----------------------------------------------------------------------------- real part
 
 def pair_list(pos, L, rc):

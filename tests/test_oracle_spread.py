@@ -127,3 +127,32 @@ def test_sample_with_forces_without_noise_is_the_mobility_product():
     out, j = pse.sample_with_forces(pos, F, plan, 1, 2, c_det=2.5, c_noise=0.0)
     assert j == 0
     assert np.allclose(out, 2.5 * pse.mobility_apply(F, pos, plan), rtol=1e-13, atol=1e-15)
+
+
+def test_repulsion_forces_pair_and_momentum():
+    """Two overlapping spheres: equal and opposite forces along the line of
+    centres, magnitude k (2a - r); a many-body packing: sum of forces 0, and a
+    pair just outside contact feels nothing; across the periodic boundary."""
+    L = 20.0
+    pos = np.array([[0.5, 5.0, 5.0], [19.7, 5.3, 5.0]])  # separated by 0.8, 0.3 through the boundary
+    F = pse.repulsion_forces(pos, L, 1.0, 10.0)
+    d = np.array([0.5 - (19.7 - 20.0), 5.0 - 5.3, 0.0])
+    r = np.linalg.norm(d)
+    assert np.allclose(F[0], 10.0 * (2 - r) * d / r, rtol=1e-14)
+    assert np.allclose(F[1], -F[0], rtol=1e-14)
+    far = pse.repulsion_forces(np.array([[1.0, 1.0, 1.0], [3.0001, 1.0, 1.0]]), L, 1.0, 10.0)
+    assert np.all(far == 0)
+    rng = np.random.default_rng(3)
+    many = rng.uniform(0, L, (300, 3))
+    Fm = pse.repulsion_forces(many, L, 1.0, 5.0)
+    assert np.abs(Fm.sum(axis=0)).max() < 1e-10 * np.abs(Fm).max()
+
+
+def test_bd_step_without_noise_is_the_mobility_product():
+    pos, L = _hs(200, 0.3, 21)
+    plan = ewald.plan(L, 1.0, 0.5, 1e-3)
+    new, dx, j = pse.bd_step(pos, plan, 1, 2, dt=1e-3, kT=0.0, k_rep=100.0)
+    F = pse.repulsion_forces(pos, L, 1.0, 100.0)
+    assert j == 0
+    assert np.allclose(dx, 1e-3 * pse.mobility_apply(F, pos, plan), rtol=1e-12, atol=1e-16)
+    assert np.allclose(new, np.mod(pos + dx, L))
