@@ -233,6 +233,15 @@ def variants_learned_batched(dev, flush, stream, steps):
         per = timed_steps(fn, steps, flush, stream)
         out[name] = {"value": N_PART * steps / (sum(per) / 1e3), "ms_per_step": sum(per) / steps}
     out["euler_maruyama_N1e6"]["lanczos_iters"] = s.stats()["lanczos_iters"]
+    # a whole Brownian dynamics step: neighbour list, overlap repulsion
+    # (k_rep = 100), the fused displacement and the position update, in place
+    x = d.clone()
+    bd = lambda i: s.bd_step(x, 1, 700 + i, 1e-3, 1.0, 100.0)  # noqa: E731
+    for i in range(3):
+        bd(i)
+    per = timed_steps(bd, steps, flush, stream)
+    out["bd_step_N1e6"] = {"value": N_PART * steps / (sum(per) / 1e3), "ms_per_step": sum(per) / steps,
+                           "lanczos_iters": s.stats()["lanczos_iters"]}
     s.close()
     s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=1, wave_noise=1)
     for i in range(3):

@@ -206,6 +206,25 @@ pse_status pse_sample_with_forces_f64(pse_ctx *ctx, int64_t N, const double *d_p
                                       uint64_t seed, uint64_t sample_index, double c_det, double c_noise,
                                       double *d_out, void *stream);
 
+/* One Euler-Maruyama step of Brownian dynamics (Sec. II B, eq. langevin with
+ * div M = 0 in a periodic box), positions updated in place:
+ *   d_pos <- wrap(d_pos + dt M F + sqrt(2 kT dt) M^{1/2} z),
+ * F_i = k_rep sum_j (2a - r_ij) rhat_ij over the pairs closer than 2a (a
+ * harmonic overlap repulsion, computed from the neighbour list in the same
+ * graph) plus d_fext (3N float32, device, caller order; NULL for none); the
+ * noise is that of (seed, step).  kT = 0 gives the deterministic step.
+ * dt, kT, k_rep >= 0.  One graph launch per step; the neighbour list and the
+ * forces follow the positions of the step.  Contexts with wave_noise = 1
+ * need kT = 0, and k_rep > 0 needs r_cut >= 2a so that the neighbour list
+ * holds every contact (PSE_ENOTSUPPORTED otherwise); PSE_EINVAL for a
+ * negative or non-finite dt, kT or k_rep. */
+pse_status pse_bd_step(pse_ctx *ctx, int64_t N, float *d_pos, const float *d_fext, double dt, double kT,
+                       double k_rep, uint64_t seed, uint64_t step, void *stream);
+
+/* FP64 context form of pse_bd_step. */
+pse_status pse_bd_step_f64(pse_ctx *ctx, int64_t N, double *d_pos, const double *d_fext, double dt, double kT,
+                           double k_rep, uint64_t seed, uint64_t step, void *stream);
+
 /* The deterministic product d_out = M d_force alone (pse_sample_with_forces
  * with c_det = 1, c_noise = 0), FP32 context. */
 pse_status pse_mobility_apply(pse_ctx *ctx, int64_t N, const float *d_pos, const float *d_force, float *d_out,
@@ -291,33 +310,6 @@ enum {
  * The output equals pse_sample's for the same arguments. */
 pse_status pse_profile_stages(pse_ctx *ctx, int64_t N, const float *d_pos, uint64_t seed,
                               uint64_t sample_index, float *d_out, double *ms, int *launches,
-                              void *stream);
-
-/* One Euler-Maruyama displacement's two parts in one call (Sec. III: the
- * deterministic and Brownian wave parts share one inverse FFT):
- *   d_out = c_det M F + c_noise M^{1/2} z,
- * M F = M_r F (sparse, eq. Mreal) + M_w F (spread F with the Gaussian, forward
- * FFT, per mode h^3 B(k) (I - kk) with B from eq. Mwave and the Gaussian
- * deconvolution, inverse FFT, interpolate), M^{1/2} z as in pse_sample with
- * the same (seed, sample_index) noise.  c_noise = 0 skips the Lanczos loop
- * and the noise (the deterministic product alone); for a Brownian step take
- * c_det = dt and c_noise = sqrt(2 kT dt).  d_pos, d_force, d_out: 3N float32
- * device arrays in the caller's order (d_out may not alias the inputs).
- * Contexts with wave_noise = 1 support only c_noise = 0 here
- * (PSE_ENOTSUPPORTED otherwise).  The spreading uses float atomics, so the
- * last bits of M F may differ from call to call. */
-pse_status pse_sample_with_forces(pse_ctx *ctx, int64_t N, const float *d_pos, const float *d_force,
-                                  uint64_t seed, uint64_t sample_index, double c_det, double c_noise,
-                                  float *d_out, void *stream);
-
-/* FP64 context form of pse_sample_with_forces (float64 arrays). */
-pse_status pse_sample_with_forces_f64(pse_ctx *ctx, int64_t N, const double *d_pos, const double *d_force,
-                                      uint64_t seed, uint64_t sample_index, double c_det, double c_noise,
-                                      double *d_out, void *stream);
-
-/* The deterministic product d_out = M d_force alone (pse_sample_with_forces
- * with c_det = 1, c_noise = 0), FP32 context. */
-pse_status pse_mobility_apply(pse_ctx *ctx, int64_t N, const float *d_pos, const float *d_force, float *d_out,
                               void *stream);
 
 /* Near-field product d_out = M_r d_v, like pse_real_matvec, for callers that

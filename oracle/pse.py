@@ -333,7 +333,7 @@ def repulsion_forces(pos, L, a, k_rep):
 
 
 def bd_step(pos, plan, seed, step, dt, kT, k_rep, f_ext=None, n_iter=None, system=0):
-    """One Euler-Maruyama step of Brownian dynamics (Sec. II, eq. for dx):
+    """One Euler-Maruyama step of Brownian dynamics (Sec. II B, eq. langevin, div M = 0 in a periodic box):
     x + dt M F + sqrt(2 kT dt) M^{1/2} z, F = overlap repulsion (+ f_ext), the
     noise of (seed, step); the new positions are wrapped into [0, L).
     Returns (new positions, displacement, j_lanczos)."""

@@ -193,6 +193,16 @@ class Sampler:
                       float(c_noise), _ptr(out), _stream()), "pse_sample_with_forces")
         return out
 
+    def bd_step(self, pos, seed, step, dt, kT=1.0, k_rep=0.0, f_ext=None):
+        """One Euler-Maruyama step in place: pos += dt M F + sqrt(2 kT dt) M^{1/2} z (pse_bd_step)."""
+        self._check_pos(pos)
+        if f_ext is not None and (f_ext.dtype != pos.dtype or f_ext.shape != pos.shape or not f_ext.is_cuda):
+            raise ValueError("f_ext must be a CUDA tensor shaped and typed like pos")
+        fn = self.lib.pse_bd_step_f64 if self.fp64 else self.lib.pse_bd_step
+        _lib.check(fn(self.ctx, pos.shape[0], _ptr(pos), _ptr(f_ext), float(dt), float(kT), float(k_rep), seed, step,
+                      _stream()), "pse_bd_step")
+        return pos
+
     def mobility_apply(self, pos, force, out=None):
         """The deterministic product M F (c_det = 1, c_noise = 0)."""
         return self.sample_with_forces(pos, force, 0, 0, 1.0, 0.0, out=out)

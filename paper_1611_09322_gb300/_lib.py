@@ -76,6 +76,9 @@ SIGNATURES = {
     "pse_sample_with_forces_f64": (_ST, [_VP, _I64, _VP, _VP, _U64, _U64, ctypes.c_double, ctypes.c_double, _VP,
                                          _VP]),
     "pse_mobility_apply": (_ST, [_VP, _I64, _VP, _VP, _VP, _VP]),
+    "pse_bd_step": (_ST, [_VP, _I64, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, _U64, _U64, _VP]),
+    "pse_bd_step_f64": (_ST, [_VP, _I64, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, _U64, _U64,
+                              _VP]),
     "pse_get_stats": (_ST, [_VP, ctypes.POINTER(pse_stats)]),
     "pse_strerror": (ctypes.c_char_p, [_ST]),
     "pse_profile_stages": (_ST, [_VP, _I64, _VP, _U64, _U64, _VP, _VP, _VP, _VP]),

@@ -19,6 +19,15 @@
 
 namespace pse {
 
+template <typename T> __device__ __forceinline__ T sqrt_hd(T x) {
+    if constexpr (sizeof(T) == 4) return sqrtf(x);
+    else return sqrt(x);
+}
+template <typename T> __device__ __forceinline__ T floor_hd(T x) {
+    if constexpr (sizeof(T) == 4) return floorf(x);
+    else return floor(x);
+}
+
 template <typename T> __device__ __forceinline__ long long w_bits_r(T w) {
     if constexpr (sizeof(T) == 4) return (long long)__float_as_int(w);
     else return __double_as_longlong(w);
@@ -601,6 +610,57 @@ __global__ void k_det_final(int64_t N, const SampleArgs<T> *args, const V4<T> *p
     args->out[o + 2] = cd * m.z + w.z;
 }
 
+// ------------------------------------------------------------------ Brownian dynamics step
+// Overlap repulsion F_s = k_rep sum_t (2a - r) rhat over the list entries of
+// s closer than 2a (pair vectors from cell-local offsets, as in the matvec),
+// plus the external force, written in caller order.
+template <typename T>
+__global__ void k_repulsion(int64_t N, Geom<T> g, const SampleArgs<T> *args, const Rec<T> *__restrict__ rec,
+                            const int *__restrict__ count, const int *__restrict__ nbr,
+                            const V4<T> *__restrict__ pos_sorted, T *F) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const V4<T> li = rec[s].l;
+    const T two_a = T(2) * g.a, k = (T)args->k_rep;
+    T fx = 0, fy = 0, fz = 0;
+    const int cnt = count[s];
+    for (int q = 0; q < cnt; ++q) {
+        const int e = nbr[(int64_t)q * N + s];
+        const V4<T> lt = rec[e >> 6].l;
+        const int ox = ((e >> 4) & 3) - 1, oy = ((e >> 2) & 3) - 1, oz = (e & 3) - 1;
+        const T dx = (li.x - lt.x) - (T(ox) * g.cs + T(ox) * g.cs_lo);
+        const T dy = (li.y - lt.y) - (T(oy) * g.cs + T(oy) * g.cs_lo);
+        const T dz = (li.z - lt.z) - (T(oz) * g.cs + T(oz) * g.cs_lo);
+        const T r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < two_a * two_a && r2 > T(0)) {
+            const T r = sqrt_hd(r2);
+            const T f = k * (two_a - r) / r;
+            fx += f * dx;
+            fy += f * dy;
+            fz += f * dz;
+        }
+    }
+    const int64_t o = 3 * w_bits_r(pos_sorted[s].w);
+    if (args->fext) {
+        fx += args->fext[o];
+        fy += args->fext[o + 1];
+        fz += args->fext[o + 2];
+    }
+    F[o] = fx;
+    F[o + 1] = fy;
+    F[o + 2] = fz;
+}
+
+// x <- x + dx, wrapped into [0, L) (caller order).
+template <typename T> __global__ void k_advance(int64_t N, Geom<T> g, const SampleArgs<T> *args) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= 3 * N || !args->advance) return;
+    T x = args->advance[i] + args->out[i];
+    x -= g.L * floor_hd(x / g.L);
+    if (x >= g.L || x < T(0)) x = T(0);
+    args->advance[i] = x;
+}
+
 // ------------------------------------------------------------------ caller-vector matvec
 template <typename T>
 __global__ void k_gather_vec(int64_t N, const SampleArgs<T> *args, const V4<T> *pos_sorted, Rec<T> *rec) {
@@ -716,6 +776,12 @@ void launch_lz_final_forces(int64_t N, const SampleArgs<T> *args, const Dev<T> &
     k_lz_final<T><<<nb(N, 256), 256, 0, s>>>(N, args, d.pos_sorted, d.basis, d.uwave, d.lz, true,
                                              sizeof(T) == 4 ? d.pc_on : nullptr, d.udet);
 }
+template <typename T> void launch_repulsion(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
+    k_repulsion<T><<<nb(N, 128), 128, 0, s>>>(N, g, d.args, d.rec, d.nbr_count, d.nbr, d.pos_sorted, d.bd_force);
+}
+template <typename T> void launch_advance(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
+    k_advance<T><<<nb(3 * N, 256), 256, 0, s>>>(N, g, d.args);
+}
 template <typename T> void launch_det_final(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, cudaStream_t s) {
     k_det_final<T><<<nb(N, 256), 256, 0, s>>>(N, args, d.pos_sorted, d.udet, d.uwave);
 }
@@ -741,6 +807,8 @@ void launch_matvec_caller(int64_t N, const SampleArgs<T> *args, Geom<T> g, const
     template void launch_lz_final<T>(int64_t, const SampleArgs<T> *, const Dev<T> &, bool, cudaStream_t);    \
     template void launch_lz_final_forces<T>(int64_t, const SampleArgs<T> *, const Dev<T> &, cudaStream_t);   \
     template void launch_det_final<T>(int64_t, const SampleArgs<T> *, const Dev<T> &, cudaStream_t);         \
+    template void launch_repulsion<T>(int64_t, Geom<T>, const Dev<T> &, cudaStream_t);                       \
+    template void launch_advance<T>(int64_t, Geom<T>, const Dev<T> &, cudaStream_t);                         \
     template void launch_gather_vec<T>(int64_t, const SampleArgs<T> *, const Dev<T> &, cudaStream_t);        \
     template void launch_matvec_sorted<T>(int64_t, Geom<T>, const Dev<T> &, cudaStream_t);                   \
     template void launch_matvec_caller<T>(int64_t, const SampleArgs<T> *, Geom<T>, const Dev<T> &, cudaStream_t);

@@ -41,9 +41,9 @@ struct pse_ctx {
     bool fft_made = false;
     cudaStream_t s_main = nullptr, s_wave = nullptr, s_body = nullptr, s_body2 = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};  // per graph mode (GM_*)
-    cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
-    cudaGraphConditionalHandle cond[3] = {0, 0, 0};
+    cudaGraph_t graph[5] = {};            // per graph mode (GM_*)
+    cudaGraphExec_t exec[5] = {};
+    cudaGraphConditionalHandle cond[5] = {};
     cufftHandle fft_r2c = 0;                            // forward FFT (spreading / grid noise)
     bool r2c_made = false;
     SpreadTile spread{};                                // spreading tile shape
@@ -115,11 +115,15 @@ void free_list(std::vector<void *> &list) {
     list.clear();
 }
 
-// Graph modes: a plain sample, the forces path with noise, without noise.
-enum { GM_SAMPLE = 0, GM_FORCES_NOISE = 1, GM_FORCES = 2 };
+// Graph modes: a plain sample; the forces path with and without noise; a
+// Brownian step (overlap forces computed in the graph, positions advanced)
+// with and without noise.
+enum { GM_SAMPLE = 0, GM_FORCES_NOISE = 1, GM_FORCES = 2, GM_BD_NOISE = 3, GM_BD = 4, GM_COUNT = 5 };
+static inline bool gm_noise(int m) { return m == GM_SAMPLE || m == GM_FORCES_NOISE || m == GM_BD_NOISE; }
+static inline bool gm_bd(int m) { return m == GM_BD_NOISE || m == GM_BD; }
 
 void drop_graph(pse_ctx *c) {
-    for (int m = 0; m < 3; ++m) {
+    for (int m = 0; m < GM_COUNT; ++m) {
         if (c->exec[m]) cudaGraphExecDestroy(c->exec[m]);
         if (c->graph[m]) cudaGraphDestroy(c->graph[m]);
         c->exec[m] = nullptr;
@@ -386,6 +390,8 @@ template <typename T> pse_status ensure(pse_ctx *c, int64_t N) {
     d.pc_on = c->pc_enabled ? d.pc : nullptr;
     A(d.uwave, sizeof(V4<T>) * N);
     A(d.udet, sizeof(V4<T>) * N);
+    A(d.bd_force, sizeof(T) * 3 * N);
+    A(d.bd_dx, sizeof(T) * 3 * N);
     A(d.partials, sizeof(double) * (2 * num_sms() * 16 + 64));
     A(c->stage_pos, sizeof(T) * 3 * N);
     A(c->stage_out, sizeof(T) * 3 * N);
@@ -437,7 +443,7 @@ template <typename T> pse_status wave_branch(pse_ctx *c, int64_t N, cudaStream_t
             CKF(cufftExecD2Z(c->fft_r2c, (cufftDoubleReal *)d.grid, (cufftDoubleComplex *)d.spec));
         }
         launch_wave_apply<T>(w, d.args, c->params.system, d.spec,
-                             mode == GM_SAMPLE ? WAVE_MODE_GRIDNOISE : WAVE_MODE_DET, mode == GM_FORCES_NOISE, s);
+                             mode == GM_SAMPLE ? WAVE_MODE_GRIDNOISE : WAVE_MODE_DET, gm_noise(mode), s);
     }
     CKF(cufftSetStream(c->fft, s));
     if constexpr (sizeof(T) == 4) {
@@ -459,16 +465,20 @@ template <typename T> pse_status capture_pre(pse_ctx *c, int mode) {
     Dev<T> &d = dev<T>(c);
     cudaStream_t s = c->s_main;
     pre<T>(c, N, s);
+    if (gm_bd(mode)) {  // the forces need the neighbour list before the wave branch spreads them
+        launch_nbr<T>(N, geom<T>(c), d, s);
+        launch_repulsion<T>(N, geom<T>(c), d, s);
+    }
     cudaEventRecord(c->ev[0], s);
     cudaStreamWaitEvent(c->s_wave, c->ev[0], 0);
     const pse_status wst = wave_branch<T>(c, N, c->s_wave, mode);
     cudaEventRecord(c->ev[1], c->s_wave);
-    launch_nbr<T>(N, geom<T>(c), d, s);
+    if (!gm_bd(mode)) launch_nbr<T>(N, geom<T>(c), d, s);
     if (mode != GM_SAMPLE) {  // M_r F into udet (the records are overwritten by q_1 next)
         launch_gather_vec<T>(N, d.args, d, s);
         launch_matvec_sorted<T>(N, geom<T>(c), d, s);
     }
-    if (mode != GM_FORCES) real_setup<T>(c, N, s);
+    if (gm_noise(mode)) real_setup<T>(c, N, s);
     return wst;
 }
 
@@ -485,8 +495,9 @@ template <typename T> void capture_post(pse_ctx *c, int mode) {
     Dev<T> &d = dev<T>(c);
     cudaStreamWaitEvent(c->s_main, c->ev[1], 0);
     if (mode == GM_SAMPLE) launch_lz_final<T>(c->N, d.args, d, true, c->s_main);
-    else if (mode == GM_FORCES_NOISE) launch_lz_final_forces<T>(c->N, d.args, d, c->s_main);
+    else if (gm_noise(mode)) launch_lz_final_forces<T>(c->N, d.args, d, c->s_main);
     else launch_det_final<T>(c->N, d.args, d, c->s_main);
+    if (gm_bd(mode)) launch_advance<T>(c->N, geom<T>(c), d, c->s_main);
 }
 
 // Insert a WHILE node (default condition 1) at the capture point of `s`;
@@ -517,7 +528,7 @@ static cudaError_t add_while(cudaStream_t s, cudaGraphConditionalHandle *h, cuda
 // the epilogue.
 template <typename T> pse_status capture_sample(pse_ctx *c, int mode) {
     const pse_status wst = capture_pre<T>(c, mode);
-    if (mode == GM_FORCES) {
+    if (!gm_noise(mode)) {
         capture_post<T>(c, mode);
         return wst;
     }
@@ -563,15 +574,17 @@ template <typename T> pse_status run_plain(pse_ctx *c, cudaStream_t s, int mode)
     Dev<T> &d = dev<T>(c);
     const double ltol = c->params.lanczos_tol > 0 ? c->params.lanczos_tol : c->plan.tol;
     pre<T>(c, N, s);
+    launch_nbr<T>(N, geom<T>(c), d, s);
+    if (gm_bd(mode)) launch_repulsion<T>(N, geom<T>(c), d, s);
     pse_status st = wave_branch<T>(c, N, s, mode);
     if (st != PSE_OK) return st;
-    launch_nbr<T>(N, geom<T>(c), d, s);
     if (mode != GM_SAMPLE) {
         launch_gather_vec<T>(N, d.args, d, s);
         launch_matvec_sorted<T>(N, geom<T>(c), d, s);
     }
-    if (mode == GM_FORCES) {
+    if (!gm_noise(mode)) {
         launch_det_final<T>(N, d.args, d, s);
+        if (gm_bd(mode)) launch_advance<T>(N, geom<T>(c), d, s);
         return PSE_OK;
     }
     real_setup<T>(c, N, s);
@@ -586,6 +599,7 @@ template <typename T> pse_status run_plain(pse_ctx *c, cudaStream_t s, int mode)
     }
     if (mode == GM_SAMPLE) launch_lz_final<T>(N, d.args, d, true, s);
     else launch_lz_final_forces<T>(N, d.args, d, s);
+    if (gm_bd(mode)) launch_advance<T>(N, geom<T>(c), d, s);
     return PSE_OK;
 }
 
@@ -705,6 +719,49 @@ template <typename T> pse_status tune_spread(pse_ctx *c, cudaStream_t s) {
     cudaGetLastError();
     c->spread_tuned = true;
     return set_spread_tile<T>(c, keep);
+}
+
+template <typename T>
+pse_status bd_impl(pse_ctx *c, int64_t N, T *pos, const T *fext, double dt, double kT, double k_rep, uint64_t seed,
+                   uint64_t step, cudaStream_t s) {
+    if (!pos || N < 1) return PSE_EINVAL;
+    if (!(dt >= 0.0) || !(kT >= 0.0) || !(k_rep >= 0.0) || !isfinite(dt) || !isfinite(kT) || !isfinite(k_rep))
+        return PSE_EINVAL;
+    if (kT > 0.0 && c->params.wave_noise == 1) return PSE_ENOTSUPPORTED;
+    if (k_rep > 0.0 && c->plan.r_cut < 2.0 * c->plan.a) return PSE_ENOTSUPPORTED;  // contacts beyond the list
+    DeviceGuard guard(c->device);
+    pse_status st = ensure<T>(c, N);
+    if (st != PSE_OK) return st;
+    if ((st = ensure_r2c<T>(c)) != PSE_OK) return st;
+    if ((st = choose_spread<T>(c)) != PSE_OK) return st;
+    const int mode = kT > 0.0 ? GM_BD_NOISE : GM_BD;
+    Dev<T> &d = dev<T>(c);
+    SampleArgs<T> a{};
+    a.pos = pos;
+    a.out = d.bd_dx;
+    a.vin = d.bd_force;
+    a.advance = pos;
+    a.fext = fext;
+    a.k_rep = k_rep;
+    a.seed = seed;
+    a.sample = step;
+    a.c_det = dt;
+    a.c_noise = sqrt(2.0 * kT * dt);
+    CK(cudaMemcpyAsync(d.args, &a, sizeof(a), cudaMemcpyHostToDevice, s));
+    const bool use_graph = c->params.use_graph >= 0;
+    if (use_graph && !c->exec[mode]) {
+        st = build_graph<T>(c, mode);
+        if (st != PSE_OK) return st;
+    }
+    if (use_graph) {
+        CK(cudaGraphLaunch(c->exec[mode], s));
+    } else {
+        st = run_plain<T>(c, s, mode);
+        if (st != PSE_OK) return st;
+    }
+    c->last_stream = s;
+    CK(cudaGetLastError());
+    return PSE_OK;
 }
 
 template <typename T>
@@ -910,6 +967,18 @@ pse_status pse_sample_with_forces_f64(pse_ctx *c, int64_t N, const double *d_pos
     if (!c || c->plan.precision != PSE_FP64) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
     return forces_impl<double>(c, N, d_pos, d_force, seed, sample_index, c_det, c_noise, d_out,
                                (cudaStream_t)stream);
+}
+
+pse_status pse_bd_step(pse_ctx *c, int64_t N, float *d_pos, const float *d_fext, double dt, double kT,
+                       double k_rep, uint64_t seed, uint64_t step, void *stream) {
+    if (!c || c->plan.precision != PSE_FP32) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
+    return bd_impl<float>(c, N, d_pos, d_fext, dt, kT, k_rep, seed, step, (cudaStream_t)stream);
+}
+
+pse_status pse_bd_step_f64(pse_ctx *c, int64_t N, double *d_pos, const double *d_fext, double dt, double kT,
+                           double k_rep, uint64_t seed, uint64_t step, void *stream) {
+    if (!c || c->plan.precision != PSE_FP64) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
+    return bd_impl<double>(c, N, d_pos, d_fext, dt, kT, k_rep, seed, step, (cudaStream_t)stream);
 }
 
 pse_status pse_mobility_apply(pse_ctx *c, int64_t N, const float *d_pos, const float *d_force, float *d_out,

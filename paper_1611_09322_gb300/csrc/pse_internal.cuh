@@ -98,6 +98,9 @@ template <typename T> struct SampleArgs {
     uint64_t sample;
     double c_det;   // weight of M F (forces path)
     double c_noise; // weight of M^{1/2} z (1 for a plain sample)
+    T *advance;     // Brownian step: positions advanced in place by out (3N), or null
+    const T *fext;  // Brownian step: external force (3N) added to the repulsion, or null
+    double k_rep;   // Brownian step: overlap repulsion stiffness
 };
 
 // Tiling of the spreading kernel: tiles of G^3 cells, each spread into a
@@ -310,6 +313,8 @@ template <typename T> struct Dev {
     V4<T> *u;            // matvec output
     V4<T> *uwave;        // wave part at sorted particles
     V4<T> *udet;         // M_r F at sorted particles (forces path)
+    T *bd_force;         // 3N, caller order: forces of a Brownian step
+    T *bd_dx;            // 3N, caller order: displacement of a Brownian step
     double *partials;    // per-block partial sums
     LzState *lz;
     V4<T> *table;        // PSE_TABLE_N: (F, G - F, dF, d(G-F)) / (6 pi a)
@@ -425,6 +430,8 @@ template <typename T> void launch_gather_vec(int64_t N, const SampleArgs<T> *arg
 template <typename T> void launch_det_final(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, cudaStream_t s);
 template <typename T>
 void launch_lz_final_forces(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, cudaStream_t s);
+template <typename T> void launch_repulsion(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s);
+template <typename T> void launch_advance(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s);
 
 // learned preconditioner (float contexts)
 void launch_pc_infer(int64_t N, Geom<float> g, const Dev<float> &d, const float *theta, float s0, float *pc,
