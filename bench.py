@@ -5,7 +5,10 @@
 One step = one full PSE sample (cell list, neighbour list, device-side
 Lanczos loop, k-space noise, cuFFT, interpolation, combination) of the
 headline workload: N = 1e6 random hard spheres (a = 1, RSA seed 1) at volume
-fraction 0.1, tol 1e-3, xi a = 0.5 -- the paper's Table 1 setting at N ~ 1e6.
+fraction 0.1, tol 1e-3 -- the paper's Table 1 setting at N ~ 1e6 -- with the
+splitting xi and FFT grid chosen before the timed region by pse_tune_xi (the
+eq. xistar model calibrated at xi a = 0.5, then a timed scan of the grids
+around it, each at the largest xi it admits).
 L2 is flushed (a 256 MB write) before every timed step; each step is timed
 with CUDA events on the launching stream.  Prints one JSON line.
 
@@ -29,17 +32,26 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-samples/s at tol 1e-3 (N=1e6), learned+batched vs plain PSE"
 UNIT = "particle-samples/s"
 N_PART, PHI, XI, TOL, SEED_POS = 1_000_000, 0.1, 0.5, 1e-3, 1
+# the splitting the timed scan picks for the headline workload on a GB300
+# (grid 256^3, the largest xi that grid admits); the oracle arm, which has no
+# GPU to run the scan, samples at it
+XI_TUNED, M_TUNED = 0.5178442916, 256
 CPU_SAMPLE_N = 250_000  # bounded CPU sample: same density and parameters, smaller box
 
 
-def workload_config(plan=None):
-    cfg = {"workload": "random hard spheres, N=1e6, phi=0.1, a=1, tol=1e-3, xi*a=0.5 (RSA seed 1), "
-                       "one PSE sample per step",
-           "N": N_PART, "phi": PHI, "xi": XI, "tol": TOL, "precision": "fp32 grid/FFT/matvec, fp64 Lanczos scalars",
+def workload_config(plan=None, tuning=None, xi=XI_TUNED):
+    cfg = {"workload": "random hard spheres, N=1e6, phi=0.1, a=1, tol=1e-3 (RSA seed 1), xi from the timed scan "
+                       "started at xi*a=0.5, one PSE sample per step",
+           "N": N_PART, "phi": PHI, "xi": xi, "tol": TOL, "precision": "fp32 grid/FFT/matvec, fp64 Lanczos scalars",
            "l2": "flushed (256 MB write) before every timed step"}
     if plan:
-        cfg.update({"L": round(plan["L"], 4), "M": plan["M"], "P": plan["P"], "r_cut": round(plan["r_cut"], 4),
-                    "ncell": plan["ncell"]})
+        cfg.update({"xi": plan["xi"], "L": round(plan["L"], 4), "M": plan["M"], "P": plan["P"],
+                    "r_cut": round(plan["r_cut"], 4), "ncell": plan["ncell"]})
+    if tuning:
+        cfg["xi_tuning"] = {"xi_start": tuning["xi_start"], "xi_model": round(tuning["xi_model"], 4),
+                            "xi_best": tuning["xi_best"], "M_best": tuning["M_best"],
+                            "ms_start": round(tuning["ms_start"], 4), "ms_best": round(tuning["ms_best"], 4),
+                            "grids_timed": tuning["n_grids"], "samples_timed": len(tuning["trials"])}
     return cfg
 
 
@@ -123,7 +135,7 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def cpu_baseline(budget_s=30.0):
+def cpu_baseline(xi=XI_TUNED, budget_s=30.0):
     """The FP64 oracle (as it stands) on a bounded sample: N=2.5e5 at the same phi/xi/tol."""
     import numpy as np
     from oracle import ewald, pse
@@ -131,13 +143,13 @@ def cpu_baseline(budget_s=30.0):
     pos, L, _ = workloads.hard_spheres(CPU_SAMPLE_N, PHI, SEED_POS)
     p = pos.astype(np.float64)
     t0 = time.perf_counter()
-    plan = ewald.plan(L, 1.0, XI, TOL)
+    plan = ewald.plan(L, 1.0, xi, TOL)
     ur, j, _ = pse.real_sample(p, plan, 7, 0)
     uw = pse.wave_sample_grid(p, plan, 7, 0)
     dt = time.perf_counter() - t0
     return {"value": CPU_SAMPLE_N / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"one FP64 oracle PSE sample of N={CPU_SAMPLE_N} hard spheres at phi={PHI}, tol={TOL}, "
-                      f"xi={XI} (M={plan.M}, Lanczos j={j}); numpy/scipy on the host cores; {dt:.1f} s"}
+                      f"xi={xi:.4f} (M={plan.M}, Lanczos j={j}); numpy/scipy on the host cores; {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -149,7 +161,7 @@ def run_reference(args):
     from paper_1611_09322_gb300 import workloads
     pos, L, _ = workloads.hard_spheres(CPU_SAMPLE_N, PHI, SEED_POS)
     p = pos.astype(np.float64)
-    plan = ewald.plan(L, 1.0, XI, TOL)
+    plan = ewald.plan(L, 1.0, XI_TUNED, TOL)
     op = pse.RealOperator(p, plan)
 
     def step(i):
@@ -170,8 +182,8 @@ def run_reference(args):
             "config": workload_config(),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"each step: one FP64 oracle PSE sample of N={CPU_SAMPLE_N} at phi={PHI} "
-                                       f"(same density and parameters as the N=1e6 workload; neighbour pairs "
-                                       f"built once outside the timed steps)"},
+                                       f"(same density, tol and xi={XI_TUNED:.4f} as the N=1e6 workload; "
+                                       f"neighbour pairs built once outside the timed steps)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -191,25 +203,25 @@ def timed_steps(run, steps, flush, stream):
 
 
 def launches_per_sample(J, learned=False):
-    # bin + 3 scan + scatter + cell sort, noise + interpolation, neighbour
-    # list, (network), q_1, 3 kernels per loop body (J bodies), final;
-    # cuFFT's own kernels are not counted
-    return 11 + (1 if learned else 0) + 3 * J
+    # bin + 3 scan + scatter + cell sort, noise + node-major grid copy +
+    # interpolation, neighbour list, (network), q_1, 3 kernels per loop body
+    # (J bodies), final; cuFFT's own kernels are not counted
+    return 12 + (1 if learned else 0) + 3 * J
 
 
-def variants_learned_batched(dev, flush, stream, steps):
+def variants_learned_batched(dev, flush, stream, steps, xi, M):
     """The metric's comparison: learned preconditioner and batching vs plain."""
     import numpy as np
     import torch
     from paper_1611_09322_gb300 import BatchSampler, Sampler, precond_train, workloads
     out = {}
-    theta, info = precond_train.train(xi=XI, tol=TOL, steps=1500, lr=3e-3)
+    theta, info = precond_train.train(xi=xi, tol=TOL, steps=1500, lr=3e-3)
     out["learned_training"] = {k: v for k, v in info.items() if k != "loss_hist"}
     pos, L, _ = workloads.hard_spheres(N_PART, PHI, SEED_POS)
     d = torch.from_numpy(pos).to(dev)
     o = torch.empty_like(d)
     for name, th in (("plain_N1e6", None), ("learned_N1e6", theta)):
-        s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=1)
+        s = Sampler(L, 1.0, xi=xi, tol=TOL, grid_M=M)
         if th is not None:
             s.precond_set_weights(th)
         for i in range(3):
@@ -224,7 +236,7 @@ def variants_learned_batched(dev, flush, stream, steps):
     # dt M F + sqrt(2 dt) M^{1/2} z (kT = 1, dt = 1e-3), and the plain sample
     # with the wave noise drawn on the grid
     F = torch.randn(d.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(3))
-    s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=3)
+    s = Sampler(L, 1.0, xi=xi, tol=TOL, grid_M=M, autotune=2)
     runs = (("mobility_apply_N1e6", lambda i: s.sample_with_forces(d, F, 1, 400 + i, 1.0, 0.0, out=o)),
             ("euler_maruyama_N1e6", lambda i: s.sample_with_forces(d, F, 1, 500 + i, 1e-3, math.sqrt(2e-3), out=o)))
     for name, fn in runs:
@@ -243,7 +255,7 @@ def variants_learned_batched(dev, flush, stream, steps):
     out["bd_step_N1e6"] = {"value": N_PART * steps / (sum(per) / 1e3), "ms_per_step": sum(per) / steps,
                            "lanczos_iters": s.stats()["lanczos_iters"]}
     s.close()
-    s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=1, wave_noise=1)
+    s = Sampler(L, 1.0, xi=xi, tol=TOL, grid_M=M, wave_noise=1)
     for i in range(3):
         s.sample(d, 1, i, out=o)
     per = timed_steps(lambda i: s.sample(d, 1, 600 + i, out=o), steps, flush, stream)
@@ -274,6 +286,7 @@ def variants_learned_batched(dev, flush, stream, steps):
     out["workload_batched"] = ("64 periodic systems, N log-uniform in [1e3, 5e4], phi uniform in [0.05, 0.4], "
                                "half fractal gels (phi <= 0.2), each with its own box and FFT grid, xi a = 0.5, "
                                "tol 1e-3; one CUDA graph launch per step")
+    out["variants_xi"] = {"xi": xi, "M": M, "note": "the N=1e6 variants run at the headline's tuned xi and grid"}
     return out
 
 
@@ -343,6 +356,9 @@ def main():
     ap.add_argument("--only", choices=["forces", "batch"], default=None,
                     help="run one secondary workload alone (profiling aid)")
     ap.add_argument("--no-graph", action="store_true", help="with --only: launch without CUDA graphs")
+    ap.add_argument("--xi", type=float, default=None,
+                    help="skip the xi scan and sample at this xi (with --grid; a profiling aid)")
+    ap.add_argument("--grid", type=int, default=0, help="with --xi: the FFT grid per side")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -353,7 +369,7 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_1611_09322_gb300 import Sampler, workloads
+    from paper_1611_09322_gb300 import Sampler, pse_tune_xi, workloads
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -363,8 +379,20 @@ def main():
     torch.cuda.set_device(dev)
 
     pos, L, _ = workloads.hard_spheres(N_PART, PHI, SEED_POS)
-    s = Sampler(L, 1.0, xi=XI, tol=TOL, autotune=1)
     d_pos = torch.from_numpy(pos).to(dev)
+    # the splitting and grid: the timed scan around the model's xi* (untimed
+    # setup, like the cuFFT plans); replicas take rank 0's choice
+    if args.xi is not None:
+        tuning = None
+        xi, M_grid = args.xi, args.grid
+    else:
+        tuning = pse_tune_xi(L, d_pos, xi=XI, tol=TOL, reps=10, autotune=1)
+        xi, M_grid = tuning["xi_best"], tuning["M_best"]
+    if ws > 1:
+        t = torch.tensor([xi, float(M_grid)], dtype=torch.float64, device=dev)
+        dist.broadcast(t, 0)
+        xi, M_grid = float(t[0]), int(t[1])
+    s = Sampler(L, 1.0, xi=xi, tol=TOL, grid_M=M_grid)
     out = torch.empty_like(d_pos)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -435,15 +463,15 @@ def main():
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
                 "ms_per_step_median": statistics.median(per), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": workload_config(plan), "lanczos_iters": J, "n_pairs": n_pairs,
+                "config": workload_config(plan, tuning), "lanczos_iters": J, "n_pairs": n_pairs,
                 "variant": "plain PSE, one system, one CUDA graph per sample",
                 "roofline": roofline, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches_per_sample(J) * args.steps,
                 "parallelism": "replicas" if ws > 1 else "single GPU"}
         if not args.no_variants:
-            line["variants"] = variants_learned_batched(dev, flush, stream, max(20, args.steps // 4))
+            line["variants"] = variants_learned_batched(dev, flush, stream, max(20, args.steps // 4), xi, M_grid)
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"] = cpu_baseline(xi)
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()

@@ -88,7 +88,13 @@ typedef struct {
     int matvec_shape;    /* 0 (default): near-field matvec with 4 threads x 4
                             gathers per particle (or timed with autotune bit 2);
                             1..4 force shape 4x4, 8x2, 16x1, 4x2              */
-    int reserved[2];
+    int interp_form;     /* FP32 wave interpolation: 0 (default) copies the
+                            three velocity grids into one node-major float4
+                            grid (16 M^3 bytes more) and reads one record per
+                            support node, one warp per particle (P in 3..10);
+                            1: reads the planar grids directly, 16 lanes per
+                            particle                                           */
+    int reserved[1];
 } pse_params;
 
 /* Parameters derived from (L, a, xi, tol) by Sec. II C of the paper:
@@ -147,6 +153,68 @@ pse_status pse_create_ex(pse_ctx **out, double L, double a, const pse_params *p)
 void pse_destroy(pse_ctx *ctx);
 
 pse_status pse_get_plan(const pse_ctx *ctx, pse_plan_info *out);
+
+/* ---------------------------------------------------------------- choice of xi */
+
+/* eq. xistar (Sec. II C) with the implementation constants C_R, C_W of
+ * eq. work calibrated by two measured times at a splitting xi0 (host only,
+ * no GPU):
+ *   t_real: time of the xi-dependent real-space work at xi0 (neighbour list
+ *           and near-field matvecs; the neighbour count within r_cut ~ 1/xi
+ *           grows as r_cut^d_f),
+ *   t_wave: time of the xi-dependent wave-space work at xi0 (k-space noise
+ *           and FFT, ~ xi^3 Fourier modes),
+ *   d_f:    fractal dimension of the suspension in [1, 3] (3: hard spheres).
+ * The minimiser of t_real (xi0/xi)^d_f + t_wave (xi/xi0)^3 is
+ *   *xi_star = xi0 (d_f t_real / (3 t_wave))^(1/(d_f + 3)),
+ * n_iter and the FFT's logarithm held at their xi0 values.  PSE_EINVAL for
+ * non-positive or non-finite times or xi0, or d_f outside [1, 3]. */
+pse_status pse_xi_model(double xi0, double t_real, double t_wave, double d_f, double *xi_star);
+
+#define PSE_XI_TRIALS 8
+#define PSE_XI_GRIDS 64
+/* Result of pse_tune_xi (times in ms of device time per sample). */
+typedef struct {
+    double xi_start;     /* p->xi (or 0.5 / a)                                  */
+    double t_real, t_wave; /* xi-dependent stage times at xi_start, one staged
+                            sample: neighbour list + matvecs; noise + FFT      */
+    double xi_model;     /* pse_xi_model(xi_start, t_real, t_wave, d_f)          */
+    double xi_best;      /* fastest trial (xi_start on ties)                     */
+    double ms_start, ms_best;
+    int M_best;          /* its grid: create the sampler with xi = xi_best and
+                            grid_M = M_best                                     */
+    int n_grids;         /* candidate grids whose FFT was timed                 */
+    int n_tried;         /* trials below; trial 0 is the start context          */
+    double xi_tried[PSE_XI_TRIALS];
+    double ms_tried[PSE_XI_TRIALS]; /* -1: unusable (list overflow, no
+                                       convergence within max_iter)            */
+    double ms_pred[PSE_XI_TRIALS];  /* the prediction that selected the trial   */
+    int iters_tried[PSE_XI_TRIALS]; /* Lanczos steps of the last timed sample   */
+    int M_tried[PSE_XI_TRIALS];     /* FFT grid per side                        */
+} pse_xi_tuning;
+
+/* Choice of the splitting parameter for a configuration (Sec. II C: the work
+ * of eq. work is minimised at xi*).
+ *   1. Times `reps` FP32 samples (0 selects 5) of a context created with *p
+ *      at xi_start and one staged sample, giving t_real and t_wave; predicts
+ *      xi* with pse_xi_model.
+ *   2. Candidate grids: the 2,3,5,7-smooth sizes that the plan gives between
+ *      0.75 xi* and 1.35 xi* (at most PSE_XI_GRIDS).  On a fixed grid the wave
+ *      part costs the same for every xi it admits while the real part shrinks
+ *      as xi grows, so each grid is paired with the largest xi whose plan fits
+ *      it (k_cut L / pi <= M, eta <= 1).  Each grid's cuFFT C2R is timed and
+ *      its sample time predicted from the start context's stage times scaled
+ *      by eq. work (real part ~ xi^-d_f, noise ~ M^3, FFT as timed).
+ *   3. The best predictions are timed as whole samples (up to seven), and the
+ *      fastest trial, the start context included, is reported.
+ * Every trial context is destroyed before the next is made; d_pos (3N
+ * float32, device, caller order) is only read.  Synchronises `stream`.
+ * Create the sampler with xi = out->xi_best and grid_M = out->M_best.
+ * PSE_ENOTSUPPORTED for FP64 parameters or use_precond = 1 (the network is
+ * trained at one xi); errors of the start context are returned, those of the
+ * other trials mark them unusable. */
+pse_status pse_tune_xi(double L, double a, const pse_params *p, int64_t N, const float *d_pos, double d_f,
+                       int reps, pse_xi_tuning *out, void *stream);
 
 /* ---------------------------------------------------------------- sampling */
 

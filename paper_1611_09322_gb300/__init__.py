@@ -15,12 +15,12 @@ from . import _lib
 from ._lib import PSE_FP32, PSE_FP64, PseError, pse_params, pse_plan_info, pse_stats
 
 __all__ = ["Sampler", "BatchSampler", "pse_plan", "pse_real_scalars", "pse_real_matvec_noalloc", "pse_precond_loss_grad",
-           "pse_precond_train", "PseError", "PSE_FP32", "PSE_FP64", "make_params"]
+           "pse_precond_train", "pse_xi_model", "pse_tune_xi", "PseError", "PSE_FP32", "PSE_FP64", "make_params"]
 
 
 def make_params(tol=1e-3, xi=0.5, precision=PSE_FP32, max_iter=0, fixed_iter=0, grid_M=0, support_P=0,
                 use_precond=0, lanczos_tol=0.0, use_graph=True, autotune=0, system=0, wave_noise=0,
-                spread_tile=0, matvec_shape=0):
+                spread_tile=0, matvec_shape=0, interp_form=0):
     p = pse_params()
     p.tol = tol
     p.xi = xi
@@ -37,6 +37,7 @@ def make_params(tol=1e-3, xi=0.5, precision=PSE_FP32, max_iter=0, fixed_iter=0, 
     p.wave_noise = wave_noise
     p.spread_tile = spread_tile
     p.matvec_shape = matvec_shape
+    p.interp_form = interp_form
     return p
 
 
@@ -58,6 +59,24 @@ def pse_real_scalars(r, xi, a=1.0):
     vp = lambda x: x.ctypes.data_as(ctypes.c_void_p)
     _lib.check(lib.pse_real_scalars(xi, a, r.size, vp(r), vp(F), vp(G)), "pse_real_scalars")
     return F, G
+
+
+def pse_xi_model(xi0, t_real, t_wave, d_f=3.0):
+    """Host-only eq. xistar with constants calibrated by times at xi0 (no GPU needed)."""
+    lib = _lib.load()
+    out = ctypes.c_double()
+    _lib.check(lib.pse_xi_model(xi0, t_real, t_wave, d_f, ctypes.byref(out)), "pse_xi_model")
+    return out.value
+
+
+def pse_tune_xi(L, pos, a=1.0, d_f=3.0, reps=5, **kw):
+    """Timed choice of xi around the model's xi* for positions `pos` (CUDA float32); returns a dict."""
+    lib = _lib.load()
+    p = make_params(**kw)
+    out = _lib.pse_xi_tuning()
+    _lib.check(lib.pse_tune_xi(L, a, ctypes.byref(p), pos.shape[0], _ptr(pos), d_f, reps, ctypes.byref(out),
+                               _stream()), "pse_tune_xi")
+    return out.as_dict()
 
 
 def pse_real_matvec_noalloc(L, a, xi, tol, pos, v, out):

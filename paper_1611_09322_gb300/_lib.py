@@ -33,7 +33,7 @@ class pse_params(ctypes.Structure):
                 ("support_P", ctypes.c_int), ("use_precond", ctypes.c_int), ("lanczos_tol", ctypes.c_double),
                 ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int), ("system", ctypes.c_int),
                 ("wave_noise", ctypes.c_int), ("spread_tile", ctypes.c_int),
-                ("matvec_shape", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("matvec_shape", ctypes.c_int), ("interp_form", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class pse_plan_info(ctypes.Structure):
@@ -54,6 +54,26 @@ class pse_stats(ctypes.Structure):
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
+PSE_XI_TRIALS = 8
+
+
+class pse_xi_tuning(ctypes.Structure):
+    _fields_ = [("xi_start", ctypes.c_double), ("t_real", ctypes.c_double), ("t_wave", ctypes.c_double),
+                ("xi_model", ctypes.c_double), ("xi_best", ctypes.c_double), ("ms_start", ctypes.c_double),
+                ("ms_best", ctypes.c_double), ("M_best", ctypes.c_int), ("n_grids", ctypes.c_int),
+                ("n_tried", ctypes.c_int),
+                ("xi_tried", ctypes.c_double * PSE_XI_TRIALS), ("ms_tried", ctypes.c_double * PSE_XI_TRIALS),
+                ("ms_pred", ctypes.c_double * PSE_XI_TRIALS),
+                ("iters_tried", ctypes.c_int * PSE_XI_TRIALS), ("M_tried", ctypes.c_int * PSE_XI_TRIALS)]
+
+    def as_dict(self):
+        n = self.n_tried
+        out = {name: getattr(self, name) for name, _ in self._fields_[:10]}
+        out["trials"] = [{"xi": self.xi_tried[i], "ms": self.ms_tried[i], "ms_pred": self.ms_pred[i],
+                          "lanczos_iters": self.iters_tried[i], "M": self.M_tried[i]} for i in range(n)]
+        return out
 
 
 # name -> (restype, argtypes); the exported surface of include/pse.h
@@ -98,6 +118,10 @@ SIGNATURES = {
     "pse_batch_destroy": (None, [_VP]),
     "pse_batch_set_precond": (_ST, [_VP, ctypes.c_int, _VP, ctypes.c_int]),
     "pse_real_scalars": (_ST, [ctypes.c_double, ctypes.c_double, _I64, _VP, _VP, _VP]),
+    "pse_xi_model": (_ST, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                           ctypes.POINTER(ctypes.c_double)]),
+    "pse_tune_xi": (_ST, [ctypes.c_double, ctypes.c_double, ctypes.POINTER(pse_params), _I64, _VP, ctypes.c_double,
+                          ctypes.c_int, ctypes.POINTER(pse_xi_tuning), _VP]),
 }
 
 _lib = None

@@ -513,7 +513,94 @@ __global__ void __launch_bounds__(128) k_interp_batch(const BSys *__restrict__ s
     }
 }
 
+// Node-major copy of the three planar velocity grids: one 16-byte record
+// (x, y, z, 0) per node, so that the interpolation reads a node with one load.
+__global__ void k_grid_aos(int64_t M3, const float *__restrict__ g, V4<float> *__restrict__ g4) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= M3) return;
+    V4<float> v;
+    v.x = __ldg(g + i);
+    v.y = __ldg(g + M3 + i);
+    v.z = __ldg(g + 2 * M3 + i);
+    v.w = 0.f;
+    g4[i] = v;
+}
+
+// Interpolation from the node-major grid: a group of P lanes per particle,
+// floor(32 / P) particles per warp (consecutive in cell order, so their
+// supports overlap in L1).  Lane c of a group owns the z-node c of the
+// support and walks the P x P (x, y) columns, one 16-byte load per node; it
+// evaluates the 1-D weights of index c on all three axes, which the group's
+// lanes exchange by shuffles.  The group's partial sums meet in its first lane.
+template <int P>
+__global__ void __launch_bounds__(128) k_interp4(int64_t N, WaveGeom<float> w,
+                                                 const V4<float> *__restrict__ pos_sorted,
+                                                 const V4<float> *__restrict__ grid4, V4<float> *uwave) {
+    constexpr int R = 32 / P;  // particles per warp; lanes R P .. 31 idle
+    const int lane = threadIdx.x & 31;
+    const int g = lane / P, c = lane - (lane / P) * P;
+    const int64_t s = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * R + g;
+    const bool act = g < R && s < N;
+    const int base = (g < R ? g : 0) * P;  // first lane of the group
+    const V4<float> p = pos_sorted[act ? s : 0];
+    const int M = w.M;
+    int i0x, i0y, i0z;
+    float ux, uy, uz;
+    support(p.x, w, i0x, ux);
+    support(p.y, w, i0y, uy);
+    support(p.z, w, i0z, uz);
+    const float fc = float(c);
+    const float ex = ux - fc, ey = uy - fc, ez = uz - fc;
+    const float wxc = expf(-w.ch2 * ex * ex);
+    const float wyc = expf(-w.ch2 * ey * ey);
+    const float wzc = expf(-w.ch2 * ez * ez);
+    const int izc = wrap_grid(i0z + c, M);
+    float wyz[P];
+    int row[P];
+#pragma unroll
+    for (int b = 0; b < P; ++b) {
+        wyz[b] = __shfl_sync(0xffffffffu, wyc, base + b) * wzc;
+        row[b] = wrap_grid(i0y + b, M) * M + izc;
+    }
+    const float4 *g4 = reinterpret_cast<const float4 *>(grid4);
+    const int64_t MM = (int64_t)M * M;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+#pragma unroll 1
+    for (int a = 0; a < P; ++a) {
+        const float wxa = __shfl_sync(0xffffffffu, wxc, base + a);
+        const float4 *plane = g4 + wrap_grid(i0x + a, M) * MM;
+        if (act) {
+#pragma unroll
+            for (int b = 0; b < P; ++b) {
+                const float4 v = __ldg(plane + row[b]);
+                const float wt = wxa * wyz[b];
+                ax = fmaf(wt, v.x, ax);
+                ay = fmaf(wt, v.y, ay);
+                az = fmaf(wt, v.z, az);
+            }
+        }
+    }
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        sx += __shfl_sync(0xffffffffu, ax, base + k);
+        sy += __shfl_sync(0xffffffffu, ay, base + k);
+        sz += __shfl_sync(0xffffffffu, az, base + k);
+    }
+    if (act && c == 0) {
+        V4<float> o;
+        o.x = sx * w.norm; o.y = sy * w.norm; o.z = sz * w.norm; o.w = 0.f;
+        uwave[s] = o;
+    }
+}
+
 static inline unsigned nbw(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+template <int P>
+static void interp4(int64_t N, const WaveGeom<float> &w, const Dev<float> &d, cudaStream_t s) {
+    const int64_t warps = (N + 32 / P - 1) / (32 / P);
+    k_interp4<P><<<nbw(warps * 32, 128), 128, 0, s>>>(N, w, d.pos_sorted, d.grid4, d.uwave);
+}
 
 void launch_batch_noise(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s) {
     k_wave_noise_batch<<<nblk[BK_NOISE], 256, 0, s>>>(sys, tab[BK_NOISE]);
@@ -528,6 +615,23 @@ void launch_wave_noise(WaveGeom<T> w, const SampleArgs<T> *args, int system, voi
     k_wave_noise<T><<<nbw(plane, 256), 256, 0, s>>>(w, args, system, (typename Cplx<T>::type *)spec, plane);
 }
 template <typename T> void launch_interp(int64_t N, WaveGeom<T> w, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (w.interp_lanes == 0 && w.P >= 3 && w.P <= 10) {
+            const int64_t M3 = (int64_t)w.M * w.M * w.M;
+            k_grid_aos<<<nbw(M3, 256), 256, 0, s>>>(M3, d.grid, d.grid4);
+            switch (w.P) {
+                case 3: interp4<3>(N, w, d, s); break;
+                case 4: interp4<4>(N, w, d, s); break;
+                case 5: interp4<5>(N, w, d, s); break;
+                case 6: interp4<6>(N, w, d, s); break;
+                case 7: interp4<7>(N, w, d, s); break;
+                case 8: interp4<8>(N, w, d, s); break;
+                case 9: interp4<9>(N, w, d, s); break;
+                default: interp4<10>(N, w, d, s); break;
+            }
+            return;
+        }
+    }
     // the group must hold the P lanes that evaluate the 1-D weights
     const int G = w.interp_lanes >= w.P ? w.interp_lanes : (w.P <= 8 ? 8 : (w.P <= 16 ? 16 : 32));
     if (G <= 8) k_interp<T, 8><<<nbw(N * 8, 128), 128, 0, s>>>(N, w, d.pos_sorted, d.grid, d.uwave);

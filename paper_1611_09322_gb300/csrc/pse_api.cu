@@ -167,7 +167,8 @@ template <typename T> void fill_geom(pse_ctx *c) {
     w.ch2 = (T)(2 * p.xi * p.xi * p.h * p.h / p.eta);
     w.norm = (T)(pow(2 * p.xi * p.xi / (M_PI * p.eta), 1.5) * p.h * p.h * p.h);
     w.inv_M15 = (T)pow((double)p.M, -1.5);
-    w.interp_lanes = 16;
+    // 0: node-major grid copy + one warp per particle (FP32, P in 3..10)
+    w.interp_lanes = (sizeof(T) == 4 && c->params.interp_form == 0 && p.P >= 3 && p.P <= 10) ? 0 : 16;
     wgeom<T>(c) = w;
 }
 
@@ -220,6 +221,10 @@ template <typename T> pse_status init_ctx(pse_ctx *c) {
     const size_t csize = sizeof(T) * 2;
     if ((st = alloc(c->per_ctx, &d.spec, csize * 3 * plane)) != PSE_OK) return st;
     if ((st = alloc(c->per_ctx, (void **)&d.grid, sizeof(T) * 3 * M * M * M)) != PSE_OK) return st;
+    if constexpr (sizeof(T) == 4)
+        if (c->params.interp_form == 0 && p.P >= 3 && p.P <= 10 &&
+            (st = alloc(c->per_ctx, (void **)&d.grid4, sizeof(V4<T>) * M * M * M)) != PSE_OK)
+            return st;
     if ((st = alloc(c->per_ctx, (void **)&d.lz, sizeof(LzState))) != PSE_OK) return st;
     CK(cudaMemset(d.lz, 0, sizeof(LzState)));
     if ((st = alloc(c->per_ctx, (void **)&d.args, sizeof(SampleArgs<T>))) != PSE_OK) return st;
@@ -805,35 +810,37 @@ pse_status forces_impl(pse_ctx *c, int64_t N, const T *pos, const T *force, uint
     return PSE_OK;
 }
 
-// Fastest cuFFT C2R (batch 3) grid among the 2,3,5,7-smooth sizes in
-// [M, 1.12 M]: each candidate is timed over 3 transforms after one warm-up.
 static int smooth_2357(int n) {
     const int pr[4] = {2, 3, 5, 7};
     for (int i = 0; i < 4; ++i) while (n % pr[i] == 0) n /= pr[i];
     return n == 1;
 }
 
-template <typename T> pse_status tune_fft_size(int M0, int *best_M) {
-    *best_M = M0;
-    const int Mmax = (int)(M0 * 1.12) + 1;
+// Device time (ms) of one cuFFT C2R (batch 3) on each grid Ms[i], the mean of
+// 3 transforms after one warm-up; 1e30 where no plan or memory was had.
+template <typename T> void time_fft_sizes(const int *Ms, int n, float *ms_out) {
+    int Mmax = 0;
+    for (int i = 0; i < n; ++i) {
+        ms_out[i] = 1e30f;
+        if (Ms[i] > Mmax) Mmax = Ms[i];
+    }
     const size_t cbytes = sizeof(T) * 2 * 3 * (size_t)Mmax * Mmax * (Mmax / 2 + 1);
     const size_t rbytes = sizeof(T) * 3 * (size_t)Mmax * Mmax * Mmax;
     void *spec = nullptr, *grid = nullptr;
     if (cudaMalloc(&spec, cbytes) != cudaSuccess || cudaMalloc(&grid, rbytes) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(spec);
-        return PSE_OK;  // keep the planned grid
+        return;
     }
     cudaMemset(spec, 0, cbytes);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    float best = 1e30f;
-    for (int M = M0; M <= Mmax; ++M) {
-        if (!smooth_2357(M)) continue;
+    for (int i = 0; i < n; ++i) {
+        const int M = Ms[i];
         cufftHandle h;
-        int n[3] = {M, M, M};
-        if (cufftPlanMany(&h, 3, n, nullptr, 1, M * M * (M / 2 + 1), nullptr, 1, M * M * M,
+        int dims[3] = {M, M, M};
+        if (cufftPlanMany(&h, 3, dims, nullptr, 1, M * M * (M / 2 + 1), nullptr, 1, M * M * M,
                           sizeof(T) == 4 ? CUFFT_C2R : CUFFT_Z2D, 3) != CUFFT_SUCCESS)
             continue;
         float ms = 0.f;
@@ -846,16 +853,30 @@ template <typename T> pse_status tune_fft_size(int M0, int *best_M) {
         cudaEventSynchronize(e1);
         cudaEventElapsedTime(&ms, e0, e1);
         cufftDestroy(h);
-        if (ms < best) {
-            best = ms;
-            *best_M = M;
-        }
+        ms_out[i] = ms / 3.f;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(spec);
     cudaFree(grid);
     cudaGetLastError();
+}
+
+// Fastest cuFFT C2R (batch 3) grid among the 2,3,5,7-smooth sizes in
+// [M, 1.12 M] (a finer grid only lowers the quadrature error).
+template <typename T> pse_status tune_fft_size(int M0, int *best_M) {
+    *best_M = M0;
+    int Ms[64], n = 0;
+    for (int M = M0; M <= (int)(M0 * 1.12) + 1 && n < 64; ++M)
+        if (smooth_2357(M)) Ms[n++] = M;
+    float ms[64];
+    time_fft_sizes<T>(Ms, n, ms);
+    float best = 1e30f;
+    for (int i = 0; i < n; ++i)
+        if (ms[i] < best) {
+            best = ms[i];
+            *best_M = Ms[i];
+        }
     return PSE_OK;
 }
 
@@ -887,7 +908,7 @@ pse_status create_impl(pse_ctx **out, double L, double a, const pse_params *p) {
     if (cudaGetDevice(&c->device) != cudaSuccess) { cudaGetLastError(); delete c; return PSE_ECUDA; }
     if (p->wave_noise < 0 || p->wave_noise > 1 ||
         !(p->spread_tile == 0 || p->spread_tile == 1 || p->spread_tile == 2 || p->spread_tile == 4) ||
-        p->matvec_shape < 0 || p->matvec_shape > PSE_MV_VARIANTS) {
+        p->matvec_shape < 0 || p->matvec_shape > PSE_MV_VARIANTS || p->interp_form < 0 || p->interp_form > 1) {
         delete c;
         return PSE_EINVAL;
     }
@@ -1083,7 +1104,8 @@ pse_status pse_profile_stages(pse_ctx *c, int64_t N, const float *d_pos, uint64_
         CKF(cufftSetStream(c->fft, s));
         CKF(cufftExecC2R(c->fft, (cufftComplex *)d.spec, (cufftReal *)d.grid));
         return PSE_OK; });
-    if (r == PSE_OK) r = timed(PSE_STAGE_INTERP, 1, [&] { interp<float>(c, N, s); return PSE_OK; });
+    if (r == PSE_OK)
+        r = timed(PSE_STAGE_INTERP, c->wf.interp_lanes == 0 ? 2 : 1, [&] { interp<float>(c, N, s); return PSE_OK; });
     if (r == PSE_OK) r = timed(PSE_STAGE_NEIGHBOURS, 1, [&] {
         launch_nbr<float>(N, c->gf, d, s);
         return PSE_OK; });
@@ -1105,6 +1127,182 @@ pse_status pse_profile_stages(pse_ctx *c, int64_t N, const float *d_pos, uint64_
     cudaEventDestroy(e1);
     c->last_stream = s;
     if (r != PSE_OK) return r;
+    CK(cudaGetLastError());
+    return PSE_OK;
+}
+
+// ---------------------------------------------------------------- choice of xi
+// Mean device time of `reps` samples of a fresh context with parameters p
+// (two untimed samples first: graph capture and launch-shape tuning), its
+// Lanczos count and grid; with `stage`, also the times of one staged sample's
+// neighbour list + matvecs, k-space noise and FFT.
+static pse_status xi_trial(double L, double a, const pse_params &p, int64_t N, const float *d_pos, float *d_out,
+                           int reps, cudaStream_t s, double *ms, int *iters, int *M, double *stage) {
+    pse_ctx *c = nullptr;
+    pse_status st = create_impl(&c, L, a, &p);
+    if (st != PSE_OK) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    pse_stats stats;
+    for (int i = 0; st == PSE_OK && i < 2; ++i) st = pse_sample(c, N, d_pos, 1, 900000 + i, d_out, s);
+    if (st == PSE_OK) st = pse_get_stats(c, &stats);
+    if (st == PSE_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) st = PSE_ECUDA;
+    if (st == PSE_OK && cudaEventRecord(e0, s) != cudaSuccess) st = PSE_ECUDA;
+    for (int i = 0; st == PSE_OK && i < reps; ++i) st = pse_sample(c, N, d_pos, 1, 900002 + i, d_out, s);
+    if (st == PSE_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+        st = PSE_ECUDA;
+    if (st == PSE_OK) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        *ms = t / reps;
+        st = pse_get_stats(c, &stats);
+        *iters = stats.lanczos_iters;
+        *M = c->plan.M;
+    }
+    if (st == PSE_OK && stage) {
+        double sm[PSE_NSTAGES];
+        int nl[PSE_NSTAGES];
+        st = pse_profile_stages(c, N, d_pos, 1, 900001, d_out, sm, nl, s);
+        stage[0] = sm[PSE_STAGE_NEIGHBOURS] + sm[PSE_STAGE_MATVEC];
+        stage[1] = sm[PSE_STAGE_WAVE_NOISE];
+        stage[2] = sm[PSE_STAGE_FFT];
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    pse_destroy(c);
+    return st;
+}
+
+// Largest xi whose Sec. II C plan fits a grid of M points per side
+// (k_cut L / pi <= M, eta <= 1, r_cut < L/2), by bisection: the three
+// conditions bound xi from above, above and below.  0 if none fits.
+static double xi_max_for_grid(double L, double a, const pse_params &p0, int M) {
+    pse_params p = p0;
+    p.grid_M = M;
+    auto fits = [&](double xi) {
+        p.xi = xi;
+        pse_plan_info pl;
+        if (pse_plan(L, a, &p, &pl) != PSE_OK) return false;
+        return ceil(pl.k_cut * L / 3.141592653589793 - 1e-9) <= M;
+    };
+    double lo = sqrt(log(1.0 / p0.tol)) / (0.5 * L) * (1.0 + 1e-9);
+    if (!fits(lo)) return 0.0;
+    double hi = 2.0 * lo;
+    while (fits(hi)) {
+        lo = hi;
+        hi *= 2.0;
+        if (hi > 1e6 / a) return lo;
+    }
+    for (int it = 0; it < 50; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (fits(mid)) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+static int planned_grid(double L, double a, const pse_params &p0, double xi) {
+    pse_params p = p0;
+    p.xi = xi;
+    p.grid_M = 0;
+    pse_plan_info pl;
+    return pse_plan(L, a, &p, &pl) == PSE_OK ? pl.M : 0;
+}
+
+pse_status pse_tune_xi(double L, double a, const pse_params *p, int64_t N, const float *d_pos, double d_f, int reps,
+                       pse_xi_tuning *out, void *stream) {
+    if (!p || !out || !d_pos || N < 1) return PSE_EINVAL;
+    memset(out, 0, sizeof(*out));
+    if (p->precision != PSE_FP32 || p->use_precond) return PSE_ENOTSUPPORTED;
+    if (d_f == 0.0) d_f = 3.0;
+    if (!(d_f >= 1.0 && d_f <= 3.0) || !(a > 0) || reps < 0 || reps > 1000) return PSE_EINVAL;
+    if (reps == 0) reps = 5;
+    cudaStream_t s = (cudaStream_t)stream;
+    float *d_out = nullptr;
+    CK(cudaMalloc(&d_out, sizeof(float) * 3 * N));
+    const double xi0 = p->xi > 0 ? p->xi : 0.5 / a;
+    pse_params p0 = *p;
+    p0.xi = xi0;
+    out->xi_start = xi0;
+    double stage[3];
+    pse_status st = xi_trial(L, a, p0, N, d_pos, d_out, reps, s, &out->ms_tried[0], &out->iters_tried[0],
+                             &out->M_tried[0], stage);
+    if (st == PSE_OK) {
+        out->t_real = stage[0];
+        out->t_wave = stage[1] + stage[2];
+        st = pse_xi_model(xi0, out->t_real, out->t_wave, d_f, &out->xi_model);
+    }
+    if (st != PSE_OK) {
+        cudaFree(d_out);
+        return st;
+    }
+    out->xi_tried[0] = xi0;
+    out->ms_pred[0] = out->ms_tried[0];
+    out->ms_start = out->ms_tried[0];
+    const int M0 = out->M_tried[0];
+    // Candidate grids: the smooth sizes the plan gives between 0.75 and 1.35
+    // times xi*.  On a fixed grid the wave part costs the same for every xi
+    // that fits it while the real part shrinks as xi grows, so each grid is
+    // taken at the largest xi it admits.
+    pse_params pg = p0;
+    pg.autotune &= ~1;  // the grid is fixed per candidate
+    int Mlo = 0;
+    for (double f = 0.75; f < 1.4 && !Mlo; f += 0.05) Mlo = planned_grid(L, a, pg, out->xi_model * f);
+    int Mhi = planned_grid(L, a, pg, out->xi_model * 1.35);
+    if (!Mlo) Mlo = M0;
+    if (!Mhi || Mhi < Mlo) Mhi = Mlo;
+    int Ms[PSE_XI_GRIDS];
+    double xis[PSE_XI_GRIDS];
+    int ng = 0;
+    for (int M = Mlo; M <= Mhi && ng < PSE_XI_GRIDS; ++M) {
+        if (!smooth_2357(M)) continue;
+        const double xi = xi_max_for_grid(L, a, pg, M);
+        if (xi <= 0.0) continue;
+        Ms[ng] = M;
+        xis[ng++] = xi;
+    }
+    out->n_grids = ng;
+    float fft_ms[PSE_XI_GRIDS];
+    time_fft_sizes<float>(Ms, ng, fft_ms);
+    // predicted sample time per grid: eq. work's xi-dependent terms from the
+    // start context, the FFT as timed, the rest unchanged
+    double pred[PSE_XI_GRIDS];
+    for (int i = 0; i < ng; ++i)
+        pred[i] = out->ms_start - out->t_real - out->t_wave + out->t_real * pow(xi0 / xis[i], d_f) +
+                  stage[1] * pow((double)Ms[i] / M0, 3) + fft_ms[i];
+    int k = 1;
+    for (; k < PSE_XI_TRIALS; ++k) {  // time the best predictions in order
+        int b = -1;
+        for (int i = 0; i < ng; ++i)
+            if (pred[i] < 1e29 && (b < 0 || pred[i] < pred[b])) b = i;
+        if (b < 0) break;
+        pse_params pt = pg;
+        pt.xi = xis[b];
+        pt.grid_M = Ms[b];
+        out->xi_tried[k] = xis[b];
+        out->ms_pred[k] = pred[b];
+        pred[b] = 1e30;
+        const pse_status r = xi_trial(L, a, pt, N, d_pos, d_out, reps, s, &out->ms_tried[k], &out->iters_tried[k],
+                                      &out->M_tried[k], nullptr);
+        if (r == PSE_ECUDA || r == PSE_ECUFFT) {
+            cudaFree(d_out);
+            return r;
+        }
+        if (r != PSE_OK) {  // not usable: list overflow, no convergence within max_iter
+            out->ms_tried[k] = -1.0;
+            out->M_tried[k] = Ms[b];
+        }
+    }
+    out->n_tried = k;
+    out->xi_best = xi0;
+    out->M_best = M0;
+    out->ms_best = out->ms_start;
+    for (int i = 1; i < k; ++i)
+        if (out->ms_tried[i] > 0 && out->ms_tried[i] < out->ms_best) {
+            out->ms_best = out->ms_tried[i];
+            out->xi_best = out->xi_tried[i];
+            out->M_best = out->M_tried[i];
+        }
+    cudaFree(d_out);
     CK(cudaGetLastError());
     return PSE_OK;
 }

@@ -321,6 +321,7 @@ template <typename T> struct Dev {
     V4<T> *table_c;      // PSE_TABLEC_N, same columns, on the two-segment knots
     void *spec;          // 3 * M * M * Mh1 complex
     T *grid;             // 3 * M^3 real
+    V4<T> *grid4;        // M^3 node-major copy (x, y, z, 0) of grid for the interpolation (float)
     SampleArgs<T> *args;
 };
 

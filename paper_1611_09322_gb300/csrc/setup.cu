@@ -185,6 +185,20 @@ extern "C" pse_status pse_real_scalars(double xi, double a, int64_t n, const dou
     return PSE_OK;
 }
 
+// Sec. II C, eqs. work and xistar with the constants calibrated at xi0: the
+// xi-dependent work is T_R (xi0/xi)^d_f + T_W (xi/xi0)^3 (neighbours within
+// r_cut ~ 1/xi grow as r_cut^d_f; Fourier modes ~ k_cut^3 ~ xi^3, the FFT's
+// logarithm and n_iter held at their xi0 values), whose stationary point is
+// xi* = xi0 (d_f T_R / (3 T_W))^(1/(d_f + 3)).
+extern "C" pse_status pse_xi_model(double xi0, double t_real, double t_wave, double d_f, double *xi_star) {
+    if (!xi_star) return PSE_EINVAL;
+    if (!(xi0 > 0) || !(t_real > 0) || !(t_wave > 0) || !isfinite(xi0) || !isfinite(t_real) || !isfinite(t_wave))
+        return PSE_EINVAL;
+    if (!(d_f >= 1.0 && d_f <= 3.0)) return PSE_EINVAL;
+    *xi_star = xi0 * pow(d_f * t_real / (3.0 * t_wave), 1.0 / (d_f + 3.0));
+    return PSE_OK;
+}
+
 extern "C" const char *pse_strerror(pse_status s) {
     switch (s) {
         case PSE_OK: return "ok";

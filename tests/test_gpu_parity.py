@@ -74,18 +74,41 @@ def test_wave_part(torch, N, phi, xi, tol):
     s.close()
 
 
-@pytest.mark.parametrize("N,phi", [(3001, 0.2), (6000, 0.4), (64, 0.1)])
-def test_interpolation_dense_and_tiny(torch, N, phi):
-    """The wave sample for a dense packing and a box of a few grid nodes."""
+@pytest.mark.parametrize("N,phi,form", [(3001, 0.2, 0), (6000, 0.4, 0), (64, 0.1, 0), (3001, 0.2, 1),
+                                        (64, 0.1, 1)])
+def test_interpolation_dense_and_tiny(torch, N, phi, form):
+    """The wave sample for a dense packing and a box of a few grid nodes, with
+    the node-major grid copy (form 0) and from the planar grids (form 1)."""
     from oracle import ewald, pse
     pos, L, _ = _hs(N, phi, 16)
     plan = ewald.plan(L, 1.0, 0.5, 1e-3)
-    s = _sampler(L, xi=0.5, tol=1e-3, fixed_iter=2)
+    s = _sampler(L, xi=0.5, tol=1e-3, fixed_iter=2, interp_form=form)
     _, _, w = s.sample(torch.from_numpy(pos).cuda(), SEED, 6, parts=True)
     got = w.cpu().numpy()
     ref = pse.wave_sample_grid(pos.astype(np.float64), plan, SEED, 6)
     assert _rel(got, ref) < 1e-4 and _maxrel(got, ref) < 1e-4, (_rel(got, ref), _maxrel(got, ref))
     s.close()
+
+
+@pytest.mark.parametrize("tol,xi", [(1e-2, 0.5), (5e-3, 0.5), (1e-4, 0.5), (3e-5, 0.5), (1e-5, 0.6), (1e-6, 0.5),
+                                    (3e-7, 0.5), (1e-7, 0.5)])
+def test_interpolation_support_sizes(torch, tol, xi):
+    """Node-major interpolation for every compiled support P = 3 .. 10 (tol
+    1e-2 .. 3e-7) and the planar fallback beyond it (P = 11 at 1e-7) against
+    the oracle's wave sample, and equal to the planar form."""
+    from oracle import ewald, pse
+    N = 1200
+    pos, L, _ = _hs(N, 0.15, 17)
+    plan = ewald.plan(L, 1.0, xi, tol)
+    outs = []
+    for form in (0, 1):
+        s = _sampler(L, xi=xi, tol=tol, fixed_iter=1, interp_form=form)
+        assert s.plan["P"] == plan.P
+        _, _, w = s.sample(torch.from_numpy(pos).cuda(), SEED, 2, parts=True)
+        outs.append(w.cpu().numpy())
+        s.close()
+    ref = pse.wave_sample_grid(pos.astype(np.float64), plan, SEED, 2)
+    assert _maxrel(outs[0], ref) < 1e-4 and _maxrel(outs[0], outs[1]) < 1e-5, plan.P
 
 
 @pytest.mark.parametrize("N,phi,J", [(1000, 0.1, 6), (1000, 0.1, 1), (1500, 0.3, 12), (130, 0.2, 30)])
