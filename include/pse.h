@@ -72,7 +72,12 @@ typedef struct {
                             bit 1: time every spreading tile shape at the first
                             forces call and keep the fastest.
                             bit 2: time every near-field matvec launch shape
-                            at the first sample and keep the fastest.          */
+                            at the first sample and keep the fastest.
+                            bit 3: once the grid is fixed (planned, tuned or
+                            given), raise xi to the largest value whose
+                            Sec. II C plan fits that grid: the wave part
+                            costs the same, r_cut and the near-field work
+                            shrink (pse_get_plan reports the xi used).      */
     int system;          /* Philox stream index of this system (streams 2*system
                             and 2*system + 1): independent noise for systems
                             sampled side by side; 0 by default                 */
@@ -368,6 +373,7 @@ enum {
     PSE_STAGE_WAVE_NOISE,     /* k-space noise and B^{1/2} scaling            */
     PSE_STAGE_FFT,            /* cuFFT C2R, three components                  */
     PSE_STAGE_INTERP,         /* Gaussian interpolation at the particles      */
+    PSE_STAGE_GRID_COPY,      /* node-major copy of the velocity grid (FP32)  */
     PSE_NSTAGES
 };
 

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libpse.so")
 PSE_FP32, PSE_FP64 = 0, 1
 PSE_PRECOND_NPARAM = 450
 STAGES = ["cells", "sort", "real_noise", "neighbours", "matvec", "lanczos_update", "eigen", "final",
-          "wave_noise", "fft", "interp"]
+          "wave_noise", "fft", "interp", "grid_copy"]
 STATUS = {0: "PSE_OK", 1: "PSE_EINVAL", 2: "PSE_ENOMEM", 3: "PSE_ECUDA", 4: "PSE_ECUFFT",
           5: "PSE_ENOTCONVERGED", 6: "PSE_ENOTSUPPORTED", 7: "PSE_ENOTREADY"}
 

@@ -614,11 +614,17 @@ void launch_wave_noise(WaveGeom<T> w, const SampleArgs<T> *args, int system, voi
     const int64_t plane = (int64_t)w.M * w.M * w.Mh1;
     k_wave_noise<T><<<nbw(plane, 256), 256, 0, s>>>(w, args, system, (typename Cplx<T>::type *)spec, plane);
 }
-template <typename T> void launch_interp(int64_t N, WaveGeom<T> w, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
+template <typename T> void launch_grid_copy(WaveGeom<T> w, const Dev<T> &d, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
         if (w.interp_lanes == 0 && w.P >= 3 && w.P <= 10) {
             const int64_t M3 = (int64_t)w.M * w.M * w.M;
             k_grid_aos<<<nbw(M3, 256), 256, 0, s>>>(M3, d.grid, d.grid4);
+        }
+    }
+}
+template <typename T> void launch_interp(int64_t N, WaveGeom<T> w, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (w.interp_lanes == 0 && w.P >= 3 && w.P <= 10) {
             switch (w.P) {
                 case 3: interp4<3>(N, w, d, s); break;
                 case 4: interp4<4>(N, w, d, s); break;
@@ -688,6 +694,7 @@ cudaError_t launch_spread(WaveGeom<T> w, Geom<T> g, SpreadTile st, const int *or
 #define PSE_INST(T)                                                                                      \
     template void launch_wave_noise<T>(WaveGeom<T>, const SampleArgs<T> *, int, void *, cudaStream_t); \
     template void launch_interp<T>(int64_t, WaveGeom<T>, Geom<T>, const Dev<T> &, cudaStream_t);       \
+    template void launch_grid_copy<T>(WaveGeom<T>, const Dev<T> &, cudaStream_t);                        \
     template void launch_wave_apply<T>(WaveGeom<T>, const SampleArgs<T> *, int, void *, int, int, cudaStream_t); \
     template void launch_grid_noise<T>(WaveGeom<T>, const SampleArgs<T> *, int, T *, cudaStream_t);   \
     template cudaError_t launch_spread<T>(WaveGeom<T>, Geom<T>, SpreadTile, const int *, const int2 *, const int *, \

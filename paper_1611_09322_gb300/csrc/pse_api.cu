@@ -425,6 +425,7 @@ template <typename T> void real_setup(pse_ctx *c, int64_t N, cudaStream_t s) {
 }
 
 template <typename T> void interp(pse_ctx *c, int64_t N, cudaStream_t s) {
+    launch_grid_copy<T>(wgeom<T>(c), dev<T>(c), s);
     launch_interp<T>(N, wgeom<T>(c), geom<T>(c), dev<T>(c), s);
 }
 
@@ -880,6 +881,34 @@ template <typename T> pse_status tune_fft_size(int M0, int *best_M) {
     return PSE_OK;
 }
 
+// Largest xi whose Sec. II C plan fits a grid of M points per side
+// (k_cut L / pi <= M, eta <= 1, r_cut < L/2), by bisection: the three
+// conditions bound xi from above, above and below.  0 if none fits.
+double xi_max_for_grid(double L, double a, const pse_params &p0, int M) {
+    pse_params p = p0;
+    p.grid_M = M;
+    auto fits = [&](double xi) {
+        p.xi = xi;
+        pse_plan_info pl;
+        if (pse_plan(L, a, &p, &pl) != PSE_OK) return false;
+        return ceil(pl.k_cut * L / 3.141592653589793 - 1e-9) <= M;
+    };
+    double lo = sqrt(log(1.0 / p0.tol)) / (0.5 * L) * (1.0 + 1e-9);
+    if (!fits(lo)) return 0.0;
+    double hi = 2.0 * lo;
+    while (fits(hi)) {
+        lo = hi;
+        hi *= 2.0;
+        if (hi > 1e6 / a) return lo;
+    }
+    for (int it = 0; it < 50; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (fits(mid)) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 pse_status create_impl(pse_ctx **out, double L, double a, const pse_params *p) {
     if (!out) return PSE_EINVAL;
     *out = nullptr;
@@ -894,6 +923,15 @@ pse_status create_impl(pse_ctx **out, double L, double a, const pse_params *p) {
         st = (p->precision == PSE_FP64) ? tune_fft_size<double>(c->plan.M, &Mbest) : tune_fft_size<float>(c->plan.M, &Mbest);
         if (st == PSE_OK && Mbest != c->plan.M) {
             c->params.grid_M = Mbest;
+            st = pse_plan(L, a, &c->params, &c->plan);
+            if (st != PSE_OK) { delete c; return st; }
+        }
+    }
+    if (p->autotune & 8) {  // the largest xi the final grid admits: same wave cost, shorter r_cut
+        const double xi = xi_max_for_grid(L, a, c->params, c->plan.M);
+        if (xi > c->plan.xi) {
+            c->params.xi = xi;
+            c->params.grid_M = c->plan.M;
             st = pse_plan(L, a, &c->params, &c->plan);
             if (st != PSE_OK) { delete c; return st; }
         }
@@ -1105,7 +1143,11 @@ pse_status pse_profile_stages(pse_ctx *c, int64_t N, const float *d_pos, uint64_
         CKF(cufftExecC2R(c->fft, (cufftComplex *)d.spec, (cufftReal *)d.grid));
         return PSE_OK; });
     if (r == PSE_OK)
-        r = timed(PSE_STAGE_INTERP, c->wf.interp_lanes == 0 ? 2 : 1, [&] { interp<float>(c, N, s); return PSE_OK; });
+        r = timed(PSE_STAGE_GRID_COPY, c->wf.interp_lanes == 0 ? 1 : 0, [&] {
+            launch_grid_copy<float>(c->wf, c->df, s);
+            return PSE_OK; });
+    if (r == PSE_OK)
+        r = timed(PSE_STAGE_INTERP, 1, [&] { launch_interp<float>(N, c->wf, c->gf, c->df, s); return PSE_OK; });
     if (r == PSE_OK) r = timed(PSE_STAGE_NEIGHBOURS, 1, [&] {
         launch_nbr<float>(N, c->gf, d, s);
         return PSE_OK; });
@@ -1172,34 +1214,6 @@ static pse_status xi_trial(double L, double a, const pse_params &p, int64_t N, c
     return st;
 }
 
-// Largest xi whose Sec. II C plan fits a grid of M points per side
-// (k_cut L / pi <= M, eta <= 1, r_cut < L/2), by bisection: the three
-// conditions bound xi from above, above and below.  0 if none fits.
-static double xi_max_for_grid(double L, double a, const pse_params &p0, int M) {
-    pse_params p = p0;
-    p.grid_M = M;
-    auto fits = [&](double xi) {
-        p.xi = xi;
-        pse_plan_info pl;
-        if (pse_plan(L, a, &p, &pl) != PSE_OK) return false;
-        return ceil(pl.k_cut * L / 3.141592653589793 - 1e-9) <= M;
-    };
-    double lo = sqrt(log(1.0 / p0.tol)) / (0.5 * L) * (1.0 + 1e-9);
-    if (!fits(lo)) return 0.0;
-    double hi = 2.0 * lo;
-    while (fits(hi)) {
-        lo = hi;
-        hi *= 2.0;
-        if (hi > 1e6 / a) return lo;
-    }
-    for (int it = 0; it < 50; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (fits(mid)) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
-
 static int planned_grid(double L, double a, const pse_params &p0, double xi) {
     pse_params p = p0;
     p.xi = xi;
@@ -1222,6 +1236,7 @@ pse_status pse_tune_xi(double L, double a, const pse_params *p, int64_t N, const
     const double xi0 = p->xi > 0 ? p->xi : 0.5 / a;
     pse_params p0 = *p;
     p0.xi = xi0;
+    p0.autotune &= ~8;  // every trial keeps the xi it is given
     out->xi_start = xi0;
     double stage[3];
     pse_status st = xi_trial(L, a, p0, N, d_pos, d_out, reps, s, &out->ms_tried[0], &out->iters_tried[0],
@@ -1498,6 +1513,7 @@ extern "C" pse_status pse_batch_create(pse_batch **out, int nsys, const double *
         pse_params q = p[k];
         q.system = k;
         q.autotune &= ~1;  // the size class replaces the per-system FFT-size timing
+        q.interp_form = 1;  // the fused batch interpolation reads the pooled planar grids
         if (q.grid_M <= 0) {
             pse_plan_info pi;
             st = pse_plan(L[k], a[k], &q, &pi);

@@ -414,6 +414,8 @@ template <typename T> void launch_matvec_caller(int64_t N, const SampleArgs<T> *
 template <typename T> void launch_wave_noise(WaveGeom<T> w, const SampleArgs<T> *args, int system, void *spec,
                                              cudaStream_t s);
 template <typename T> void launch_interp(int64_t N, WaveGeom<T> w, Geom<T> g, const Dev<T> &d, cudaStream_t s);
+// node-major copy of the velocity grid for the FP32 interpolation (no-op otherwise)
+template <typename T> void launch_grid_copy(WaveGeom<T> w, const Dev<T> &d, cudaStream_t s);
 enum { WAVE_MODE_DET = 0, WAVE_MODE_GRIDNOISE = 1 };
 template <typename T>
 void launch_wave_apply(WaveGeom<T> w, const SampleArgs<T> *args, int system, void *spec, int mode, int with_noise,

@@ -92,3 +92,28 @@ def test_batch_grids_are_size_classes_at_least_the_plan(torch):
         M = b.plan(k)["M"]
         assert M in classes and M >= ewald.plan(L, 1.0, xi, 1e-3).M
     b.close()
+
+
+def test_batch_grid_fit_xi(torch):
+    """autotune bit 3 in a batch: each system keeps its size-class grid and
+    takes the largest xi that grid admits; its sample equals a lone context at
+    that (xi, grid) and the oracle's wave part at that xi."""
+    from oracle import ewald, pse
+    from paper_1611_09322_gb300 import BatchSampler, Sampler, pse_plan
+    systems = _systems()
+    Ls = [L for _, L, _ in systems]
+    b = BatchSampler(Ls, 1.0, params=[dict(xi=xi, tol=1e-3, autotune=8) for _, _, xi in systems])
+    offsets = np.cumsum([0] + [p.shape[0] for p, _, _ in systems])
+    pos_all = torch.from_numpy(np.concatenate([p for p, _, _ in systems])).cuda()
+    out = b.sample(pos_all, offsets, SEED, 6).cpu().numpy()
+    for k, (pos, L, xi) in enumerate(systems):
+        pl = b.plan(k)
+        assert pl["xi"] >= xi and np.ceil(pl["k_cut"] * L / np.pi - 1e-9) <= pl["M"]
+        bigger = pse_plan(L, 1.0, xi=pl["xi"] * 1.001, tol=1e-3, grid_M=pl["M"])
+        assert np.ceil(bigger["k_cut"] * L / np.pi - 1e-9) > pl["M"] or bigger["eta"] > 1
+        s = Sampler(L, 1.0, xi=pl["xi"], tol=1e-3, system=k, grid_M=pl["M"])
+        ref = s.sample(torch.from_numpy(pos).cuda(), SEED, 6).cpu().numpy()
+        got = out[offsets[k]:offsets[k + 1]]
+        assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max(), k
+        s.close()
+    b.close()

@@ -108,3 +108,24 @@ def test_tuned_headline_workload_full_size(torch):
     refw = pse.interpolate(vg, pos[rows].astype(np.float64), plan)
     assert _maxrel(uw.cpu().numpy()[rows], refw) < 1e-4
     s.close()
+
+
+def test_grid_fit_xi_lone_context(torch):
+    """autotune bit 3: the planned (or FFT-tuned) grid is kept and xi raised to
+    the largest value it admits; the sample matches the oracle at that xi."""
+    from oracle import ewald, pse
+    from paper_1611_09322_gb300 import Sampler, workloads
+    pos, L, _ = workloads.hard_spheres(3000, 0.2, 12)
+    M0 = ewald.plan(L, 1.0, 0.5, 1e-3).M
+    for at in (8, 9):
+        s = Sampler(L, 1.0, xi=0.5, tol=1e-3, autotune=at)
+        pl = s.plan
+        assert pl["xi"] >= 0.5 and (at == 9 or pl["M"] == M0) and pl["M"] >= M0
+        assert _grid_fits(L, pl["xi"], pl["M"]) and not _grid_fits(L, pl["xi"] * 1.001, pl["M"])
+        plan = ewald.plan(L, 1.0, pl["xi"], 1e-3, M=pl["M"])
+        _, ur, uw = s.sample(torch.from_numpy(pos).cuda(), SEED, 4, parts=True)
+        J = s.stats()["lanczos_iters"]
+        ref_r, _, _ = pse.real_sample(pos.astype(np.float64), plan, SEED, 4, n_iter=J)
+        ref_w = pse.wave_sample_grid(pos.astype(np.float64), plan, SEED, 4)
+        assert _maxrel(ur.cpu().numpy(), ref_r) < 1e-4 and _maxrel(uw.cpu().numpy(), ref_w) < 1e-4
+        s.close()
