@@ -364,6 +364,8 @@ def main():
     ap.add_argument("--xi", type=float, default=None,
                     help="skip the xi scan and sample at this xi (with --grid; a profiling aid)")
     ap.add_argument("--grid", type=int, default=0, help="with --xi: the FFT grid per side")
+    ap.add_argument("--interp-form", type=int, default=0, choices=[0, 1],
+                    help="interpolation form of the headline sampler (1: planar grids; a profiling aid)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -397,7 +399,7 @@ def main():
         t = torch.tensor([xi, float(M_grid)], dtype=torch.float64, device=dev)
         dist.broadcast(t, 0)
         xi, M_grid = float(t[0]), int(t[1])
-    s = Sampler(L, 1.0, xi=xi, tol=TOL, grid_M=M_grid)
+    s = Sampler(L, 1.0, xi=xi, tol=TOL, grid_M=M_grid, interp_form=args.interp_form)
     out = torch.empty_like(d_pos)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
