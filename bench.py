@@ -213,6 +213,74 @@ def launches_per_sample(J, learned=False):
     return 12 + (1 if learned else 0) + 3 * J
 
 
+def kernel_roofline(stages, N, M, n_pairs, peak, interp_kernel="k_interp4"):
+    """Per-kernel achieved GB/s (algorithmic bytes per launch / live per-launch
+    time from pse_profile_stages) and its fraction of the measured peak."""
+    interp_bytes = 16 * N + (16 if interp_kernel == "k_interp4" else 12) * M ** 3 + 16 * N
+    per_kernel = {
+        "matvec": ("k_lz_matvec", 32 * N + 4 * N + 4 * n_pairs + 16 * N),
+        "neighbours": ("k_nbr", 16 * N + 4 * n_pairs + 4 * N),
+        "lanczos_update": ("k_lz_update", 80 * N),
+        "interp": (interp_kernel, interp_bytes),
+        "grid_copy": ("k_grid_aos", 28 * M ** 3),
+        "wave_noise": ("k_wave_noise", 24 * M * M * (M // 2 + 1)),
+    }
+    out = {}
+    for stage, (kname, nbytes) in per_kernel.items():
+        ms, n = stages[stage]
+        if n == 0 or ms <= 0:
+            continue
+        per = ms / n
+        gbs = nbytes / (per / 1e3) / 1e9
+        out[kname] = {"ms_per_launch": round(per, 5), "algorithmic_bytes": int(nbytes), "achieved_gbs": round(gbs, 1),
+                      "frac": round(gbs / peak, 4)}
+    return out
+
+
+def variants_configs(dev, flush, stream, steps, peak):
+    """The other workloads at full size: N = 4e6 hard spheres at phi = 0.3 (tol
+    1e-3 and 1e-5) and the 2.5e5 fractal gels (phi = 0.05, 0.1), each at the
+    xi and grid of its own timed scan, plain vs learned preconditioner (network
+    trained on the GPU at that xi and tol): throughput, Lanczos counts and the
+    per-kernel roofline."""
+    import torch
+    from paper_1611_09322_gb300 import Sampler, precond_train, pse_tune_xi, workloads
+    out = {}
+    cases = [("hs_4e6_phi0.3", "hs", 4_000_000, 0.3, 4, 3.0, tol) for tol in (1e-3, 1e-5)]
+    cases += [(f"gel_2.5e5_phi{phi:g}", "gel", 250_000, phi, 3, 2.0, 1e-3) for phi in (0.05, 0.1)]
+    cache = {}
+    for name, kind, N, phi, seed, d_f, tol in cases:
+        if (kind, N, phi) not in cache:
+            cache.clear()
+            cache[(kind, N, phi)] = workloads.make(kind, N, phi, seed)
+        pos, L, _ = cache[(kind, N, phi)]
+        d = torch.from_numpy(pos).to(dev)
+        o = torch.empty_like(d)
+        tun = pse_tune_xi(L, d, xi=XI, tol=tol, d_f=d_f, reps=3, autotune=1)
+        xi, M = tun["xi_best"], tun["M_best"]
+        theta, info = precond_train.train(xi=xi, tol=tol, steps=1500, lr=3e-3)
+        for variant, th in (("plain", None), ("learned", theta)):
+            s = Sampler(L, 1.0, xi=xi, tol=tol, grid_M=M)
+            if th is not None:
+                s.precond_set_weights(th)
+            for i in range(2):
+                s.sample(d, 1, i, out=o)
+            per = timed_steps(lambda i: s.sample(d, 1, 500 + i, out=o), steps, flush, stream)
+            st = s.stats()
+            stages = s.profile_stages(d, 1, 9000, out=o)
+            P = s.plan["P"]
+            out[f"{name}_tol{tol:g}_{variant}"] = {
+                "value": N * steps / (sum(per) / 1e3), "ms_per_step": sum(per) / steps, "unit": UNIT,
+                "lanczos_iters": st["lanczos_iters"], "converged": st["converged"], "xi": round(xi, 5), "M": M,
+                "P": P, "n_pairs": st["n_pairs"], "xi_start_ms": round(tun["ms_start"], 4),
+                "kernels": kernel_roofline(stages, N, M, st["n_pairs"], peak,
+                                           "k_interp4" if 3 <= P <= 10 else "k_interp")}
+            s.close()
+        del d, o
+        torch.cuda.empty_cache()
+    return out
+
+
 def variants_learned_batched(dev, flush, stream, steps, xi, M):
     """The metric's comparison: learned preconditioner and batching vs plain."""
     import numpy as np
@@ -451,6 +519,7 @@ def main():
     roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": captured_traffic(kname, plan["xi"], M), "peak_kind": f"{peak_kind} hbm_gbs (copy), burst",
                 "algorithmic_bytes_per_launch": kb, "ms_per_launch": round(kms, 5), "dominant_stage": dom,
+                "kernels": kernel_roofline(stages, N_PART, M, n_pairs, peak),
                 "stages_ms": {k: round(v[0], 4) for k, v in stages.items()},
                 "stages_launches": {k: v[1] for k, v in stages.items()}}
 
@@ -480,6 +549,7 @@ def main():
                 "parallelism": "replicas" if ws > 1 else "single GPU"}
         if not args.no_variants:
             line["variants"] = variants_learned_batched(dev, flush, stream, max(20, args.steps // 4), xi, M_grid)
+            line["variants"].update(variants_configs(dev, flush, stream, 10, peak))
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(xi)
         print(json.dumps(line), flush=True)
