@@ -131,6 +131,7 @@ __device__ __forceinline__ int nbr_elem(int64_t s, int64_t N, const Geom<T> &g, 
         const int nc = g.nc;
         int cx, cy, cz;
         cell_xyz(c, g.nb, cx, cy, cz);
+        int *dst = nbr + s;  // ELL column cnt of row s
         for (int ox = -1; ox <= 1; ++ox) {
             int ax = cx + ox;
             ax += ax < 0 ? nc : 0;
@@ -149,15 +150,19 @@ __device__ __forceinline__ int nbr_elem(int64_t s, int64_t N, const Geom<T> &g, 
                     const int code = ((ox + 1) << 4) | ((oy + 1) << 2) | (oz + 1);
                     const int c2 = cell_id(ax, ay, az, g.nb);
                     const int b = cell_start[c2], e = cell_start[c2 + 1];
+                    const int self = code == 21 ? (int)s : -1;  // the particle itself, in its own cell
                     for (int t = b; t < e; ++t) {
-                        if (t == s && code == 21) continue;
+                        if (t == self) continue;
                         const V4<T> lt = loc[t];
                         const T dx = (li.x - lt.x) - sx;
                         const T dy = (li.y - lt.y) - sy;
                         const T dz = (li.z - lt.z) - sz;
                         const T r2 = dx * dx + dy * dy + dz * dz;
                         if (r2 < g.rc2) {
-                            if (cnt < K) nbr[(int64_t)cnt * N + s] = (t << 6) | code;
+                            if (cnt < K) {
+                                *dst = (t << 6) | code;
+                                dst += N;
+                            }
                             ++cnt;
                         }
                     }
@@ -253,7 +258,7 @@ __global__ void k_cellsort_batch(const BSys *__restrict__ sys, const int *__rest
     for (int64_t c = lb * (int64_t)blockDim.x + threadIdx.x; c < S.nc3; c += stride)
         cellsort_cell<float>((int)c, S.d.cell_start, S.d.pos_sorted, S.d.loc_sorted, S.d.rec);
 }
-__global__ void __launch_bounds__(128) k_nbr_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
+__global__ void __launch_bounds__(128, 8) k_nbr_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
     PSE_BATCH_SYS(BK_NBR);
     for (int64_t s0 = lb * (int64_t)blockDim.x; s0 < S.N; s0 += stride) {  // uniform per block
         const int64_t s = s0 + threadIdx.x;
