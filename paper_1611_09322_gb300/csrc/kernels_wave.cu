@@ -17,18 +17,9 @@ template <typename T> struct Cplx;
 template <> struct Cplx<float> { using type = cufftComplex; };
 template <> struct Cplx<double> { using type = cufftDoubleComplex; };
 
-template <typename T> __device__ __forceinline__ T sinc_over_k(T k, T a) {
-    const T ka = k * a;
-    if constexpr (sizeof(T) == 4) return sinf(ka) / (ka * k);
-    else return sin(ka) / (ka * k);
-}
 template <typename T> __device__ __forceinline__ T exp_t(T x) {
     if constexpr (sizeof(T) == 4) return expf(x);
     else return exp(x);
-}
-template <typename T> __device__ __forceinline__ T sqrt_t(T x) {
-    if constexpr (sizeof(T) == 4) return sqrtf(x);
-    else return sqrt(x);
 }
 
 // Mode (ix, iy, iz) of the half spectrum, iz in [0, M/2]: signed indices,
@@ -37,11 +28,27 @@ struct ModeIdx {
     int ix, iy, iz, nx, ny, nz;
     bool live;
 };
-__device__ __forceinline__ ModeIdx mode_of(int64_t t, int M, int Mh1) {
+// n / d for 32-bit n with the multiplier m and shift l of d >= 2
+// (Granlund and Montgomery, PLDI 1994, the round-up method).
+__device__ __forceinline__ uint32_t udiv_magic(uint32_t n, uint32_t m, int l) {
+    const uint32_t t1 = __umulhi(m, n);
+    return (t1 + ((n - t1) >> 1)) >> (l - 1);
+}
+template <typename T> __device__ __forceinline__ ModeIdx mode_of(int64_t t, const WaveGeom<T> &w) {
     ModeIdx m;
-    m.iz = (int)(t % Mh1);
-    m.iy = (int)((t / Mh1) % M);
-    m.ix = (int)(t / ((int64_t)Mh1 * M));
+    const int M = w.M, Mh1 = w.Mh1;
+    if (!w.big) {
+        const uint32_t u = (uint32_t)t;
+        const uint32_t r = udiv_magic(u, w.dv_h1_m, w.dv_h1_l);
+        const uint32_t x = udiv_magic(r, w.dv_M_m, w.dv_M_l);
+        m.iz = (int)(u - r * (uint32_t)Mh1);
+        m.iy = (int)(r - x * (uint32_t)M);
+        m.ix = (int)x;
+    } else {
+        m.iz = (int)(t % Mh1);
+        m.iy = (int)((t / Mh1) % M);
+        m.ix = (int)(t / ((int64_t)Mh1 * M));
+    }
     const int half = M / 2;
     m.nx = m.ix <= half ? m.ix : m.ix - M;
     m.ny = m.iy <= half ? m.iy : m.iy - M;
@@ -77,14 +84,25 @@ __device__ __forceinline__ void mode_noise(const ModeIdx &m, int M, int Mh1, uin
 
 // Unit wave vector and the noise scale
 //   sc(k) = V^{-1/2} sinc(ka)/k sqrt(1 + k^2/4xi^2) exp(-(1 - eta) k^2 / 8xi^2)
-// of a live mode.
+// of a live mode.  sc and 1/|n| depend on the integer n^2 = nx^2 + ny^2 + nz^2
+// only; both come from a table evaluated in FP64 on the host.
 template <typename T>
 __device__ __forceinline__ T mode_scale(const ModeIdx &m, const WaveGeom<T> &w, T &hx, T &hy, T &hz) {
-    const T kx = w.kscale * m.nx, ky = w.kscale * m.ny, kz = w.kscale * m.nz;
-    const T k2 = kx * kx + ky * ky + kz * kz;
-    const T k = sqrt_t(k2);
-    hx = kx / k; hy = ky / k; hz = kz / k;
-    return w.inv_sqrtV * sinc_over_k(k, w.a) * sqrt_t(T(1) + k2 * w.inv4xi2) * exp_t(-w.decay * k2);
+    const int n2 = m.nx * m.nx + m.ny * m.ny + m.nz * m.nz;
+    T sc, inv;
+    if constexpr (sizeof(T) == 4) {
+        const float2 e = __ldg(reinterpret_cast<const float2 *>(w.sc_tab) + n2);
+        sc = e.x;
+        inv = e.y;
+    } else {
+        const double2 e = __ldg(reinterpret_cast<const double2 *>(w.sc_tab) + n2);
+        sc = e.x;
+        inv = e.y;
+    }
+    hx = T(m.nx) * inv;
+    hy = T(m.ny) * inv;
+    hz = T(m.nz) * inv;
+    return sc;
 }
 
 // One thread per half-spectrum mode: vhat = sc(k) (I - kk) dW2(k); k = 0 and
@@ -93,7 +111,7 @@ template <typename T>
 __device__ __forceinline__ void wave_noise_elem(int64_t t, const WaveGeom<T> &w, const SampleArgs<T> *args,
                                                 int system, typename Cplx<T>::type *spec, int64_t plane) {
     using C = typename Cplx<T>::type;
-    const ModeIdx m = mode_of(t, w.M, w.Mh1);
+    const ModeIdx m = mode_of(t, w);
     C o0, o1, o2;
     o0.x = o0.y = o1.x = o1.y = o2.x = o2.y = T(0);
     if (m.live) {
@@ -136,7 +154,7 @@ __global__ void k_wave_apply(WaveGeom<T> w, const SampleArgs<T> *args, int syste
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nmodes = (int64_t)w.M * w.M * w.Mh1;
     if (t >= nmodes) return;
-    const ModeIdx m = mode_of(t, w.M, w.Mh1);
+    const ModeIdx m = mode_of(t, w);
     C o[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) o[c].x = o[c].y = T(0);

@@ -131,6 +131,32 @@ void drop_graph(pse_ctx *c) {
     }
 }
 
+// Multiplier and shift for n / d, 32-bit n, d >= 2 (Granlund and Montgomery,
+// PLDI 1994, round-up method): l = ceil(log2 d), m = 2^32 (2^l - d) / d + 1.
+static void magic_div(uint32_t d, uint32_t *m, int *l) {
+    int k = 0;
+    while ((1ull << k) < d) ++k;
+    *l = k;
+    *m = (uint32_t)((((uint64_t)1 << 32) * ((1ull << k) - d)) / d + 1);
+}
+
+// Noise scale per n^2 = nx^2 + ny^2 + nz^2 (FP64): (sc(k), 1/|n|) with k =
+// 2 pi |n| / L and sc(k) = V^{-1/2} sinc(ka)/k sqrt(1 + k^2/4xi^2)
+// exp(-(1 - eta) k^2/8xi^2) (eq. Mwave, the Gaussian's share removed).
+template <typename T> void build_scale_table(const pse_plan_info &p, std::vector<T> &tab) {
+    const int h = p.M / 2;
+    const int64_t n = 3ll * h * h + 1;
+    tab.assign(2 * n, T(0));
+    const double ks = 2 * M_PI / p.L, inv_sqrtV = 1.0 / sqrt(p.L * p.L * p.L);
+    for (int64_t n2 = 1; n2 < n; ++n2) {
+        const double k = ks * sqrt((double)n2), ka = k * p.a, k2 = k * k;
+        const double sc = inv_sqrtV * sin(ka) / (ka * k) * sqrt(1.0 + k2 / (4 * p.xi * p.xi)) *
+                          exp(-(1 - p.eta) * k2 / (8 * p.xi * p.xi));
+        tab[2 * n2] = (T)sc;
+        tab[2 * n2 + 1] = (T)(1.0 / sqrt((double)n2));
+    }
+}
+
 template <typename T> void fill_geom(pse_ctx *c) {
     const pse_plan_info &p = c->plan;
     Geom<T> g{};
@@ -167,6 +193,10 @@ template <typename T> void fill_geom(pse_ctx *c) {
     w.ch2 = (T)(2 * p.xi * p.xi * p.h * p.h / p.eta);
     w.norm = (T)(pow(2 * p.xi * p.xi / (M_PI * p.eta), 1.5) * p.h * p.h * p.h);
     w.inv_M15 = (T)pow((double)p.M, -1.5);
+    const uint64_t nmodes = (uint64_t)p.M * p.M * (p.M / 2 + 1);
+    w.big = nmodes >= (1ull << 32);
+    magic_div((uint32_t)w.Mh1, &w.dv_h1_m, &w.dv_h1_l);
+    magic_div((uint32_t)p.M, &w.dv_M_m, &w.dv_M_l);
     // 0: node-major grid copy + one warp per particle (FP32, P in 3..10)
     w.interp_lanes = (sizeof(T) == 4 && c->params.interp_form == 0 && p.P >= 3 && p.P <= 10) ? 0 : 16;
     wgeom<T>(c) = w;
@@ -221,6 +251,14 @@ template <typename T> pse_status init_ctx(pse_ctx *c) {
     const size_t csize = sizeof(T) * 2;
     if ((st = alloc(c->per_ctx, &d.spec, csize * 3 * plane)) != PSE_OK) return st;
     if ((st = alloc(c->per_ctx, (void **)&d.grid, sizeof(T) * 3 * M * M * M)) != PSE_OK) return st;
+    {
+        std::vector<T> sct;
+        build_scale_table<T>(p, sct);
+        T *d_sct = nullptr;
+        if ((st = alloc(c->per_ctx, (void **)&d_sct, sizeof(T) * sct.size())) != PSE_OK) return st;
+        CK(cudaMemcpy(d_sct, sct.data(), sizeof(T) * sct.size(), cudaMemcpyHostToDevice));
+        wgeom<T>(c).sc_tab = d_sct;
+    }
     if constexpr (sizeof(T) == 4)
         if (c->params.interp_form == 0 && p.P >= 3 && p.P <= 10 &&
             (st = alloc(c->per_ctx, (void **)&d.grid4, sizeof(V4<T>) * M * M * M)) != PSE_OK)

@@ -83,6 +83,10 @@ template <typename T> struct WaveGeom {
     T ch2;               // 2 xi^2 h^2 / eta: Gaussian exponent per squared grid unit
     T norm;              // (2 xi^2 / (pi eta))^{3/2} h^3
     T inv_M15;           // M^{-3/2}: white grid noise -> dW2 normalisation
+    const T *sc_tab;     // per n^2 = nx^2 + ny^2 + nz^2 <= 3 (M/2)^2: (sc(k), 1/|n|) pairs
+    uint32_t dv_h1_m, dv_M_m;  // division of 32-bit mode ids by Mh1 and M: multipliers
+    int dv_h1_l, dv_M_l;       // and shifts (Granlund-Montgomery, round-up form)
+    int big;             // M^2 Mh1 >= 2^32: 64-bit mode ids
     int interp_lanes;    // lanes per particle in the interpolation (8, 16, 32; 0 = pick)
 };
 
