@@ -406,7 +406,7 @@ def run_only(args):
         offsets = np.cumsum([0] + [p.shape[0] for p in pos_list])
         pa = torch.from_numpy(np.concatenate(pos_list)).to(dev)
         po = torch.empty_like(pa)
-        b = BatchSampler(Ls, 1.0, xi=XI, tol=TOL, use_graph=graph)
+        b = BatchSampler(Ls, 1.0, xi=XI, tol=TOL, use_graph=graph, autotune=9)
         for i in range(args.warmup):
             b.sample(pa, offsets, 1, i, out=po)
         per = timed_steps(lambda i: b.sample(pa, offsets, 1, 100 + i, out=po), args.steps, flush, stream)

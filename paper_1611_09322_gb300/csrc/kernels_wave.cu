@@ -551,13 +551,13 @@ __global__ void k_grid_aos(int64_t M3, const float *__restrict__ g, V4<float> *_
 // evaluates the 1-D weights of index c on all three axes, which the group's
 // lanes exchange by shuffles.  The group's partial sums meet in its first lane.
 template <int P>
-__global__ void __launch_bounds__(128) k_interp4(int64_t N, WaveGeom<float> w,
-                                                 const V4<float> *__restrict__ pos_sorted,
-                                                 const V4<float> *__restrict__ grid4, V4<float> *uwave) {
+__device__ __forceinline__ void interp4_warp(int64_t warp0, int64_t N, const WaveGeom<float> &w,
+                                             const V4<float> *__restrict__ pos_sorted,
+                                             const V4<float> *__restrict__ grid4, V4<float> *uwave) {
     constexpr int R = 32 / P;  // particles per warp; lanes R P .. 31 idle
     const int lane = threadIdx.x & 31;
     const int g = lane / P, c = lane - (lane / P) * P;
-    const int64_t s = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * R + g;
+    const int64_t s = warp0 + g;
     const bool act = g < R && s < N;
     const int base = (g < R ? g : 0) * P;  // first lane of the group
     const V4<float> p = pos_sorted[act ? s : 0];
@@ -612,6 +612,42 @@ __global__ void __launch_bounds__(128) k_interp4(int64_t N, WaveGeom<float> w,
     }
 }
 
+template <int P>
+__global__ void __launch_bounds__(128) k_interp4(int64_t N, WaveGeom<float> w,
+                                                 const V4<float> *__restrict__ pos_sorted,
+                                                 const V4<float> *__restrict__ grid4, V4<float> *uwave) {
+    const int64_t warp0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * (32 / P);
+    if (warp0 >= N) return;  // whole warps leave together
+    interp4_warp<P>(warp0, N, w, pos_sorted, grid4, uwave);
+}
+
+// Fused over the systems of a batch: the node-major copy of every system's
+// grid, then the interpolation of every system (all with the same P).
+__global__ void k_grid_aos_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
+    const BSys &S = sys[tab[blockIdx.x]];
+    const int lb = (int)blockIdx.x - S.b0[BK_COPY];
+    const int64_t M3 = (int64_t)S.w.M * S.w.M * S.w.M;
+    const int64_t stride = (int64_t)S.nb[BK_COPY] * blockDim.x;
+    for (int64_t i = lb * (int64_t)blockDim.x + threadIdx.x; i < M3; i += stride) {
+        V4<float> v;
+        v.x = __ldg(S.d.grid + i);
+        v.y = __ldg(S.d.grid + M3 + i);
+        v.z = __ldg(S.d.grid + 2 * M3 + i);
+        v.w = 0.f;
+        S.d.grid4[i] = v;
+    }
+}
+template <int P> __global__ void __launch_bounds__(128) k_interp4_batch(const BSys *__restrict__ sys,
+                                                                         const int *__restrict__ tab) {
+    constexpr int R = 32 / P;
+    const BSys &S = sys[tab[blockIdx.x]];
+    const int lb = (int)blockIdx.x - S.b0[BK_INTERP];
+    const int64_t per_block = (blockDim.x / 32) * R;
+    const int64_t wofs = (threadIdx.x >> 5) * R;
+    for (int64_t base = lb * per_block; base < S.N; base += (int64_t)S.nb[BK_INTERP] * per_block)  // uniform
+        if (base + wofs < S.N) interp4_warp<P>(base + wofs, S.N, S.w, S.d.pos_sorted, S.d.grid4, S.d.uwave);
+}
+
 static inline unsigned nbw(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 template <int P>
@@ -623,8 +659,22 @@ static void interp4(int64_t N, const WaveGeom<float> &w, const Dev<float> &d, cu
 void launch_batch_noise(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s) {
     k_wave_noise_batch<<<nblk[BK_NOISE], 256, 0, s>>>(sys, tab[BK_NOISE]);
 }
-void launch_batch_interp(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s) {
-    k_interp_batch<<<nblk[BK_INTERP], 128, 0, s>>>(sys, tab[BK_INTERP]);
+void launch_batch_interp(const BSys *sys, int *const *tab, const int *nblk, int P4, cudaStream_t s) {
+    if (P4 == 0) {
+        k_interp_batch<<<nblk[BK_INTERP], 128, 0, s>>>(sys, tab[BK_INTERP]);
+        return;
+    }
+    k_grid_aos_batch<<<nblk[BK_COPY], 256, 0, s>>>(sys, tab[BK_COPY]);
+    switch (P4) {
+        case 3: k_interp4_batch<3><<<nblk[BK_INTERP], 128, 0, s>>>(sys, tab[BK_INTERP]); break;
+        case 4: k_interp4_batch<4><<<nblk[BK_INTERP], 128, 0, s>>>(sys, tab[BK_INTERP]); break;
+        case 5: k_interp4_batch<5><<<nblk[BK_INTERP], 128, 0, s>>>(sys, tab[BK_INTERP]); break;
+        case 6: k_interp4_batch<6><<<nblk[BK_INTERP], 128, 0, s>>>(sys, tab[BK_INTERP]); break;
+        case 7: k_interp4_batch<7><<<nblk[BK_INTERP], 128, 0, s>>>(sys, tab[BK_INTERP]); break;
+        case 8: k_interp4_batch<8><<<nblk[BK_INTERP], 128, 0, s>>>(sys, tab[BK_INTERP]); break;
+        case 9: k_interp4_batch<9><<<nblk[BK_INTERP], 128, 0, s>>>(sys, tab[BK_INTERP]); break;
+        default: k_interp4_batch<10><<<nblk[BK_INTERP], 128, 0, s>>>(sys, tab[BK_INTERP]); break;
+    }
 }
 
 template <typename T>

@@ -1481,10 +1481,12 @@ struct pse_batch {
         int M = 0;
         std::vector<int> members;
         void *spec = nullptr, *grid = nullptr;
+        void *grid4 = nullptr;  // node-major copies of the members' grids
         cufftHandle plan = 0;
         bool plan_made = false;
     };
     std::vector<FftGroup> groups;
+    int p4 = 0;  // common support P of the node-major interpolation, 0: planar
     cudaEvent_t ev_sorted = nullptr, ev_wave = nullptr, ev_noise = nullptr;
     std::vector<cudaEvent_t> ev_pre;
     cudaGraphConditionalHandle cond = 0;
@@ -1518,6 +1520,7 @@ extern "C" void pse_batch_destroy(pse_batch *b) {
         if (g.plan_made) cufftDestroy(g.plan);
         if (g.spec) cudaFree(g.spec);
         if (g.grid) cudaFree(g.grid);
+        if (g.grid4) cudaFree(g.grid4);
     }
     if (b->wave) cudaStreamDestroy(b->wave);
     if (b->d_any) cudaFree(b->d_any);
@@ -1594,6 +1597,26 @@ extern "C" pse_status pse_batch_create(pse_batch **out, int nsys, const double *
             pse_ctx *c = b->sys[g.members[i]];
             c->df.spec = (cufftComplex *)g.spec + 3 * plane * i;
             c->df.grid = (float *)g.grid + 3 * M * M * M * i;
+        }
+    }
+    // node-major interpolation when every system has the same support P in
+    // 3..10 (one instantiation serves all): pooled float4 grids per size
+    if (st == PSE_OK) {
+        const int P0 = b->sys[0]->plan.P;
+        bool same = P0 >= 3 && P0 <= 10;
+        for (pse_ctx *c : b->sys) same = same && c->plan.P == P0;
+        if (same) {
+            for (auto &g : b->groups) {
+                const int64_t M = g.M, n = (int64_t)g.members.size();
+                if (cudaMalloc(&g.grid4, sizeof(V4<float>) * M * M * M * n) != cudaSuccess) {
+                    cudaGetLastError();
+                    same = false;
+                    break;
+                }
+                for (int i = 0; i < (int)n; ++i)
+                    b->sys[g.members[i]]->df.grid4 = (V4<float> *)g.grid4 + M * M * M * i;
+            }
+            b->p4 = same ? P0 : 0;
         }
     }
     if (st == PSE_OK && cudaMalloc(&b->d_args, sizeof(SampleArgs<float>) * nsys) != cudaSuccess) {
@@ -1723,16 +1746,18 @@ static pse_status batch_descriptors(pse_batch *b) {
             (d.N + 127) / 128,                                 // neighbours
             0,                                                 // init (set below)
             (modes + 255) / 256,                               // noise
-            (d.N * PSE_BATCH_INTERP_G + 127) / 128,            // interpolation
+            b->p4 ? (d.N + 4 * (32 / b->p4) - 1) / (4 * (32 / b->p4))  // interpolation: 4 warps of
+                  : (d.N * PSE_BATCH_INTERP_G + 127) / 128,       // 32/P particles, or 16 lanes each
             (d.N + 255) / 256,                                 // final (one block per 256, exact)
-            c->pc_enabled ? (d.N + 127) / 128 : 0};            // network blocks (only where installed)
+            c->pc_enabled ? (d.N + 127) / 128 : 0,             // network blocks (only where installed)
+            b->p4 ? ((int64_t)c->plan.M * c->plan.M * c->plan.M + 255) / 256 : 0};  // node-major copy
         for (int kind = 0; kind < PSE_BK; ++kind) {
             int64_t n = n_per[kind];
             if (kind == BK_INIT) {  // the lone context's grid, so beta_0 adds the same partials
                 const int64_t need = (d.N + 255) / 256, cap = (int64_t)num_sms() * 8;
                 n = need < cap ? need : cap;
             }
-            if (n < 1 && kind != BK_PC) n = 1;
+            if (n < 1 && kind != BK_PC && kind != BK_COPY) n = 1;
             if (n > (1 << 24)) return PSE_EINVAL;
             d.b0[kind] = (int)tabs[kind].size();
             d.nb[kind] = (int)n;
@@ -1786,7 +1811,7 @@ static pse_status batch_prologue(pse_batch *b, cudaStream_t s) {
         cudaEventRecord(b->ev_pre[gi], c->s_wave);
         cudaStreamWaitEvent(b->wave, b->ev_pre[gi], 0);
     }
-    launch_batch_interp(b->d_bsys, b->d_btab, b->bnblk, b->wave);
+    launch_batch_interp(b->d_bsys, b->d_btab, b->bnblk, b->p4, b->wave);
     cudaEventRecord(b->ev_wave, b->wave);
     launch_batch_nbr(b->d_bsys, b->d_btab, b->bnblk, s);
     launch_batch_pc_infer(b->d_bsys, b->d_btab, b->bnblk, s);

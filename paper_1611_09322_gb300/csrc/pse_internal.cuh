@@ -385,7 +385,7 @@ struct LzSys {
 // One system of a batch for the fused prologue / epilogue kernels (FP32):
 // sizes, geometry, buffers and, per fused kernel kind, the first block and
 // block count it owns (block -> system tables map the other way).
-enum { BK_ZERO = 0, BK_BIN, BK_SCATTER, BK_SORT, BK_NBR, BK_INIT, BK_NOISE, BK_INTERP, BK_FINAL, BK_PC, PSE_BK };
+enum { BK_ZERO = 0, BK_BIN, BK_SCATTER, BK_SORT, BK_NBR, BK_INIT, BK_NOISE, BK_INTERP, BK_FINAL, BK_PC, BK_COPY, PSE_BK };
 #define PSE_BATCH_INTERP_G 16
 struct BSys {
     int64_t N;
@@ -403,7 +403,8 @@ void launch_batch_nbr(const BSys *sys, int *const *tab, const int *nblk, cudaStr
 void launch_batch_init(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s);
 void launch_batch_final(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s);
 void launch_batch_noise(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s);
-void launch_batch_interp(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s);
+// P4 = the common support P (3..10) of node-major interpolation, 0 for the planar form
+void launch_batch_interp(const BSys *sys, int *const *tab, const int *nblk, int P4, cudaStream_t s);
 void launch_batch_pc_infer(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s);
 void launch_lz_matvec_batch(const LzSys *sys, const int *blk2sys, int nblocks, cudaStream_t s);
 void launch_lz_update_batch(const LzSys *sys, const int *blk2sys, int nblocks, cudaStream_t s);
