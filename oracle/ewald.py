@@ -147,10 +147,17 @@ def plan(L, a, xi, tol, M=None, P=None):
     return Plan(L=L, a=a, xi=xi, tol=tol, r_cut=rc, k_cut=kc, P=P, m=m, M=M, h=h, eta=eta)
 
 
+def unit(rvec):
+    """Unit vectors of rows of rvec; 0 for a zero row.  At r = 0 the App. A
+    scalars meet (F(0) = G(0), eq. self), so the block F (I - rr) + G rr is
+    F I whatever direction is used."""
+    r = np.linalg.norm(rvec, axis=1)
+    return np.divide(rvec, r[:, None], out=np.zeros_like(rvec), where=r[:, None] > 0)
+
+
 def _block(rvec, F, G, a):
     """Pair blocks (F (I - rr) + G rr) / (6 pi a) for rows of rvec (K, 3)."""
-    r = np.linalg.norm(rvec, axis=1)
-    rh = rvec / r[:, None]
+    rh = unit(rvec)
     outer = rh[:, :, None] * rh[:, None, :]
     eye = np.eye(3)[None]
     return (F[:, None, None] * (eye - outer) + G[:, None, None] * outer) / (6 * np.pi * a)
@@ -170,10 +177,13 @@ def mobility_real_dense(pos, L, a, xi, rc):
     R = np.array(np.meshgrid(rng, rng, rng, indexing="ij")).reshape(3, -1).T * L
     d0 = pos[:, None, :] - pos[None, :, :]
     d0 -= L * np.round(d0 / L)
+    same = np.eye(N, dtype=bool)
     for Rv in R:
         d = d0 + Rv
         r = np.linalg.norm(d, axis=2)
-        mask = (r < rc) & (r > 0)
+        # every image pair inside r_cut except a particle with itself at R = 0
+        # (the self term below); distinct particles at r = 0 keep the r -> 0 block
+        mask = (r < rc) & ~(same & (r == 0))
         if not mask.any():
             continue
         ii, jj = np.nonzero(mask)

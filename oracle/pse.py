@@ -376,7 +376,7 @@ class RealOperator:
         r = np.linalg.norm(d, axis=1)
         F, G = rpy.fg(r, xi, a)
         self.i, self.j = i, j
-        self.rh = d / r[:, None] if r.size else d
+        self.rh = ewald.unit(d) if r.size else d
         self.F = F / (6 * np.pi * a)
         self.GmF = (G - F) / (6 * np.pi * a)
         self.self_ = rpy.self_real(xi, a) / (6 * np.pi * a)
@@ -419,7 +419,7 @@ def real_rows(pos, plan, rows, v):
         acc = s * v[i]
         if nb.size:
             F, G = rpy.fg(r, xi, a)
-            rh = d / r[:, None]
+            rh = ewald.unit(d)
             vj = v[nb]
             dot = np.einsum("kd,kd->k", rh, vj)
             acc = acc + ((F[:, None] * vj + ((G - F) * dot)[:, None] * rh) / (6 * np.pi * a)).sum(axis=0)

@@ -254,3 +254,39 @@ def test_invalid_calls(torch):
     with pytest.raises(ValueError):
         s.sample(torch.from_numpy(pos.astype(np.float64)).cuda(), 1, 0)
     s.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_coincident_and_overlapping_particles(torch, prec):
+    """Degenerate configurations: pairs of distinct particles at exactly the
+    same position (block F(0) I, one zero mode each) and pairs a small
+    fraction of a radius apart, inside a random suspension: the near-field
+    product and the J-step real sample match the oracle, the full sample is
+    finite and the Lanczos test converges."""
+    from oracle import ewald, pse
+    pos, L, _ = _hs(600, 0.1, 31)
+    pos = pos.astype(np.float64)
+    pos[1] = pos[0]
+    pos[3] = pos[2]
+    pos[5] = pos[4] + np.array([0.05, 0.0, 0.0])
+    pos[7] = pos[6] + np.array([0.0, 0.3, -0.2])
+    dt = np.float64 if prec else np.float32
+    p = pos.astype(dt)
+    plan = ewald.plan(L, 1.0, 0.5, 1e-3)
+    p64 = p.astype(np.float64)
+    op = pse.RealOperator(p64, plan)
+    v = np.random.default_rng(4).standard_normal((600, 3)).astype(dt)
+    s = _sampler(L, xi=0.5, tol=1e-3, precision=prec)
+    if prec == 0:  # the caller-vector product is an FP32 entry point
+        got = s.real_matvec(torch.from_numpy(p).cuda(), torch.from_numpy(v).cuda()).cpu().numpy()
+        assert _maxrel(got, op(v.astype(np.float64))) < 1e-5
+    u = s.sample(torch.from_numpy(p).cuda(), SEED, 3)
+    st = s.stats()
+    assert torch.isfinite(u).all() and st["converged"] == 1
+    s.close()
+    J = 5
+    s = _sampler(L, xi=0.5, tol=1e-3, precision=prec, fixed_iter=J)
+    _, r, _ = s.sample(torch.from_numpy(p).cuda(), SEED, 4, parts=True)
+    ref, _, _ = pse.real_sample(p64, plan, SEED, 4, n_iter=J)
+    assert _maxrel(r.cpu().numpy(), ref) < (1e-9 if prec else 1e-4)
+    s.close()

@@ -4,7 +4,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import ewald, pse
+from oracle import ewald, pse, rpy
 
 SEED = 20240601
 
@@ -143,3 +143,30 @@ def test_real_rows_match_the_dense_real_mobility():
     got = pse.real_rows(pos, plan, rows, v)
     ref = (Mr @ v.ravel()).reshape(200, 3)[rows]
     assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+def test_coincident_particles_take_the_r_to_zero_limit():
+    """Distinct particles at the same position (the degenerate overlap of App. B):
+    the pair block is the r -> 0 limit F(0) I of App. A (F(0) = G(0), eq. self),
+    so M_r is continuous as two particles merge; it stays positive
+    semi-definite (two coincident spheres act as one, one zero mode); the
+    sparse operator and the row-by-row product agree with the dense matrix."""
+    L, xi = 20.0, 0.5
+    plan = ewald.plan(L, 1.0, xi, 1e-3)
+    base = np.array([[3.0, 4.0, 5.0], [3.0, 4.0, 5.0], [6.2, 4.1, 5.3], [10.0, 10.0, 10.0]])
+    M0 = ewald.mobility_real_dense(base, L, 1.0, xi, plan.r_cut)
+    for eps in (1e-3, 1e-5):
+        moved = base.copy()
+        moved[1, 0] += eps
+        Me = ewald.mobility_real_dense(moved, L, 1.0, xi, plan.r_cut)
+        assert np.abs(Me - M0).max() <= 10 * eps * np.abs(M0).max()
+    # the pair block of the coincident particles is F(0) I = the self term
+    s = rpy.self_real(xi, 1.0) / (6 * math.pi)
+    assert np.allclose(M0[0:3, 3:6], s * np.eye(3), rtol=1e-12, atol=0)
+    w = np.linalg.eigvalsh(M0)
+    assert w.min() >= -1e-12 * w.max() and np.sum(np.abs(w) < 1e-10 * w.max()) == 3
+    op = pse.RealOperator(base, plan)
+    v = np.random.default_rng(3).standard_normal((4, 3))
+    ref = (M0 @ v.ravel()).reshape(4, 3)
+    assert np.allclose(op(v), ref, rtol=1e-12, atol=1e-14)
+    assert np.allclose(pse.real_rows(base, plan, np.arange(4), v), ref, rtol=1e-12, atol=1e-14)
