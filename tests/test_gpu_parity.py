@@ -288,5 +288,31 @@ def test_coincident_and_overlapping_particles(torch, prec):
     s = _sampler(L, xi=0.5, tol=1e-3, precision=prec, fixed_iter=J)
     _, r, _ = s.sample(torch.from_numpy(p).cuda(), SEED, 4, parts=True)
     ref, _, _ = pse.real_sample(p64, plan, SEED, 4, n_iter=J)
-    assert _maxrel(r.cpu().numpy(), ref) < (1e-9 if prec else 1e-4)
+    # each coincident pair gives M_r an exact zero eigenvalue, where the square
+    # root's derivative is unbounded: rounding differences of size eps reach
+    # the result as ~sqrt(eps), so FP64 agrees to 1e-7 here, not to 1e-9
+    assert _maxrel(r.cpu().numpy(), ref) < (1e-7 if prec else 1e-4)
     s.close()
+
+
+def test_empty_inputs_are_rejected_and_leave_the_context_usable(torch):
+    """N = 0 (a single context, or one system of a batch) is refused with
+    PSE_EINVAL before anything is launched; the next valid call works."""
+    from paper_1611_09322_gb300 import BatchSampler, PseError
+    pos, L, _ = _hs(300, 0.1, 32)
+    s = _sampler(L, xi=0.5, tol=1e-3)
+    empty = torch.empty((0, 3), dtype=torch.float32, device="cuda")
+    with pytest.raises(PseError):
+        s.sample(empty, SEED, 0)
+    with pytest.raises(PseError):
+        s.real_matvec(empty, empty)
+    u = s.sample(torch.from_numpy(pos).cuda(), SEED, 0)
+    assert torch.isfinite(u).all() and s.stats()["converged"] == 1
+    s.close()
+    b = BatchSampler([L, L], 1.0, xi=0.5, tol=1e-3)
+    d = torch.from_numpy(pos).cuda()
+    with pytest.raises(PseError):
+        b.sample(d, [0, 300, 300], SEED, 0)
+    out = b.sample(torch.cat([d, d]), [0, 300, 600], SEED, 0)
+    assert torch.isfinite(out).all()
+    b.close()
