@@ -99,7 +99,17 @@ typedef struct {
                             support node, one warp per particle (P in 3..10);
                             1: reads the planar grids directly, 16 lanes per
                             particle                                           */
-    int reserved[1];
+    int wave_fft;        /* FP32 sample path with k-space noise: 0 (default)
+                            cuFFT C2R; 1: on grids M = 64 and 256, the noise
+                            and the inverse FFT as three kernels of this
+                            library (noise generated inside the first pass,
+                            the last pass writing the node-major grid of the
+                            interpolation; needs interp_form = 0), cuFFT on
+                            other grids.  Alone the three passes take about
+                            as long as noise + cuFFT + grid copy (417 vs 434 us
+                            at M = 256); beside the near-field kernels of a
+                            sample their shared memory costs those kernels
+                            L1, so the default is cuFFT                        */
 } pse_params;
 
 /* Parameters derived from (L, a, xi, tol) by Sec. II C of the paper:
@@ -370,8 +380,10 @@ enum {
     PSE_STAGE_LANCZOS_UPDATE, /* three-term update + ||w||, all iterations    */
     PSE_STAGE_EIGEN,          /* FP64 T_j^{1/2} e_1 + stop test, all iterations */
     PSE_STAGE_FINAL,          /* x = V y, + wave part, caller order           */
-    PSE_STAGE_WAVE_NOISE,     /* k-space noise and B^{1/2} scaling            */
-    PSE_STAGE_FFT,            /* cuFFT C2R, three components                  */
+    PSE_STAGE_WAVE_NOISE,     /* k-space noise and B^{1/2} scaling (fused
+                                 path: with the first FFT pass)               */
+    PSE_STAGE_FFT,            /* cuFFT C2R, three components (fused path:
+                                 the second and third passes)                 */
     PSE_STAGE_INTERP,         /* Gaussian interpolation at the particles      */
     PSE_STAGE_GRID_COPY,      /* node-major copy of the velocity grid (FP32)  */
     PSE_NSTAGES

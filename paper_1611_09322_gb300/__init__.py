@@ -20,7 +20,7 @@ __all__ = ["Sampler", "BatchSampler", "pse_plan", "pse_real_scalars", "pse_real_
 
 def make_params(tol=1e-3, xi=0.5, precision=PSE_FP32, max_iter=0, fixed_iter=0, grid_M=0, support_P=0,
                 use_precond=0, lanczos_tol=0.0, use_graph=True, autotune=0, system=0, wave_noise=0,
-                spread_tile=0, matvec_shape=0, interp_form=0):
+                spread_tile=0, matvec_shape=0, interp_form=0, wave_fft=0):
     p = pse_params()
     p.tol = tol
     p.xi = xi
@@ -38,6 +38,7 @@ def make_params(tol=1e-3, xi=0.5, precision=PSE_FP32, max_iter=0, fixed_iter=0, 
     p.spread_tile = spread_tile
     p.matvec_shape = matvec_shape
     p.interp_form = interp_form
+    p.wave_fft = wave_fft
     return p
 
 

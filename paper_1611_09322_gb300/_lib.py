@@ -33,7 +33,7 @@ class pse_params(ctypes.Structure):
                 ("support_P", ctypes.c_int), ("use_precond", ctypes.c_int), ("lanczos_tol", ctypes.c_double),
                 ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int), ("system", ctypes.c_int),
                 ("wave_noise", ctypes.c_int), ("spread_tile", ctypes.c_int),
-                ("matvec_shape", ctypes.c_int), ("interp_form", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("matvec_shape", ctypes.c_int), ("interp_form", ctypes.c_int), ("wave_fft", ctypes.c_int)]
 
 
 class pse_plan_info(ctypes.Structure):

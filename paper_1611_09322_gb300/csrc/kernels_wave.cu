@@ -759,6 +759,279 @@ cudaError_t launch_spread(WaveGeom<T> w, Geom<T> g, SpreadTile st, const int *or
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ fused k-space noise and inverse FFT
+// For grids M = R^2 (R = 8, 16: M = 64, 256; FP32, k-space noise): the
+// unnormalised C2R of the noise spectrum in three passes of our own, the
+// noise generated inside the first pass and the last pass writing the
+// node-major records the interpolation reads (no spectrum written by a noise
+// kernel, no planar grid, no copy).
+//   pass x: per (ky, tile of kz < M/2): noise of the modes, DFT over kx;
+//   pass y: per (ix, tile of kz): DFT over ky, in place in the spectrum buffer;
+//   pass z: per (ix, tile of iy): the real inverse DFT over kz, two real rows
+//           per complex transform (z = IDFT(Ya + i Yb): x_a = Re z, x_b = Im z,
+//           Y extended by Y_{M-k} = conj(Y_k), the Nyquist term Y_{M/2} = 0).
+// Each line of M = R^2 points is transformed by R threads in two register
+// passes (the four-step split n = t + R m, k = k1 + R k2):
+//   A_t[k1] = w_M^{t k1} sum_m x[t + R m] w_R^{m k1},
+//   X[k1 + R k2] = sum_t A_t[k1] w_R^{t k2},  w_L = e^{2 pi i / L},
+// with one padded shared-memory transpose between them.
+constexpr int PSE_FFT_TZ = 8;   // kz values per block in the x and y passes
+constexpr int PSE_FFT_TY = 8;   // iy rows per block in the z pass
+
+template <int R> __device__ __forceinline__ constexpr int bitrev_c(int v) {
+    int r = 0;
+    for (int b = 1; b < R; b <<= 1) {
+        r = (r << 1) | (v & 1);
+        v >>= 1;
+    }
+    return r;
+}
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// In-register radix-2 DIT of R points: v in bit-reversed order, output in
+// natural order, w[k] = w_R^k for k < R/2.
+template <int R> __device__ __forceinline__ void fft_reg(float2 (&v)[R], const float2 (&w)[R / 2]) {
+#pragma unroll
+    for (int half = 1; half < R; half <<= 1) {
+#pragma unroll
+        for (int j = 0; j < R / 2; ++j) {
+            const int pos = j & (half - 1);
+            const int i0 = ((j - pos) << 1) + pos, i1 = i0 + half;
+            const float2 t = cmulf(w[pos * (R / (2 * half))], v[i1]);
+            const float2 a = v[i0];
+            v[i0] = make_float2(a.x + t.x, a.y + t.y);
+            v[i1] = make_float2(a.x - t.x, a.y - t.y);
+        }
+    }
+}
+
+// w_M^j for any j >= 0 from the half-circle table tw[k] = w_M^k, k < M/2.
+template <int M> __device__ __forceinline__ float2 tw_full(const float2 *tw, int j) {
+    j &= M - 1;
+    const float2 e = tw[j & (M / 2 - 1)];
+    return j < M / 2 ? e : make_float2(-e.x, -e.y);
+}
+
+// One line of M = R^2 points, natural order in `line` (stride 1, R (R + 1)
+// entries of room), transformed by the R threads t = 0..R-1 of a group;
+// returns X[t + R k2] in out[k2].  The group's threads must lie in one warp.
+template <int R>
+__device__ __forceinline__ void fft_line_sq(float2 *line, int t, const float2 *tw, const float2 (&wR)[R / 2],
+                                            float2 (&out)[R]) {
+    constexpr int M = R * R;
+    float2 v[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = line[t + R * bitrev_c<R>(m)];
+    fft_reg<R>(v, wR);
+#pragma unroll
+    for (int k1 = 1; k1 < R; ++k1) v[k1] = cmulf(v[k1], tw_full<M>(tw, t * k1));
+    __syncwarp();
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) line[k1 * (R + 1) + t] = v[k1];
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < R; ++m) out[m] = line[t * (R + 1) + bitrev_c<R>(m)];
+    fft_reg<R>(out, wR);
+    __syncwarp();
+}
+
+// Shared-memory line stride: room for the R (R + 1) transpose, padded to
+// 4 mod 16 float2 so that the TZ lines touched by one row of a tile load or
+// store start on different banks.
+template <int R> constexpr int fft_lsz() { return R * (R + 1) + ((4 - R * (R + 1)) % 16 + 16) % 16; }
+
+template <int R> __device__ __forceinline__ void load_wR(const float2 *tw, float2 (&wR)[R / 2]) {
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) wR[k] = tw[k * R];  // w_R^k = w_M^{k R}
+}
+
+// pass x: block = (tile of TZ kz values, ky); threads: 3 TZ lines x R.
+template <int R>
+__global__ void __launch_bounds__(3 * PSE_FFT_TZ * R, 3) k_fftx_noise(WaveGeom<float> w, const SampleArgs<float> *args,
+                                                                   int system, const float2 *__restrict__ tw_g,
+                                                                   float2 *spec) {
+    constexpr int M = R * R, TZ = PSE_FFT_TZ, LSZ = fft_lsz<R>(), Mh1 = M / 2 + 1;
+    extern __shared__ float2 sm[];
+    float2 *tw = sm;           // M/2
+    float2 *buf = sm + M / 2;  // [3 TZ lines][LSZ], line = c * TZ + kzl
+    for (int k = threadIdx.x; k < M / 2; k += blockDim.x) tw[k] = tw_g[k];
+    const int kz0 = blockIdx.x * TZ, ky = blockIdx.y;
+    const uint32_t strm = 2u * system + 1u;
+    const uint64_t seed = args->seed, sample = args->sample;
+    for (int i = threadIdx.x; i < M * TZ; i += blockDim.x) {
+        const int kzl = i % TZ, kx = i / TZ;
+        ModeIdx m;
+        m.ix = kx; m.iy = ky; m.iz = kz0 + kzl;
+        m.nx = kx <= M / 2 ? kx : kx - M;
+        m.ny = ky <= M / 2 ? ky : ky - M;
+        m.nz = m.iz;
+        m.live = kx != M / 2 && ky != M / 2 && (m.nx | m.ny | m.nz) != 0;
+        float2 o0 = make_float2(0.f, 0.f), o1 = o0, o2 = o0;
+        if (m.live) {
+            float wr[3], wi[3];
+            mode_noise<float>(m, M, Mh1, strm, seed, sample, wr, wi);
+            float hx, hy, hz;
+            const float sc = mode_scale<float>(m, w, hx, hy, hz);
+            const float dr = hx * wr[0] + hy * wr[1] + hz * wr[2];
+            const float di = hx * wi[0] + hy * wi[1] + hz * wi[2];
+            o0 = make_float2(sc * (wr[0] - hx * dr), sc * (wi[0] - hx * di));
+            o1 = make_float2(sc * (wr[1] - hy * dr), sc * (wi[1] - hy * di));
+            o2 = make_float2(sc * (wr[2] - hz * dr), sc * (wi[2] - hz * di));
+        }
+        buf[(0 * TZ + kzl) * LSZ + kx] = o0;
+        buf[(1 * TZ + kzl) * LSZ + kx] = o1;
+        buf[(2 * TZ + kzl) * LSZ + kx] = o2;
+    }
+    __syncthreads();
+    float2 wR[R / 2];
+    load_wR<R>(tw, wR);
+    const int line = threadIdx.x / R, t = threadIdx.x % R;
+    float2 out[R];
+    fft_line_sq<R>(buf + line * LSZ, t, tw, wR, out);
+#pragma unroll
+    for (int k2 = 0; k2 < R; ++k2) buf[line * LSZ + t + R * k2] = out[k2];
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * M * TZ; i += blockDim.x) {
+        const int kzl = i % TZ, rest = i / TZ, ix = rest % M, c = rest / M;
+        spec[(((int64_t)c * M + ix) * M + ky) * Mh1 + kz0 + kzl] = buf[(c * TZ + kzl) * LSZ + ix];
+    }
+}
+
+// pass y: block = (tile of TZ kz values, ix); in place.
+template <int R>
+__global__ void __launch_bounds__(3 * PSE_FFT_TZ * R, 3) k_ffty(const float2 *__restrict__ tw_g, float2 *spec) {
+    constexpr int M = R * R, TZ = PSE_FFT_TZ, LSZ = fft_lsz<R>(), Mh1 = M / 2 + 1;
+    extern __shared__ float2 sm[];
+    float2 *tw = sm;
+    float2 *buf = sm + M / 2;
+    for (int k = threadIdx.x; k < M / 2; k += blockDim.x) tw[k] = tw_g[k];
+    const int kz0 = blockIdx.x * TZ, ix = blockIdx.y;
+    for (int i = threadIdx.x; i < 3 * M * TZ; i += blockDim.x) {
+        const int kzl = i % TZ, rest = i / TZ, ky = rest % M, c = rest / M;
+        buf[(c * TZ + kzl) * LSZ + ky] = spec[(((int64_t)c * M + ix) * M + ky) * Mh1 + kz0 + kzl];
+    }
+    __syncthreads();
+    float2 wR[R / 2];
+    load_wR<R>(tw, wR);
+    const int line = threadIdx.x / R, t = threadIdx.x % R;
+    float2 out[R];
+    fft_line_sq<R>(buf + line * LSZ, t, tw, wR, out);
+#pragma unroll
+    for (int k2 = 0; k2 < R; ++k2) buf[line * LSZ + t + R * k2] = out[k2];
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * M * TZ; i += blockDim.x) {
+        const int kzl = i % TZ, rest = i / TZ, ky = rest % M, c = rest / M;
+        spec[(((int64_t)c * M + ix) * M + ky) * Mh1 + kz0 + kzl] = buf[(c * TZ + kzl) * LSZ + ky];
+    }
+}
+
+// pass z: block = (tile of TY iy rows, ix); the 3 TY real rows (c, iyl) are
+// transformed in pairs (c, iyl) + i (c, iyl + TY/2).
+template <int R>
+__global__ void __launch_bounds__(3 * PSE_FFT_TY / 2 * R) k_fftz_c2r(const float2 *__restrict__ tw_g,
+                                                                   const float2 *__restrict__ spec, V4<float> *grid4) {
+    constexpr int M = R * R, H = M / 2, TY = PSE_FFT_TY, LSZ = fft_lsz<R>(), Mh1 = M / 2 + 1, NP = 3 * TY / 2;
+    extern __shared__ float2 sm[];
+    float2 *tw = sm;                      // M/2
+    float2 *raw = tw + M / 2;             // [3][TY][H]
+    float2 *buf = raw + 3 * TY * H;       // [NP][LSZ]
+    float *xo = reinterpret_cast<float *>(raw);  // [3][TY][M], over raw once Z is built
+    for (int k = threadIdx.x; k < M / 2; k += blockDim.x) tw[k] = tw_g[k];
+    const int iy0 = blockIdx.x * TY, ix = blockIdx.y;
+    for (int i = threadIdx.x; i < 3 * TY * H; i += blockDim.x) {
+        const int k = i % H, rest = i / H, iyl = rest % TY, c = rest / TY;
+        raw[i] = spec[(((int64_t)c * M + ix) * M + iy0 + iyl) * Mh1 + k];
+    }
+    __syncthreads();
+    // pair p = c * (TY/2) + j holds rows (c, j) and (c, j + TY/2)
+    for (int i = threadIdx.x; i < NP * M; i += blockDim.x) {
+        const int k = i % M, p = i / M, c = p / (TY / 2), j = p % (TY / 2);
+        const float2 *ra = raw + (c * TY + j) * H, *rb = raw + (c * TY + j + TY / 2) * H;
+        float2 ya, yb;
+        if (k < H) {
+            ya = ra[k];
+            yb = rb[k];
+        } else if (k == H) {
+            ya = yb = make_float2(0.f, 0.f);
+        } else {
+            const float2 a = ra[M - k], b = rb[M - k];
+            ya = make_float2(a.x, -a.y);
+            yb = make_float2(b.x, -b.y);
+        }
+        buf[p * LSZ + k] = make_float2(ya.x - yb.y, ya.y + yb.x);  // Ya + i Yb
+    }
+    __syncthreads();
+    float2 wR[R / 2];
+    load_wR<R>(tw, wR);
+    const int p = threadIdx.x / R, t = threadIdx.x % R;
+    float2 out[R];
+    fft_line_sq<R>(buf + p * LSZ, t, tw, wR, out);
+    {
+        const int c = p / (TY / 2), j = p % (TY / 2);
+        float *xa = xo + (c * TY + j) * M, *xb = xo + (c * TY + j + TY / 2) * M;
+#pragma unroll
+        for (int k2 = 0; k2 < R; ++k2) {
+            xa[t + R * k2] = out[k2].x;
+            xb[t + R * k2] = out[k2].y;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < TY * M; i += blockDim.x) {
+        const int iz = i % M, iyl = i / M;
+        V4<float> v;
+        v.x = xo[(0 * TY + iyl) * M + iz];
+        v.y = xo[(1 * TY + iyl) * M + iz];
+        v.z = xo[(2 * TY + iyl) * M + iz];
+        v.w = 0.f;
+        grid4[((int64_t)ix * M + iy0 + iyl) * M + iz] = v;
+    }
+}
+
+template <int R> static size_t fft_smem_xy() {
+    return sizeof(float2) * (R * R / 2 + 3 * PSE_FFT_TZ * fft_lsz<R>());
+}
+template <int R> static size_t fft_smem_z() {
+    constexpr int M = R * R;  // raw (3 TY rows of M/2 float2) is reused for the 3 TY rows of M real outputs
+    return sizeof(float2) * (M / 2 + 3 * PSE_FFT_TY * (M / 2) + 3 * PSE_FFT_TY / 2 * fft_lsz<R>());
+}
+
+template <int R> static void fused_fft_launch(const WaveGeom<float> &w, const SampleArgs<float> *args, int system,
+                                              const Dev<float> &d, int parts, cudaStream_t s) {
+    constexpr int M = R * R;
+    const float2 *tw = reinterpret_cast<const float2 *>(w.fft_tw);
+    float2 *spec = reinterpret_cast<float2 *>(d.spec);
+    const dim3 gxy(M / 2 / PSE_FFT_TZ, M), gz(M / PSE_FFT_TY, M);
+    if (parts & 1) k_fftx_noise<R><<<gxy, 3 * PSE_FFT_TZ * R, fft_smem_xy<R>(), s>>>(w, args, system, tw, spec);
+    if (parts & 2) k_ffty<R><<<gxy, 3 * PSE_FFT_TZ * R, fft_smem_xy<R>(), s>>>(tw, spec);
+    if (parts & 4) k_fftz_c2r<R><<<gz, 3 * PSE_FFT_TY / 2 * R, fft_smem_z<R>(), s>>>(tw, spec, d.grid4);
+}
+
+bool fused_fft_supported(int M) { return M == 64 || M == 256; }
+
+template <int R> static cudaError_t fused_fft_attrs() {
+    cudaError_t e = cudaFuncSetAttribute(k_fftx_noise<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)fft_smem_xy<R>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ffty<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem_xy<R>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fftz_c2r<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem_z<R>());
+    return e;
+}
+
+cudaError_t fused_fft_prepare(int M) {
+    if (M == 64) return fused_fft_attrs<8>();
+    if (M == 256) return fused_fft_attrs<16>();
+    return cudaErrorInvalidValue;
+}
+
+void launch_fused_fft(const WaveGeom<float> &w, const SampleArgs<float> *args, int system, const Dev<float> &d,
+                      int parts, cudaStream_t s) {
+    if (w.M == 64) fused_fft_launch<8>(w, args, system, d, parts, s);
+    else fused_fft_launch<16>(w, args, system, d, parts, s);
+}
+
 #define PSE_INST(T)                                                                                      \
     template void launch_wave_noise<T>(WaveGeom<T>, const SampleArgs<T> *, int, void *, cudaStream_t); \
     template void launch_interp<T>(int64_t, WaveGeom<T>, Geom<T>, const Dev<T> &, cudaStream_t);       \

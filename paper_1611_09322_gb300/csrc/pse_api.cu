@@ -46,6 +46,7 @@ struct pse_ctx {
     cudaGraphConditionalHandle cond[5] = {};
     cufftHandle fft_r2c = 0;                            // forward FFT (spreading / grid noise)
     bool r2c_made = false;
+    bool fused_fft = false;                             // sample path: our noise + C2R kernels (FP32, M = 2^k)
     SpreadTile spread{};                                // spreading tile shape
     bool spread_ready = false, spread_tuned = false;
     size_t spread_smem_max = 0;                         // dynamic shared memory the spreading may use
@@ -251,6 +252,24 @@ template <typename T> pse_status init_ctx(pse_ctx *c) {
     const size_t csize = sizeof(T) * 2;
     if ((st = alloc(c->per_ctx, &d.spec, csize * 3 * plane)) != PSE_OK) return st;
     if ((st = alloc(c->per_ctx, (void **)&d.grid, sizeof(T) * 3 * M * M * M)) != PSE_OK) return st;
+    if constexpr (sizeof(T) == 4) {
+        // power-of-two grids: the sample path's own inverse FFT (needs the
+        // node-major grid of the interpolation)
+        if (c->params.wave_fft == 1 && c->params.wave_noise == 0 && wgeom<T>(c).interp_lanes == 0 &&
+            fused_fft_supported((int)M) && fused_fft_prepare((int)M) == cudaSuccess) {
+            std::vector<float> tw(M);
+            for (int64_t k = 0; k < M / 2; ++k) {
+                tw[2 * k] = (float)cos(2 * M_PI * k / M);
+                tw[2 * k + 1] = (float)sin(2 * M_PI * k / M);
+            }
+            float *d_tw = nullptr;
+            if ((st = alloc(c->per_ctx, (void **)&d_tw, sizeof(float) * tw.size())) != PSE_OK) return st;
+            CK(cudaMemcpy(d_tw, tw.data(), sizeof(float) * tw.size(), cudaMemcpyHostToDevice));
+            wgeom<T>(c).fft_tw = d_tw;
+            c->fused_fft = true;
+        }
+        cudaGetLastError();
+    }
     {
         std::vector<T> sct;
         build_scale_table<T>(p, sct);
@@ -470,6 +489,13 @@ template <typename T> void interp(pse_ctx *c, int64_t N, cudaStream_t s) {
 template <typename T> pse_status wave_branch(pse_ctx *c, int64_t N, cudaStream_t s, int mode) {
     Dev<T> &d = dev<T>(c);
     const WaveGeom<T> &w = wgeom<T>(c);
+    if constexpr (sizeof(T) == 4) {
+        if (mode == GM_SAMPLE && c->fused_fft) {
+            launch_fused_fft(w, d.args, c->params.system, d, 7, s);
+            launch_interp<T>(N, w, geom<T>(c), d, s);
+            return PSE_OK;
+        }
+    }
     if (mode == GM_SAMPLE && c->params.wave_noise == 0) {
         launch_wave_noise<T>(w, d.args, c->params.system, d.spec, s);
     } else {
@@ -984,7 +1010,8 @@ pse_status create_impl(pse_ctx **out, double L, double a, const pse_params *p) {
     if (cudaGetDevice(&c->device) != cudaSuccess) { cudaGetLastError(); delete c; return PSE_ECUDA; }
     if (p->wave_noise < 0 || p->wave_noise > 1 ||
         !(p->spread_tile == 0 || p->spread_tile == 1 || p->spread_tile == 2 || p->spread_tile == 4) ||
-        p->matvec_shape < 0 || p->matvec_shape > PSE_MV_VARIANTS || p->interp_form < 0 || p->interp_form > 1) {
+        p->matvec_shape < 0 || p->matvec_shape > PSE_MV_VARIANTS || p->interp_form < 0 || p->interp_form > 1 ||
+        p->wave_fft < 0 || p->wave_fft > 1) {
         delete c;
         return PSE_EINVAL;
     }
@@ -1166,7 +1193,12 @@ pse_status pse_profile_stages(pse_ctx *c, int64_t N, const float *d_pos, uint64_
         cudaMemsetAsync(&d.lz->overflow, 0, sizeof(int), s);
         cudaMemsetAsync(&d.lz->n_pairs, 0, sizeof(unsigned long long), s);
         return PSE_OK; });
+    const bool fused = c->fused_fft;
     if (r == PSE_OK) r = timed(PSE_STAGE_WAVE_NOISE, c->params.wave_noise ? 2 : 1, [&] {
+        if (fused) {  // noise generated inside the first FFT pass (x)
+            launch_fused_fft(c->wf, d.args, c->params.system, d, 1, s);
+            return PSE_OK;
+        }
         if (c->params.wave_noise == 0) {
             launch_wave_noise<float>(c->wf, d.args, c->params.system, d.spec, s);
             return PSE_OK;
@@ -1176,13 +1208,17 @@ pse_status pse_profile_stages(pse_ctx *c, int64_t N, const float *d_pos, uint64_
         CKF(cufftExecR2C(c->fft_r2c, (cufftReal *)d.grid, (cufftComplex *)d.spec));
         launch_wave_apply<float>(c->wf, d.args, c->params.system, d.spec, WAVE_MODE_GRIDNOISE, 0, s);
         return PSE_OK; });
-    if (r == PSE_OK) r = timed(PSE_STAGE_FFT, 0, [&] {
+    if (r == PSE_OK) r = timed(PSE_STAGE_FFT, fused ? 2 : 0, [&] {
+        if (fused) {  // y and z passes, the last one writing the node-major grid
+            launch_fused_fft(c->wf, d.args, c->params.system, d, 6, s);
+            return PSE_OK;
+        }
         CKF(cufftSetStream(c->fft, s));
         CKF(cufftExecC2R(c->fft, (cufftComplex *)d.spec, (cufftReal *)d.grid));
         return PSE_OK; });
     if (r == PSE_OK)
-        r = timed(PSE_STAGE_GRID_COPY, c->wf.interp_lanes == 0 ? 1 : 0, [&] {
-            launch_grid_copy<float>(c->wf, c->df, s);
+        r = timed(PSE_STAGE_GRID_COPY, (c->wf.interp_lanes == 0 && !fused) ? 1 : 0, [&] {
+            if (!fused) launch_grid_copy<float>(c->wf, c->df, s);
             return PSE_OK; });
     if (r == PSE_OK)
         r = timed(PSE_STAGE_INTERP, 1, [&] { launch_interp<float>(N, c->wf, c->gf, c->df, s); return PSE_OK; });

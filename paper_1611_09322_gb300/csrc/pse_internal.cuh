@@ -87,6 +87,7 @@ template <typename T> struct WaveGeom {
     uint32_t dv_h1_m, dv_M_m;  // division of 32-bit mode ids by Mh1 and M: multipliers
     int dv_h1_l, dv_M_l;       // and shifts (Granlund-Montgomery, round-up form)
     int big;             // M^2 Mh1 >= 2^32: 64-bit mode ids
+    const void *fft_tw;  // M/2 float2 e^{2 pi i k / M} (power-of-two grids, fused FFT path)
     int interp_lanes;    // lanes per particle in the interpolation (8, 16, 32; 0 = pick)
 };
 
@@ -419,6 +420,13 @@ template <typename T> void launch_matvec_caller(int64_t N, const SampleArgs<T> *
 template <typename T> void launch_wave_noise(WaveGeom<T> w, const SampleArgs<T> *args, int system, void *spec,
                                              cudaStream_t s);
 template <typename T> void launch_interp(int64_t N, WaveGeom<T> w, Geom<T> g, const Dev<T> &d, cudaStream_t s);
+// fused k-space noise + three-pass C2R into the node-major grid (FP32,
+// power-of-two M in 16..512); prepare once per M outside any capture
+bool fused_fft_supported(int M);
+cudaError_t fused_fft_prepare(int M);
+// parts: bit 0 the noise + x pass, bit 1 the y pass, bit 2 the z pass
+void launch_fused_fft(const WaveGeom<float> &w, const SampleArgs<float> *args, int system, const Dev<float> &d,
+                      int parts, cudaStream_t s);
 // node-major copy of the velocity grid for the FP32 interpolation (no-op otherwise)
 template <typename T> void launch_grid_copy(WaveGeom<T> w, const Dev<T> &d, cudaStream_t s);
 enum { WAVE_MODE_DET = 0, WAVE_MODE_GRIDNOISE = 1 };

@@ -316,3 +316,27 @@ def test_empty_inputs_are_rejected_and_leave_the_context_usable(torch):
     out = b.sample(torch.cat([d, d]), [0, 300, 600], SEED, 0)
     assert torch.isfinite(out).all()
     b.close()
+
+
+@pytest.mark.parametrize("M,N", [(64, 2000), (256, 2000), (32, 2000), (16, 250)])
+def test_fused_noise_fft_matches_cufft_and_oracle(torch, M, N):
+    """Grids M = 64 and 256: the sample path's own noise + three-pass C2R
+    (wave_fft = 1) gives the wave part of the oracle's gridded sample and of
+    the cuFFT path (wave_fft = 0) to float rounding; the real part is the
+    same bit for bit (same kernels).  Other grids keep cuFFT either way."""
+    from oracle import ewald, pse
+    pos, L, _ = _hs(N, 0.1, 33)
+    assert ewald.plan(L, 1.0, 0.5, 1e-3).M <= M
+    plan = ewald.plan(L, 1.0, 0.5, 1e-3, M=M)
+    outs = []
+    for f in (1, 0):
+        s = _sampler(L, xi=0.5, tol=1e-3, grid_M=M, fixed_iter=3, wave_fft=f)
+        _, r, w = s.sample(torch.from_numpy(pos).cuda(), SEED, 11, parts=True)
+        outs.append((r.cpu().numpy(), w.cpu().numpy()))
+        # the fused path launches our y and z passes, the cuFFT path none
+        fused = f == 1 and M in (64, 256)
+        assert s.profile_stages(torch.from_numpy(pos).cuda(), SEED, 11)["fft"][1] == (2 if fused else 0)
+        s.close()
+    ref = pse.wave_sample_grid(pos.astype(np.float64), plan, SEED, 11)
+    assert _maxrel(outs[0][1], ref) < 1e-4 and _maxrel(outs[0][1], outs[1][1]) < 1e-5
+    assert np.array_equal(outs[0][0], outs[1][0])
