@@ -206,13 +206,6 @@ def timed_steps(run, steps, flush, stream):
     return [a.elapsed_time(b) for a, b in evs]
 
 
-def launches_per_sample(J, learned=False):
-    # bin + 3 scan + scatter + cell sort, noise + node-major grid copy +
-    # interpolation, neighbour list, (network), q_1, 3 kernels per loop body
-    # (J bodies), final; cuFFT's own kernels are not counted
-    return 12 + (1 if learned else 0) + 3 * J
-
-
 def kernel_roofline(stages, N, M, n_pairs, peak, interp_kernel="k_interp4"):
     """Per-kernel achieved GB/s (algorithmic bytes per launch / live per-launch
     time from pse_profile_stages) and its fraction of the measured peak."""
@@ -545,12 +538,12 @@ def main():
                 "config": workload_config(plan, tuning), "lanczos_iters": J, "n_pairs": n_pairs,
                 "variant": "plain PSE, one system, one CUDA graph per sample",
                 "roofline": roofline, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": launches_per_sample(J) * args.steps,
+                "gpu_launches": sum(n for _, n in stages.values()) * args.steps,
                 "parallelism": "replicas" if ws > 1 else "single GPU"}
-        if not args.no_variants:
+        if not args.no_variants and ws == 1:
             line["variants"] = variants_learned_batched(dev, flush, stream, max(20, args.steps // 4), xi, M_grid)
             line["variants"].update(variants_configs(dev, flush, stream, 10, peak))
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(xi)
         print(json.dumps(line), flush=True)
     if ws > 1:
