@@ -55,6 +55,34 @@ def workload_config(plan=None, tuning=None, xi=XI_TUNED):
     return cfg
 
 
+def replica_plan(xi, M, dev):
+    """Every replica samples rank 0's splitting and grid (one broadcast)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([xi, float(M)], dtype=torch.float64, device=dev)
+    dist.broadcast(t, 0)
+    return float(t[0]), int(t[1])
+
+
+def replica_time(total_ms, dev):
+    """The slowest replica's timed region (max over ranks), in ms."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(ws, n_part, steps, total_ms):
+    """Whole-job particle-samples/s: every replica's samples over the slowest time."""
+    return ws * n_part * steps / (total_ms / 1e3)
+
+
+def replica_seed(rank):
+    """Independent noise per replica."""
+    return 1000 + rank
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -457,14 +485,12 @@ def main():
         tuning = pse_tune_xi(L, d_pos, xi=XI, tol=TOL, reps=10, autotune=1)
         xi, M_grid = tuning["xi_best"], tuning["M_best"]
     if ws > 1:
-        t = torch.tensor([xi, float(M_grid)], dtype=torch.float64, device=dev)
-        dist.broadcast(t, 0)
-        xi, M_grid = float(t[0]), int(t[1])
+        xi, M_grid = replica_plan(xi, M_grid, dev)
     s = Sampler(L, 1.0, xi=xi, tol=TOL, grid_M=M_grid, interp_form=args.interp_form)
     out = torch.empty_like(d_pos)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    seed = 1000 + rank
+    seed = replica_seed(rank)
 
     clk, clkf = clocks_start()
     for i in range(args.warmup):
@@ -481,10 +507,8 @@ def main():
     st = s.stats()
     J = st["lanczos_iters"]
     if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * N_PART * args.steps / (total_ms / 1e3)
+        total_ms = replica_time(total_ms, dev)
+    value = replica_value(ws, N_PART, args.steps, total_ms)
 
     # live per-stage timing (CUDA events on the launching stream) for the roofline
     stages = None
