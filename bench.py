@@ -540,15 +540,20 @@ def main():
                 "stages_ms": {k: round(v[0], 4) for k, v in stages.items()},
                 "stages_launches": {k: v[1] for k, v in stages.items()}}
 
-    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    # the timed region: every step copies its positions in and its result
+    # out (pse_sample_host_async: the copies of one step overlap the
+    # sampling of its neighbours), all results on the host at the end
     hp = torch.from_numpy(pos).pin_memory()
-    ho = torch.empty_like(hp).pin_memory()
+    ho = [torch.empty_like(hp).pin_memory() for _ in range(2)]
     for i in range(2):
-        s.sample_host_ptr(N_PART, hp.data_ptr(), ho.data_ptr(), seed, 50_000 + i)
-    K2 = max(3, min(args.steps, 20))
+        s.sample_host_async_ptr(N_PART, hp.data_ptr(), ho[i % 2].data_ptr(), seed, 50_000 + i)
+    s.host_sync()
+    K2 = max(3, min(args.steps, 50))
     t0 = time.perf_counter()
     for i in range(K2):
-        s.sample_host_ptr(N_PART, hp.data_ptr(), ho.data_ptr(), seed, 60_000 + i)
+        s.sample_host_async_ptr(N_PART, hp.data_ptr(), ho[i % 2].data_ptr(), seed, 60_000 + i)
+    s.host_sync()
     e2e_s = (time.perf_counter() - t0) / K2
     e2e = {"value": ws * N_PART / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 12 * N_PART,
            "d2h_bytes_per_step": 12 * N_PART}

@@ -261,6 +261,21 @@ pse_status pse_sample_parts(pse_ctx *ctx, int64_t N, const float *d_pos, uint64_
 pse_status pse_sample_host(pse_ctx *ctx, int64_t N, const float *h_pos, uint64_t seed,
                            uint64_t sample_index, float *h_out, void *stream);
 
+/* Pipelined form of pse_sample_host: returns without waiting.  The input
+ * copy runs on a copy stream of the context and `stream` waits for it; the
+ * result is copied back on a second copy stream once the sample on `stream`
+ * is done.  Two staging buffer pairs alternate, so the copies of one call
+ * overlap the sampling of its neighbours.  h_pos and h_out must stay valid
+ * and untouched until pse_host_sync returns; h_out then holds the result.
+ * Host memory should be pinned (pageable memory makes the copies
+ * synchronous). */
+pse_status pse_sample_host_async(pse_ctx *ctx, int64_t N, const float *h_pos, uint64_t seed,
+                                 uint64_t sample_index, float *h_out, void *stream);
+
+/* Waits for every copy issued by pse_sample_host_async (and so for their
+ * samples). */
+pse_status pse_host_sync(pse_ctx *ctx);
+
 /* FP64 context (params.precision = PSE_FP64): positions, outputs and all
  * arithmetic in float64.  Same semantics as pse_sample_parts. */
 pse_status pse_sample_f64(pse_ctx *ctx, int64_t N, const double *d_pos, uint64_t seed,

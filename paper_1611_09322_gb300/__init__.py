@@ -190,6 +190,14 @@ class Sampler:
         _lib.check(self.lib.pse_sample_host(self.ctx, N, ctypes.c_void_p(h_pos_ptr), seed, sample_index,
                                             ctypes.c_void_p(h_out_ptr), _stream()), "pse_sample_host")
 
+    def sample_host_async_ptr(self, N, h_pos_ptr, h_out_ptr, seed, sample_index=0):
+        """Pipelined host-buffer sample (pse_sample_host_async); the result is in h_out after host_sync()."""
+        _lib.check(self.lib.pse_sample_host_async(self.ctx, N, ctypes.c_void_p(h_pos_ptr), seed, sample_index,
+                                                  ctypes.c_void_p(h_out_ptr), _stream()), "pse_sample_host_async")
+
+    def host_sync(self):
+        _lib.check(self.lib.pse_host_sync(self.ctx), "pse_host_sync")
+
     def real_matvec(self, pos, v, out=None):
         """M_r v (near-field product, eq. Mreal) for (N, 3) CUDA float32 tensors."""
         import torch

@@ -90,6 +90,8 @@ SIGNATURES = {
     "pse_sample": (_ST, [_VP, _I64, _VP, _U64, _U64, _VP, _VP]),
     "pse_sample_parts": (_ST, [_VP, _I64, _VP, _U64, _U64, _VP, _VP, _VP, _VP]),
     "pse_sample_host": (_ST, [_VP, _I64, _VP, _U64, _U64, _VP, _VP]),
+    "pse_sample_host_async": (_ST, [_VP, _I64, _VP, _U64, _U64, _VP, _VP]),
+    "pse_host_sync": (_ST, [_VP]),
     "pse_sample_f64": (_ST, [_VP, _I64, _VP, _U64, _U64, _VP, _VP, _VP, _VP]),
     "pse_real_matvec": (_ST, [_VP, _I64, _VP, _VP, _VP, _VP]),
     "pse_sample_with_forces": (_ST, [_VP, _I64, _VP, _VP, _U64, _U64, ctypes.c_double, ctypes.c_double, _VP, _VP]),

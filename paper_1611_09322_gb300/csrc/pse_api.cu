@@ -59,6 +59,20 @@ struct pse_ctx {
     bool mv_tuned = false;                              // matvec launch shape timed
     cudaStream_t last_stream = nullptr;
     void *stage_pos = nullptr, *stage_out = nullptr;  // device staging for the host-buffer call
+    // pipelined host-buffer calls: two staging pairs, a copy stream, and per
+    // pair the event of its input copy and of its sample
+    void *stage_pos2 = nullptr, *stage_out2 = nullptr;
+    cudaStream_t s_copy = nullptr, s_back = nullptr;  // input copies; result copies
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr}, ev_back[2] = {nullptr, nullptr};
+    bool host_used[2] = {false, false};
+    int host_flip = 0;
+    // per-call arguments go to the device from a ring of pinned host slots:
+    // a copy from pageable memory would wait for the stream, so a call would
+    // block until the previous sample is done
+    unsigned char *args_ring = nullptr;
+    cudaEvent_t ev_args[8] = {};
+    bool args_used[8] = {};
+    int args_slot = 0;
     std::vector<void *> per_n;                          // buffers freed when N changes
     std::vector<void *> per_ctx;                        // buffers freed at destroy
     bool pc_enabled = false;                            // learned preconditioner installed
@@ -89,6 +103,14 @@ struct DeviceGuard {
     }
 };
 
+constexpr int PSE_ARGS_SLOTS = 8, PSE_ARGS_SLOT_BYTES = 256;
+static_assert(sizeof(SampleArgs<double>) <= PSE_ARGS_SLOT_BYTES, "argument slot too small");
+static_assert(PSE_ARGS_SLOTS == sizeof(pse_ctx::ev_args) / sizeof(cudaEvent_t), "argument ring size");
+
+// Copy n bytes of per-call arguments to dst on s through the next pinned slot
+// (waiting, on the host, only for that slot's copy of 8 calls ago).
+cudaError_t push_args(pse_ctx *c, void *dst, const void *src, size_t n, cudaStream_t s);
+
 template <typename T> Dev<T> &dev(pse_ctx *c);
 template <> Dev<float> &dev<float>(pse_ctx *c) { return c->df; }
 template <> Dev<double> &dev<double>(pse_ctx *c) { return c->dd; }
@@ -109,6 +131,21 @@ pse_status alloc(std::vector<void *> &list, void **p, size_t bytes) {
     }
     list.push_back(*p);
     return PSE_OK;
+}
+
+cudaError_t push_args(pse_ctx *c, void *dst, const void *src, size_t n, cudaStream_t s) {
+    const int k = c->args_slot;
+    c->args_slot = (k + 1) % PSE_ARGS_SLOTS;
+    if (c->args_used[k]) {
+        const cudaError_t e = cudaEventSynchronize(c->ev_args[k]);
+        if (e != cudaSuccess) return e;
+    }
+    unsigned char *slot = c->args_ring + (size_t)k * PSE_ARGS_SLOT_BYTES;
+    memcpy(slot, src, n);
+    cudaError_t e = cudaMemcpyAsync(dst, slot, n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_args[k], s);
+    c->args_used[k] = e == cudaSuccess;
+    return e;
 }
 
 void free_list(std::vector<void *> &list) {
@@ -293,6 +330,15 @@ template <typename T> pse_status init_ctx(pse_ctx *c) {
                       sizeof(T) == 4 ? CUFFT_C2R : CUFFT_Z2D, 3));
     c->fft_made = true;
     CK(cudaStreamCreateWithFlags(&c->s_main, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&c->s_copy, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&c->s_back, cudaStreamNonBlocking));
+    CK(cudaMallocHost((void **)&c->args_ring, (size_t)PSE_ARGS_SLOTS * PSE_ARGS_SLOT_BYTES));
+    for (int k = 0; k < PSE_ARGS_SLOTS; ++k) CK(cudaEventCreateWithFlags(&c->ev_args[k], cudaEventDisableTiming));
+    for (int b = 0; b < 2; ++b) {
+        CK(cudaEventCreateWithFlags(&c->ev_in[b], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->ev_done[b], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->ev_back[b], cudaEventDisableTiming));
+    }
     CK(cudaStreamCreateWithFlags(&c->s_wave, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&c->s_body, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&c->s_body2, cudaStreamNonBlocking));
@@ -457,6 +503,9 @@ template <typename T> pse_status ensure(pse_ctx *c, int64_t N) {
     A(d.partials, sizeof(double) * (2 * num_sms() * 16 + 64));
     A(c->stage_pos, sizeof(T) * 3 * N);
     A(c->stage_out, sizeof(T) * 3 * N);
+    A(c->stage_pos2, sizeof(T) * 3 * N);
+    A(c->stage_out2, sizeof(T) * 3 * N);
+    c->host_used[0] = c->host_used[1] = false;
 #undef A
     c->N = N;
     return PSE_OK;
@@ -738,7 +787,7 @@ pse_status sample_impl(pse_ctx *c, int64_t N, const T *pos, uint64_t seed, uint6
     a.sample = sample;
     a.c_det = 0.0;
     a.c_noise = 1.0;
-    CK(cudaMemcpyAsync(dev<T>(c).args, &a, sizeof(a), cudaMemcpyHostToDevice, s));
+    CK(push_args(c, dev<T>(c).args, &a, sizeof(a), s));
     if ((c->params.autotune & 4) && c->params.matvec_shape == 0 && !c->mv_tuned) {
         if ((st = tune_matvec<T>(c, s)) != PSE_OK) return st;
         if (use_graph && (st = build_graph<T>(c, GM_SAMPLE)) != PSE_OK) return st;
@@ -817,7 +866,7 @@ pse_status bd_impl(pse_ctx *c, int64_t N, T *pos, const T *fext, double dt, doub
     a.sample = step;
     a.c_det = dt;
     a.c_noise = sqrt(2.0 * kT * dt);
-    CK(cudaMemcpyAsync(d.args, &a, sizeof(a), cudaMemcpyHostToDevice, s));
+    CK(push_args(c, d.args, &a, sizeof(a), s));
     const bool use_graph = c->params.use_graph >= 0;
     if (use_graph && !c->exec[mode]) {
         st = build_graph<T>(c, mode);
@@ -854,7 +903,7 @@ pse_status forces_impl(pse_ctx *c, int64_t N, const T *pos, const T *force, uint
     a.sample = sample;
     a.c_det = c_det;
     a.c_noise = c_noise;
-    CK(cudaMemcpyAsync(dev<T>(c).args, &a, sizeof(a), cudaMemcpyHostToDevice, s));
+    CK(push_args(c, dev<T>(c).args, &a, sizeof(a), s));
     if ((c->params.autotune & 2) && c->params.spread_tile == 0 && !c->spread_tuned) {
         pre<T>(c, N, s);
         if ((st = tune_spread<T>(c, s)) != PSE_OK) return st;
@@ -1048,8 +1097,16 @@ void pse_destroy(pse_ctx *c) {
     if (c->sp_scratch) cudaFree(c->sp_scratch);
     free_list(c->per_n);
     free_list(c->per_ctx);
-    cudaStream_t ss[4] = {c->s_main, c->s_wave, c->s_body, c->s_body2};
+    cudaStream_t ss[6] = {c->s_main, c->s_wave, c->s_body, c->s_body2, c->s_copy, c->s_back};
     for (cudaStream_t s : ss) if (s) cudaStreamDestroy(s);
+    for (int b = 0; b < 2; ++b) {
+        if (c->ev_in[b]) cudaEventDestroy(c->ev_in[b]);
+        if (c->ev_done[b]) cudaEventDestroy(c->ev_done[b]);
+        if (c->ev_back[b]) cudaEventDestroy(c->ev_back[b]);
+    }
+    for (int k = 0; k < PSE_ARGS_SLOTS; ++k)
+        if (c->ev_args[k]) cudaEventDestroy(c->ev_args[k]);
+    if (c->args_ring) cudaFreeHost(c->args_ring);
     for (cudaEvent_t e : c->ev) if (e) cudaEventDestroy(e);
     delete c;
 }
@@ -1140,7 +1197,7 @@ pse_status pse_real_matvec(pse_ctx *c, int64_t N, const float *d_pos, const floa
     a.pos = d_pos;
     a.out = d_out;
     a.vin = d_v;
-    CK(cudaMemcpyAsync(c->df.args, &a, sizeof(a), cudaMemcpyHostToDevice, s));
+    CK(push_args(c, c->df.args, &a, sizeof(a), s));
     pre<float>(c, N, s);
     launch_nbr<float>(N, c->gf, c->df, s);
     launch_matvec_caller<float>(N, c->df.args, c->gf, c->df, s);
@@ -1165,7 +1222,7 @@ pse_status pse_profile_stages(pse_ctx *c, int64_t N, const float *d_pos, uint64_
     a.seed = seed;
     a.sample = sample_index;
     a.c_noise = 1.0;
-    CK(cudaMemcpyAsync(d.args, &a, sizeof(a), cudaMemcpyHostToDevice, s));
+    CK(push_args(c, d.args, &a, sizeof(a), s));
     if (c->params.wave_noise == 1 && (st = ensure_r2c<float>(c)) != PSE_OK) return st;
     const double ltol = c->params.lanczos_tol > 0 ? c->params.lanczos_tol : c->plan.tol;
     cudaEvent_t e0, e1;
@@ -1405,7 +1462,7 @@ static pse_status pc_prepare(pse_ctx *c, int64_t N, const float *d_pos, cudaStre
     if (st != PSE_OK) return st;
     SampleArgs<float> a{};
     a.pos = d_pos;
-    CK(cudaMemcpyAsync(c->df.args, &a, sizeof(a), cudaMemcpyHostToDevice, s));
+    CK(push_args(c, c->df.args, &a, sizeof(a), s));
     pre<float>(c, N, s);
     launch_nbr<float>(N, c->gf, c->df, s);
     return PSE_OK;
@@ -1463,6 +1520,48 @@ pse_status pse_precond_blocks(pse_ctx *c, int64_t N, const float *d_pos, float *
     return PSE_OK;
 }
 
+pse_status pse_sample_host_async(pse_ctx *c, int64_t N, const float *h_pos, uint64_t seed, uint64_t sample_index,
+                                 float *h_out, void *stream) {
+    if (!c || c->plan.precision != PSE_FP32) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
+    if (!h_pos || !h_out || N < 1) return PSE_EINVAL;
+    DeviceGuard guard(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (N != c->N) CK(cudaDeviceSynchronize());  // staging buffers are re-allocated for a new N
+    pse_status st = ensure<float>(c, N);
+    if (st != PSE_OK) return st;
+    const int b = c->host_flip;
+    c->host_flip ^= 1;
+    float *dp = (float *)(b ? c->stage_pos2 : c->stage_pos), *dout = (float *)(b ? c->stage_out2 : c->stage_out);
+    const size_t bytes = sizeof(float) * 3 * N;
+    // pair b was last used two calls ago: its sample must be done before its
+    // input is overwritten, and its result copied out before its output is
+    // (the result copies run on their own stream, in call order, so an input
+    // copy never queues behind the result copy of the sample still running)
+    if (c->host_used[b]) {
+        CK(cudaStreamWaitEvent(c->s_copy, c->ev_done[b], 0));
+        CK(cudaStreamWaitEvent(s, c->ev_back[b], 0));
+    }
+    CK(cudaMemcpyAsync(dp, h_pos, bytes, cudaMemcpyHostToDevice, c->s_copy));
+    CK(cudaEventRecord(c->ev_in[b], c->s_copy));
+    CK(cudaStreamWaitEvent(s, c->ev_in[b], 0));
+    st = sample_impl<float>(c, N, dp, seed, sample_index, dout, nullptr, nullptr, s);
+    if (st != PSE_OK) return st;
+    CK(cudaEventRecord(c->ev_done[b], s));
+    c->host_used[b] = true;
+    CK(cudaStreamWaitEvent(c->s_back, c->ev_done[b], 0));
+    CK(cudaMemcpyAsync(h_out, dout, bytes, cudaMemcpyDeviceToHost, c->s_back));
+    CK(cudaEventRecord(c->ev_back[b], c->s_back));
+    return PSE_OK;
+}
+
+pse_status pse_host_sync(pse_ctx *c) {
+    if (!c) return PSE_EINVAL;
+    DeviceGuard guard(c->device);
+    CK(cudaStreamSynchronize(c->s_copy));
+    CK(cudaStreamSynchronize(c->s_back));
+    return PSE_OK;
+}
+
 pse_status pse_get_stats(pse_ctx *c, pse_stats *out) {
     if (!c || !out) return PSE_EINVAL;
     memset(out, 0, sizeof(*out));
@@ -1499,6 +1598,12 @@ struct pse_batch {
     std::vector<int64_t> built_N;
     SampleArgs<float> *d_args = nullptr;  // one per system, read by that system's kernels
     std::vector<SampleArgs<float>> h_args;
+    // pinned ring of argument tables (nsys entries per slot): the per-call
+    // copy then does not wait for the previous batched sample
+    SampleArgs<float> *args_ring = nullptr;
+    cudaEvent_t ev_args[PSE_ARGS_SLOTS] = {};
+    bool args_used[PSE_ARGS_SLOTS] = {};
+    int args_slot = 0;
     LzState **d_lzs = nullptr;            // each system's Lanczos state, for the loop condition
     cudaStream_t body = nullptr;          // captures the shared loop body
     cudaStream_t body2 = nullptr;         // the eigen-solves, beside the matvec and update
@@ -1542,6 +1647,9 @@ extern "C" void pse_batch_destroy(pse_batch *b) {
     batch_drop_graph(b);
     for (pse_ctx *c : b->sys) pse_destroy(c);
     if (b->d_args) cudaFree(b->d_args);
+    for (int k = 0; k < PSE_ARGS_SLOTS; ++k)
+        if (b->ev_args[k]) cudaEventDestroy(b->ev_args[k]);
+    if (b->args_ring) cudaFreeHost(b->args_ring);
     if (b->d_lzs) cudaFree(b->d_lzs);
     if (b->root) cudaStreamDestroy(b->root);
     if (b->body) cudaStreamDestroy(b->body);
@@ -1935,7 +2043,20 @@ extern "C" pse_status pse_batch_sample(pse_batch *b, const int64_t *offsets, con
         a.c_det = 0.0;
         a.c_noise = 1.0;
     }
-    CK(cudaMemcpyAsync(b->d_args, b->h_args.data(), sizeof(SampleArgs<float>) * S, cudaMemcpyHostToDevice, s));
+    {
+        if (!b->args_ring) {
+            CK(cudaMallocHost((void **)&b->args_ring, sizeof(SampleArgs<float>) * S * PSE_ARGS_SLOTS));
+            for (int k = 0; k < PSE_ARGS_SLOTS; ++k) CK(cudaEventCreateWithFlags(&b->ev_args[k], cudaEventDisableTiming));
+        }
+        const int k = b->args_slot;
+        b->args_slot = (k + 1) % PSE_ARGS_SLOTS;
+        if (b->args_used[k]) CK(cudaEventSynchronize(b->ev_args[k]));
+        SampleArgs<float> *slot = b->args_ring + (size_t)k * S;
+        memcpy(slot, b->h_args.data(), sizeof(SampleArgs<float>) * S);
+        CK(cudaMemcpyAsync(b->d_args, slot, sizeof(SampleArgs<float>) * S, cudaMemcpyHostToDevice, s));
+        CK(cudaEventRecord(b->ev_args[k], s));
+        b->args_used[k] = true;
+    }
     if (plain) {  // the same kernels without a graph, host-side loop (one sync per step)
         if (!b->d_any && cudaMalloc((void **)&b->d_any, sizeof(int)) != cudaSuccess) {
             cudaGetLastError();

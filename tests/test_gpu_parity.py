@@ -340,3 +340,26 @@ def test_fused_noise_fft_matches_cufft_and_oracle(torch, M, N):
     ref = pse.wave_sample_grid(pos.astype(np.float64), plan, SEED, 11)
     assert _maxrel(outs[0][1], ref) < 1e-4 and _maxrel(outs[0][1], outs[1][1]) < 1e-5
     assert np.array_equal(outs[0][0], outs[1][0])
+
+
+def test_pipelined_host_buffers(torch):
+    """pse_sample_host_async: consecutive calls with pinned host buffers (two
+    staging pairs alternating, copies on the context's copy stream) give, after
+    pse_host_sync, exactly the samples of the device-buffer call; a change of
+    N in between re-allocates safely."""
+    pos, L, _ = _hs(3000, 0.1, 34)
+    s = _sampler(L, xi=0.5, tol=1e-3)
+    hp = torch.from_numpy(pos).pin_memory()
+    outs = [torch.empty_like(hp).pin_memory() for _ in range(5)]
+    for i, o in enumerate(outs):
+        s.sample_host_async_ptr(3000, hp.data_ptr(), o.data_ptr(), SEED, 40 + i)
+    s.host_sync()
+    d = torch.from_numpy(pos).cuda()
+    for i, o in enumerate(outs):
+        assert torch.equal(o, s.sample(d, SEED, 40 + i).cpu())
+    small = torch.from_numpy(pos[:1000].copy()).pin_memory()
+    o2 = torch.empty_like(small).pin_memory()
+    s.sample_host_async_ptr(1000, small.data_ptr(), o2.data_ptr(), SEED, 3)
+    s.host_sync()
+    assert torch.equal(o2, s.sample(torch.from_numpy(pos[:1000].copy()).cuda(), SEED, 3).cpu())
+    s.close()
