@@ -211,7 +211,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(),
+            "config": dict(workload_config(), precision="fp64 throughout (the CPU oracle)", M=plan.M),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"each step: one FP64 oracle PSE sample of N={CPU_SAMPLE_N} at phi={PHI} "
                                        f"(same density, tol and xi={XI_TUNED:.4f} as the N=1e6 workload; "
