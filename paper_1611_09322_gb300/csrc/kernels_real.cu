@@ -729,8 +729,32 @@ void launch_lz_init(int64_t N, const SampleArgs<T> *args, int system, const Dev<
 }
 // Matvec launch shapes (threads per particle, independent gathers per thread),
 // selected by Geom::mv; the sampler may time them all and keep the fastest.
+// Persistent grid: one wave of resident blocks (at most 16 per SM), so that
+// no second, partly filled wave of equal-work blocks trails the first.
+template <typename T, int TPP, int ILP> int mv_blocks_per_sm() {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lz_matvec<T, TPP, ILP>, 128, 0) != cudaSuccess ||
+            nb < 1) {
+            cudaGetLastError();
+            nb = 16;
+        }
+        per_sm = nb < 16 ? nb : 16;
+    }
+    return per_sm;
+}
+int matvec_blocks_per_sm() { return mv_blocks_per_sm<float, 4, 4>(); }
+// occupancy of every matvec shape, queried once outside any stream capture
+void matvec_prepare() {
+    mv_blocks_per_sm<float, 4, 4>(); mv_blocks_per_sm<float, 8, 2>();
+    mv_blocks_per_sm<float, 16, 1>(); mv_blocks_per_sm<float, 4, 2>();
+    mv_blocks_per_sm<double, 4, 4>(); mv_blocks_per_sm<double, 8, 2>();
+    mv_blocks_per_sm<double, 16, 1>(); mv_blocks_per_sm<double, 4, 2>();
+}
+
 template <typename T, int TPP, int ILP> void mv_launch(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
-    k_lz_matvec<T, TPP, ILP><<<pgrid(N, 128 / TPP, 16), 128, 0, s>>>(
+    k_lz_matvec<T, TPP, ILP><<<pgrid(N, 128 / TPP, mv_blocks_per_sm<T, TPP, ILP>()), 128, 0, s>>>(
         N, nbr_k(N, d.nbr_cap), g, d.rec, d.nbr_count, d.nbr, d.table, d.table_c, d.u, d.partials, d.lz,
         sizeof(T) == 4 ? d.pc_on : nullptr, d.basis);
 }

@@ -243,6 +243,7 @@ template <typename T> void fill_geom(pse_ctx *c) {
 // Per-context buffers: table, spectrum, grid, FFT plan, streams, events.
 template <typename T> pse_status init_ctx(pse_ctx *c) {
     fill_geom<T>(c);
+    matvec_prepare();
 
     Dev<T> &d = dev<T>(c);
     const pse_plan_info &p = c->plan;
@@ -1814,7 +1815,7 @@ extern "C" pse_status pse_batch_create(pse_batch **out, int nsys, const double *
 // system's sample is bitwise that of a lone context.
 static pse_status batch_descriptors(pse_batch *b) {
     const int S = (int)b->sys.size();
-    const int64_t cap_mv = num_sms() * 16, cap_up = num_sms() * 8;
+    const int64_t cap_mv = (int64_t)num_sms() * matvec_blocks_per_sm(), cap_up = num_sms() * 8;
     std::vector<LzSys> hs(S);
     std::vector<int> blk_mv, blk_up;
     for (int k = 0; k < S; ++k) {

@@ -427,6 +427,9 @@ cudaError_t fused_fft_prepare(int M);
 // parts: bit 0 the noise + x pass, bit 1 the y pass, bit 2 the z pass
 void launch_fused_fft(const WaveGeom<float> &w, const SampleArgs<float> *args, int system, const Dev<float> &d,
                       int parts, cudaStream_t s);
+// resident blocks per SM of the FP32 4x4 matvec (its persistent grid is one wave of them)
+int matvec_blocks_per_sm();
+void matvec_prepare();
 // node-major copy of the velocity grid for the FP32 interpolation (no-op otherwise)
 template <typename T> void launch_grid_copy(WaveGeom<T> w, const Dev<T> &d, cudaStream_t s);
 enum { WAVE_MODE_DET = 0, WAVE_MODE_GRIDNOISE = 1 };
