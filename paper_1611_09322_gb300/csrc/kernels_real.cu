@@ -745,12 +745,27 @@ template <typename T, int TPP, int ILP> int mv_blocks_per_sm() {
     return per_sm;
 }
 int matvec_blocks_per_sm() { return mv_blocks_per_sm<float, 4, 4>(); }
+// the same for the Lanczos update (FP32 and FP64), at most 8 per SM
+template <typename T> int up_blocks_per_sm() {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lz_update<T>, 256, 0) != cudaSuccess || nb < 1) {
+            cudaGetLastError();
+            nb = 8;
+        }
+        per_sm = nb < 8 ? nb : 8;
+    }
+    return per_sm;
+}
+int update_blocks_per_sm() { return up_blocks_per_sm<float>(); }
 // occupancy of every matvec shape, queried once outside any stream capture
 void matvec_prepare() {
     mv_blocks_per_sm<float, 4, 4>(); mv_blocks_per_sm<float, 8, 2>();
     mv_blocks_per_sm<float, 16, 1>(); mv_blocks_per_sm<float, 4, 2>();
     mv_blocks_per_sm<double, 4, 4>(); mv_blocks_per_sm<double, 8, 2>();
     mv_blocks_per_sm<double, 16, 1>(); mv_blocks_per_sm<double, 4, 2>();
+    up_blocks_per_sm<float>(); up_blocks_per_sm<double>();
 }
 
 template <typename T, int TPP, int ILP> void mv_launch(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
@@ -767,7 +782,7 @@ template <typename T> void launch_lz_matvec(int64_t N, Geom<T> g, const Dev<T> &
     }
 }
 template <typename T> void launch_lz_update(int64_t N, int, const Dev<T> &d, cudaStream_t s) {
-    k_lz_update<T><<<pgrid(N, 256, 8), 256, 0, s>>>(N, d.basis, d.rec, d.u, d.partials + num_sms() * 16 + 32, d.lz,
+    k_lz_update<T><<<pgrid(N, 256, up_blocks_per_sm<T>()), 256, 0, s>>>(N, d.basis, d.rec, d.u, d.partials + num_sms() * 16 + 32, d.lz,
                                                     sizeof(T) == 4 ? d.pc_on : nullptr);
 }
 void launch_lz_eig(LzState *lz, int max_iter, int fixed_iter, double tol, cudaGraphConditionalHandle h,

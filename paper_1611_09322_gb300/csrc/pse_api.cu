@@ -1815,7 +1815,8 @@ extern "C" pse_status pse_batch_create(pse_batch **out, int nsys, const double *
 // system's sample is bitwise that of a lone context.
 static pse_status batch_descriptors(pse_batch *b) {
     const int S = (int)b->sys.size();
-    const int64_t cap_mv = (int64_t)num_sms() * matvec_blocks_per_sm(), cap_up = num_sms() * 8;
+    const int64_t cap_mv = (int64_t)num_sms() * matvec_blocks_per_sm(),
+                  cap_up = (int64_t)num_sms() * update_blocks_per_sm();
     std::vector<LzSys> hs(S);
     std::vector<int> blk_mv, blk_up;
     for (int k = 0; k < S; ++k) {

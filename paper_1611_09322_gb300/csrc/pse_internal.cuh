@@ -429,6 +429,7 @@ void launch_fused_fft(const WaveGeom<float> &w, const SampleArgs<float> *args, i
                       int parts, cudaStream_t s);
 // resident blocks per SM of the FP32 4x4 matvec (its persistent grid is one wave of them)
 int matvec_blocks_per_sm();
+int update_blocks_per_sm();
 void matvec_prepare();
 // node-major copy of the velocity grid for the FP32 interpolation (no-op otherwise)
 template <typename T> void launch_grid_copy(WaveGeom<T> w, const Dev<T> &d, cudaStream_t s);
