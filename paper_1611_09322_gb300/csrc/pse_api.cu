@@ -39,8 +39,8 @@ struct pse_ctx {
     int ncell3 = 0;
     cufftHandle fft = 0;
     bool fft_made = false;
-    cudaStream_t s_main = nullptr, s_wave = nullptr, s_body = nullptr, s_body2 = nullptr;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t s_main = nullptr, s_wave = nullptr, s_body = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};  // fork of the wave branch; its join
     cudaGraph_t graph[5] = {};            // per graph mode (GM_*)
     cudaGraphExec_t exec[5] = {};
     cudaGraphConditionalHandle cond[5] = {};
@@ -342,8 +342,7 @@ template <typename T> pse_status init_ctx(pse_ctx *c) {
     }
     CK(cudaStreamCreateWithFlags(&c->s_wave, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&c->s_body, cudaStreamNonBlocking));
-    CK(cudaStreamCreateWithFlags(&c->s_body2, cudaStreamNonBlocking));
-    for (int i = 0; i < 4; ++i) CK(cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming));
+    for (int i = 0; i < 2; ++i) CK(cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming));
     return PSE_OK;
 }
 
@@ -1098,7 +1097,7 @@ void pse_destroy(pse_ctx *c) {
     if (c->sp_scratch) cudaFree(c->sp_scratch);
     free_list(c->per_n);
     free_list(c->per_ctx);
-    cudaStream_t ss[6] = {c->s_main, c->s_wave, c->s_body, c->s_body2, c->s_copy, c->s_back};
+    cudaStream_t ss[5] = {c->s_main, c->s_wave, c->s_body, c->s_copy, c->s_back};
     for (cudaStream_t s : ss) if (s) cudaStreamDestroy(s);
     for (int b = 0; b < 2; ++b) {
         if (c->ev_in[b]) cudaEventDestroy(c->ev_in[b]);
@@ -1592,8 +1591,6 @@ struct pse_batch {
     std::vector<pse_ctx *> sys;
     int device = 0;
     cudaStream_t root = nullptr;
-    cudaEvent_t ev_fork = nullptr;
-    std::vector<cudaEvent_t> ev_join;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<int64_t> built_N;
@@ -1607,8 +1604,6 @@ struct pse_batch {
     int args_slot = 0;
     LzState **d_lzs = nullptr;            // each system's Lanczos state, for the loop condition
     cudaStream_t body = nullptr;          // captures the shared loop body
-    cudaStream_t body2 = nullptr;         // the eigen-solves, beside the matvec and update
-    cudaEvent_t ev_body = nullptr, ev_after = nullptr, ev_eig = nullptr;
     LzSys *d_sys = nullptr;               // per-system descriptors of the fused loop kernels
     int *d_blk_mv = nullptr, *d_blk_up = nullptr;  // block -> system of the fused matvec / update
     int nblk_mv = 0, nblk_up = 0;
@@ -1654,8 +1649,6 @@ extern "C" void pse_batch_destroy(pse_batch *b) {
     if (b->d_lzs) cudaFree(b->d_lzs);
     if (b->root) cudaStreamDestroy(b->root);
     if (b->body) cudaStreamDestroy(b->body);
-    if (b->body2) cudaStreamDestroy(b->body2);
-    if (b->ev_eig) cudaEventDestroy(b->ev_eig);
     if (b->d_sys) cudaFree(b->d_sys);
     if (b->d_blk_mv) cudaFree(b->d_blk_mv);
     if (b->d_blk_up) cudaFree(b->d_blk_up);
@@ -1672,10 +1665,6 @@ extern "C" void pse_batch_destroy(pse_batch *b) {
     if (b->ev_sorted) cudaEventDestroy(b->ev_sorted);
     if (b->ev_wave) cudaEventDestroy(b->ev_wave);
     if (b->ev_noise) cudaEventDestroy(b->ev_noise);
-    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
-    if (b->ev_body) cudaEventDestroy(b->ev_body);
-    if (b->ev_after) cudaEventDestroy(b->ev_after);
-    for (cudaEvent_t e : b->ev_join) if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : b->ev_pre) if (e) cudaEventDestroy(e);
     delete b;
 }
@@ -1774,23 +1763,15 @@ extern "C" pse_status pse_batch_create(pse_batch **out, int nsys, const double *
     }
     if (st == PSE_OK && (cudaStreamCreateWithFlags(&b->root, cudaStreamNonBlocking) != cudaSuccess ||
                          cudaStreamCreateWithFlags(&b->body, cudaStreamNonBlocking) != cudaSuccess ||
-                         cudaStreamCreateWithFlags(&b->body2, cudaStreamNonBlocking) != cudaSuccess ||
                          cudaStreamCreateWithFlags(&b->wave, cudaStreamNonBlocking) != cudaSuccess ||
                          cudaEventCreateWithFlags(&b->ev_sorted, cudaEventDisableTiming) != cudaSuccess ||
                          cudaEventCreateWithFlags(&b->ev_wave, cudaEventDisableTiming) != cudaSuccess ||
-                         cudaEventCreateWithFlags(&b->ev_noise, cudaEventDisableTiming) != cudaSuccess ||
-                         cudaEventCreateWithFlags(&b->ev_eig, cudaEventDisableTiming) != cudaSuccess ||
-                         cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-                         cudaEventCreateWithFlags(&b->ev_body, cudaEventDisableTiming) != cudaSuccess ||
-                         cudaEventCreateWithFlags(&b->ev_after, cudaEventDisableTiming) != cudaSuccess))
+                         cudaEventCreateWithFlags(&b->ev_noise, cudaEventDisableTiming) != cudaSuccess))
         st = PSE_ECUDA;
     if (st == PSE_OK) {
-        b->ev_join.assign(nsys, nullptr);
         b->ev_pre.assign(nsys, nullptr);
         for (int k = 0; k < nsys && st == PSE_OK; ++k)
-            if (cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&b->ev_pre[k], cudaEventDisableTiming) != cudaSuccess)
-                st = PSE_ECUDA;
+            if (cudaEventCreateWithFlags(&b->ev_pre[k], cudaEventDisableTiming) != cudaSuccess) st = PSE_ECUDA;
         std::vector<LzState *> lzs(nsys);
         for (int k = 0; k < nsys; ++k) lzs[k] = b->sys[k]->df.lz;
         if (st == PSE_OK && cudaMemcpy(b->d_lzs, lzs.data(), sizeof(LzState *) * nsys, cudaMemcpyHostToDevice) != cudaSuccess)
