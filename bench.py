@@ -90,9 +90,9 @@ def dist_env():
     return ws, rank, local
 
 
-def clocks_start():
-    f = open(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-             else os.devnull, "w")
+def clocks_start(rank=0):
+    keep = rank == 0 and os.path.isdir(os.path.join(ROOT, "gpurun_out"))  # one log, from rank 0
+    f = open(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if keep else os.devnull, "w")
     try:
         p = subprocess.Popen(["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
                               "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -492,7 +492,7 @@ def main():
     stream = torch.cuda.current_stream()
     seed = replica_seed(rank)
 
-    clk, clkf = clocks_start()
+    clk, clkf = clocks_start(rank)
     for i in range(args.warmup):
         s.sample(d_pos, seed, i, out=out)
     torch.cuda.synchronize()
