@@ -53,7 +53,7 @@ __global__ void k_bin(int64_t N, const SampleArgs<T> *args, Geom<T> g, int *cell
 template <typename T>
 __device__ __forceinline__ void scatter_elem(int64_t i, const SampleArgs<T> *args, const Geom<T> &g,
                                              const int *cell_of, const int *slot, const int *start, V4<T> *pos_sorted,
-                                             V4<T> *loc_sorted, Rec<T> *rec) {
+                                             V4<T> *loc_sorted) {
     const T *p = args->pos + 3 * i;
     const T x = wrap_box(p[0], g.L), y = wrap_box(p[1], g.L), z = wrap_box(p[2], g.L);
     const int c = cell_of[i];
@@ -71,15 +71,14 @@ __device__ __forceinline__ void scatter_elem(int64_t i, const SampleArgs<T> *arg
     l.z = cell_offset(z, cz, g.cs, g.cs_lo);
     if constexpr (sizeof(T) == 4) l.w = __int_as_float(c);
     else l.w = __longlong_as_double((long long)c);
-    loc_sorted[dst] = l;
-    rec[dst].l = l;
+    loc_sorted[dst] = l;  // the per-cell sort copies the offsets into the matvec records
 }
 
 template <typename T>
 __global__ void k_scatter(int64_t N, const SampleArgs<T> *args, Geom<T> g, const int *cell_of, const int *slot,
-                          const int *start, V4<T> *pos_sorted, V4<T> *loc_sorted, Rec<T> *rec) {
+                          const int *start, V4<T> *pos_sorted, V4<T> *loc_sorted) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < N) scatter_elem<T>(i, args, g, cell_of, slot, start, pos_sorted, loc_sorted, rec);
+    if (i < N) scatter_elem<T>(i, args, g, cell_of, slot, start, pos_sorted, loc_sorted);
 }
 
 template <typename T> __device__ __forceinline__ long long w_bits(T w) {
@@ -250,8 +249,7 @@ __global__ void __launch_bounds__(1024) k_scan_batch(const BSys *__restrict__ sy
 __global__ void k_scatter_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
     PSE_BATCH_SYS(BK_SCATTER);
     for (int64_t i = lb * (int64_t)blockDim.x + threadIdx.x; i < S.N; i += stride)
-        scatter_elem<float>(i, S.d.args, S.g, S.d.cell_of, S.d.slot, S.d.cell_start, S.d.pos_sorted, S.d.loc_sorted,
-                            S.d.rec);
+        scatter_elem<float>(i, S.d.args, S.g, S.d.cell_of, S.d.slot, S.d.cell_start, S.d.pos_sorted, S.d.loc_sorted);
 }
 __global__ void k_cellsort_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
     PSE_BATCH_SYS(BK_SORT);
@@ -376,7 +374,7 @@ void launch_bin(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d
 template <typename T>
 void launch_scatter(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
     k_scatter<T><<<nblk(N, 256), 256, 0, s>>>(N, args, g, d.cell_of, d.slot, d.cell_start, d.pos_sorted,
-                                              d.loc_sorted, d.rec);
+                                              d.loc_sorted);
 }
 
 template <typename T> void launch_cellsort(int ncell3, const Dev<T> &d, cudaStream_t s) {
