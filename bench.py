@@ -91,9 +91,9 @@ def dist_env():
     return ws, rank, local
 
 
-def clocks_start(rank=0):
-    keep = rank == 0 and os.path.isdir(os.path.join(ROOT, "gpurun_out"))  # one log, from rank 0
-    f = open(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if keep else os.devnull, "w")
+def clocks_start(rank=0, log_path=None):
+    keep = rank == 0 and log_path  # one raw log, from rank 0, when asked for
+    f = open(log_path if keep else os.devnull, "w")
     try:
         p = subprocess.Popen(["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
                               "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -469,6 +469,8 @@ def main():
     ap.add_argument("--xi", type=float, default=None,
                     help="skip the xi scan and sample at this xi (with --grid; a profiling aid)")
     ap.add_argument("--grid", type=int, default=0, help="with --xi: the FFT grid per side")
+    ap.add_argument("--clock-log", default=None,
+                    help="also write the raw nvidia-smi samples of the timed region to this file")
     ap.add_argument("--interp-form", type=int, default=0, choices=[0, 1],
                     help="interpolation form of the headline sampler (1: planar grids; a profiling aid)")
     args = ap.parse_args()
@@ -508,7 +510,7 @@ def main():
     stream = torch.cuda.current_stream()
     seed = replica_seed(rank)
 
-    clk, clkf = clocks_start(rank)
+    clk, clkf = clocks_start(rank, args.clock_log)
     for i in range(args.warmup):
         s.sample(d_pos, seed, i, out=out)
     torch.cuda.synchronize()
