@@ -36,8 +36,17 @@ N_PART, PHI, XI, TOL, SEED_POS = 1_000_000, 0.1, 0.5, 1e-3, 1
 # (grid 256^3, the largest xi that grid admits); the oracle arm, which has no
 # GPU to run the scan, samples at it
 XI_TUNED, M_TUNED = 0.5178442916, 256
-CPU_SAMPLE_N = 250_000  # bounded CPU sample: same density and parameters, smaller box
+CPU_SAMPLE_N = 100_000  # bounded CPU sample: same density and parameters, smaller box
 REF_BUDGET_S = 150.0    # the oracle arm's warm-up + timed steps together
+# wall time of one oracle sample per particle on the GPU machine's host (16 Arm
+# cores): 6.5 s for N = 2.5e5
+REF_S_PER_PARTICLE = 2.6e-5
+
+
+def ref_sample_size(steps, warmup):
+    """Particles per oracle-arm step: a function of the step count only."""
+    n = int(REF_BUDGET_S / (max(steps + warmup, 1) * REF_S_PER_PARTICLE)) // 1000 * 1000
+    return max(4000, min(CPU_SAMPLE_N, n))
 
 
 def workload_config(plan=None, tuning=None, xi=XI_TUNED):
@@ -168,21 +177,97 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def cpu_baseline(xi=XI_TUNED, budget_s=30.0):
-    """The FP64 oracle (as it stands) on a bounded sample: N=2.5e5 at the same phi/xi/tol."""
+def _oracle_sample_times(n, xi, reps, seed0=0):
+    """Wall and CPU seconds of `reps` FP64 oracle PSE samples (real Lanczos
+    part + gridded wave part) of an n-particle box at the headline's density
+    and parameters; the configuration is generated outside the timing."""
+    import resource
     import numpy as np
     from oracle import ewald, pse
     from paper_1611_09322_gb300 import workloads
-    pos, L, _ = workloads.hard_spheres(CPU_SAMPLE_N, PHI, SEED_POS)
+    pos, L, _ = workloads.hard_spheres(n, PHI, SEED_POS)
     p = pos.astype(np.float64)
-    t0 = time.perf_counter()
-    plan = ewald.plan(L, 1.0, xi, TOL)
-    ur, j, _ = pse.real_sample(p, plan, 7, 0)
-    uw = pse.wave_sample_grid(p, plan, 7, 0)
-    dt = time.perf_counter() - t0
-    return {"value": CPU_SAMPLE_N / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"one FP64 oracle PSE sample of N={CPU_SAMPLE_N} hard spheres at phi={PHI}, tol={TOL}, "
-                      f"xi={xi:.4f} (M={plan.M}, Lanczos j={j}); numpy/scipy on the host cores; {dt:.1f} s"}
+    walls, cpus, js = [], [], []
+    for r in range(reps):
+        r0 = resource.getrusage(resource.RUSAGE_SELF)
+        t0 = time.perf_counter()
+        plan = ewald.plan(L, 1.0, xi, TOL)
+        ur, j, _ = pse.real_sample(p, plan, 7, seed0 + r)
+        uw = pse.wave_sample_grid(p, plan, 7, seed0 + r)
+        walls.append(time.perf_counter() - t0)
+        r1 = resource.getrusage(resource.RUSAGE_SELF)
+        cpus.append(r1.ru_utime - r0.ru_utime + r1.ru_stime - r0.ru_stime)
+        js.append(j)
+    return walls, cpus, js, plan.M
+
+
+def _one_thread_env():
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    return env
+
+
+def _quartiles(x):
+    q = statistics.quantiles(x, n=4, method="inclusive") if len(x) > 1 else [x[0]] * 3
+    return q[0], statistics.median(x), q[2]
+
+
+def cpu_baseline(xi=XI_TUNED, n=CPU_SAMPLE_N, reps=3, one_thread=True):
+    """The FP64 oracle as it stands, on a bounded sample of the headline
+    workload: `reps` samples of an n-particle box at the same density, xi and
+    tol (median and interquartile range of particle-samples/s), on the host's
+    cores as the oracle uses them (`cores` = CPU time / wall time, the
+    threads it actually kept busy), plus one sample in a subprocess limited
+    to one thread."""
+    walls, cpus, js, M = _oracle_sample_times(n, xi, reps)
+    rates = [n / w for w in walls]
+    q1, med, q3 = _quartiles(rates)
+    busy = sum(cpus) / sum(walls)
+    out = {"value": med, "unit": UNIT, "cores": max(1, round(busy)), "cpu_time_per_wall": round(busy, 2),
+           "host_cores": os.cpu_count(), "cpu_model": _cpu_model(), "kind": "oracle",
+           "iqr": [q1, q3], "samples": len(rates),
+           "sample": f"{reps} FP64 oracle PSE samples of N={n} hard spheres at phi={PHI}, tol={TOL}, xi={xi:.4f} "
+                     f"(M={M}, Lanczos j={js}); numpy/scipy; median {statistics.median(walls):.2f} s per sample"}
+    if one_thread:
+        code = ("import json,sys; sys.path.insert(0, %r); import bench; w, c, j, M = "
+                "bench._oracle_sample_times(%d, %r, 1, 100); print(json.dumps([w[0], c[0]]))" % (ROOT, n, xi))
+        try:
+            p = subprocess.run([sys.executable, "-c", code], env=_one_thread_env(), capture_output=True, text=True,
+                               timeout=600)
+            w1, c1 = json.loads(p.stdout.strip().splitlines()[-1])
+            out["one_thread"] = {"value": n / w1, "unit": UNIT, "wall_s": round(w1, 3),
+                                 "cpu_time_per_wall": round(c1 / w1, 2)}
+        except (subprocess.SubprocessError, ValueError, IndexError) as e:
+            out["one_thread"] = {"unavailable": str(e)[:200]}
+    return out
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "processor name"):
+                    return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def run_cpu_full(args):
+    """The CPU protocol at the headline size: N = 1e6, `--steps` FP64 oracle
+    samples (at least 3) on the host's cores as the oracle uses them, median
+    and interquartile range, and one sample limited to one thread."""
+    reps = max(3, min(args.steps, 10))
+    line = cpu_baseline(XI_TUNED, n=N_PART, reps=reps, one_thread=True)
+    line = {"impl": "oracle-cpu", "metric": METRIC, "config": workload_config(), **line}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_reference(args):
@@ -199,16 +284,11 @@ def run_reference(args):
         plan = ewald.plan(L, 1.0, XI_TUNED, TOL)
         return p, plan, pse.RealOperator(p, plan)
 
-    # each step is a bounded sample: the box (same density and parameters) is
-    # sized from a timed calibration sample so that warm-up and timed steps
-    # take about REF_BUDGET_S together, at most CPU_SAMPLE_N particles
-    p, plan, op = setup(20_000)
-    t0 = time.perf_counter()
-    pse.real_sample(p, plan, 7, 0, op=op)
-    pse.wave_sample_grid(p, plan, 7, 0)
-    per_particle = (time.perf_counter() - t0) / 20_000
-    n_ref = int(REF_BUDGET_S / (max(args.steps + args.warmup, 1) * per_particle)) // 1000 * 1000
-    n_ref = max(4000, min(CPU_SAMPLE_N, n_ref))
+    # each step is a bounded sample: the box (same density and parameters)
+    # holds N_ref particles, fixed by the step count alone (no timing), so
+    # that warm-up and timed steps take about REF_BUDGET_S together at the
+    # oracle's measured cost of REF_S_PER_PARTICLE seconds per particle
+    n_ref = ref_sample_size(args.steps, args.warmup)
     p, plan, op = setup(n_ref)
 
     def step(i):
@@ -216,22 +296,27 @@ def run_reference(args):
         uw = pse.wave_sample_grid(p, plan, 7, i)
         return j
 
+    import resource
     for i in range(args.warmup):
         step(i)
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
     t0 = time.perf_counter()
     for i in range(args.steps):
         step(1000 + i)
     dt = time.perf_counter() - t0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    busy = (r1.ru_utime - r0.ru_utime + r1.ru_stime - r0.ru_stime) / dt
     value = n_ref * args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(workload_config(), precision="fp64 throughout (the CPU oracle)", M=plan.M),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": max(1, round(busy)),
+                             "cpu_time_per_wall": round(busy, 2), "host_cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"each step: one FP64 oracle PSE sample of N={n_ref} at phi={PHI} "
-                                       f"(same density, tol and xi={XI_TUNED:.4f} as the N=1e6 workload, box "
-                                       f"sized for ~{REF_BUDGET_S:.0f} s over all steps; neighbour pairs built "
-                                       f"once outside the timed steps)"},
+                                       f"(same density, tol and xi={XI_TUNED:.4f} as the N=1e6 workload; N "
+                                       f"fixed by --steps/--warmup for ~{REF_BUDGET_S:.0f} s over all steps; "
+                                       f"neighbour pairs built once outside the timed steps)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -324,12 +409,15 @@ def variants_learned_batched(dev, flush, stream, steps, xi, M):
     import torch
     from paper_1611_09322_gb300 import BatchSampler, Sampler, precond_train, workloads
     out = {}
-    theta, info = precond_train.train(xi=xi, tol=TOL, steps=1500, lr=3e-3)
+    # the network is kept only if it cuts the held-out mean Lanczos count by
+    # one iteration; otherwise the learned form falls back to P = I
+    theta, info = precond_train.train_or_fallback(xi=xi, tol=TOL, steps=1500, lr=3e-3)
+    theta_raw = info.pop("theta")
     out["learned_training"] = {k: v for k, v in info.items() if k != "loss_hist"}
     pos, L, _ = workloads.hard_spheres(N_PART, PHI, SEED_POS)
     d = torch.from_numpy(pos).to(dev)
     o = torch.empty_like(d)
-    for name, th in (("plain_N1e6", None), ("learned_N1e6", theta)):
+    for name, th in (("plain_N1e6", None), ("learned_N1e6", theta), ("learned_no_fallback_N1e6", theta_raw)):
         s = Sampler(L, 1.0, xi=xi, tol=TOL, grid_M=M)
         if th is not None:
             s.precond_set_weights(th)
@@ -338,7 +426,9 @@ def variants_learned_batched(dev, flush, stream, steps, xi, M):
         per = timed_steps(lambda i: s.sample(d, 1, 200 + i, out=o), steps, flush, stream)
         st = s.stats()
         out[name] = {"value": N_PART * steps / (sum(per) / 1e3), "ms_per_step": sum(per) / steps,
-                     "lanczos_iters": st["lanczos_iters"], "converged": st["converged"]}
+                     "lanczos_iters": st["lanczos_iters"], "converged": st["converged"],
+                     "preconditioner": "none" if name.startswith("plain") else
+                     ("network" if th is not None else "fallback P = I (no held-out iteration gain)")}
         s.close()
     # the forces path at the same workload: deterministic M F alone (the
     # paper's deterministic benchmark), one fused Euler-Maruyama displacement
@@ -384,30 +474,45 @@ def variants_learned_batched(dev, flush, stream, steps, xi, M):
         b = BatchSampler(Ls, 1.0, xi=XI, tol=TOL, autotune=9)
         if th is not None:
             for k in range(len(spec)):
-                _lib_set(b, k, th)
+                b.set_precond(k, th)
         for i in range(3):
             b.sample(pa, offsets, 1, i, out=po)
         per = timed_steps(lambda i: b.sample(pa, offsets, 1, 300 + i, out=po), steps, flush, stream)
         its = [b.stats(k)["lanczos_iters"] for k in range(len(spec))]
         out[name] = {"value": int(offsets[-1]) * steps / (sum(per) / 1e3), "ms_per_step": sum(per) / steps,
-                     "n_systems": len(spec), "n_particles": int(offsets[-1]), "lanczos_iters_mean": float(np.mean(its))}
+                     "n_systems": len(spec), "n_particles": int(offsets[-1]), "lanczos_iters_mean": float(np.mean(its)),
+                     "preconditioner": "none" if th is None and name.endswith("plain") else
+                     ("network" if th is not None else "fallback P = I (no held-out iteration gain)")}
+        grids = [b.plan(k)["M"] for k in range(len(spec))]
+        xis = [b.plan(k)["xi"] for k in range(len(spec))]
         b.close()
+    # the same 64 systems without batching: one lone sampler per system (its
+    # own xi, grid and CUDA graph, the settings the batch gave it), sampled
+    # one after another on one stream, timed with the same protocol
+    lone = [Sampler(Lk, 1.0, xi=xis[k], tol=TOL, grid_M=grids[k], system=k) for k, Lk in enumerate(Ls)]
+    views = [pa[offsets[k]:offsets[k + 1]] for k in range(len(spec))]
+    outs = [po[offsets[k]:offsets[k + 1]] for k in range(len(spec))]
+
+    def lone_step(i):
+        for k, sk in enumerate(lone):
+            sk.sample(views[k], 1, 300 + i, out=outs[k])
+    for i in range(3):
+        lone_step(i)
+    per = timed_steps(lone_step, steps, flush, stream)
+    its = [sk.stats()["lanczos_iters"] for sk in lone]
+    out["batched_64sys_lone"] = {"value": int(offsets[-1]) * steps / (sum(per) / 1e3), "ms_per_step": sum(per) / steps,
+                                 "n_systems": len(spec), "n_particles": int(offsets[-1]),
+                                 "lanczos_iters_mean": float(np.mean(its)),
+                                 "what": "the 64 systems through 64 lone samplers (one CUDA graph each, same xi and "
+                                         "grid as in the batch), one after another on one stream"}
+    for sk in lone:
+        sk.close()
     out["workload_batched"] = ("64 periodic systems, N log-uniform in [1e3, 5e4], phi uniform in [0.05, 0.4], "
                                "half fractal gels (phi <= 0.2), each with its own box, FFT grid (the planned grid "
                                "raised to a size class) and xi (the largest its grid admits, from xi a = 0.5), "
                                "tol 1e-3; one CUDA graph launch per step")
     out["variants_xi"] = {"xi": xi, "M": M, "note": "the N=1e6 variants run at the headline's tuned xi and grid"}
     return out
-
-
-def _lib_set(batch, k, theta):
-    """Install preconditioner weights in system k of a batch (through its context)."""
-    import ctypes
-    import numpy as np
-    from paper_1611_09322_gb300 import _lib
-    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float32))
-    _lib.check(batch.lib.pse_batch_set_precond(batch.h, k, th.ctypes.data_as(ctypes.c_void_p), th.size),
-               "pse_batch_set_precond")
 
 
 def run_only(args):
@@ -462,6 +567,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="only the CPU protocol at N = 1e6: the FP64 oracle, max(3, min(--steps, 10)) samples, "
+                         "median and IQR, and one sample on one thread")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--only", choices=["forces", "batch"], default=None,
                     help="run one secondary workload alone (profiling aid)")
@@ -478,6 +586,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.cpu_full:
+        return run_cpu_full(args)
     if args.only:
         return run_only(args)
 
@@ -589,6 +699,11 @@ def main():
                 "parallelism": "replicas" if ws > 1 else "single GPU"}
         if not args.no_variants and ws == 1:
             line["variants"] = variants_learned_batched(dev, flush, stream, max(20, args.steps // 4), xi, M_grid)
+            # the metric's comparison at the top level: learned (with its
+            # fallback) and batched against plain, and the batch against the
+            # same systems sampled one by one
+            for k in ("learned_N1e6", "batched_64sys_plain", "batched_64sys_learned", "batched_64sys_lone"):
+                line[k] = line["variants"][k]
             line["variants"].update(variants_configs(dev, flush, stream, 10, peak))
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(xi)

@@ -423,8 +423,11 @@ pse_status pse_profile_stages(pse_ctx *ctx, int64_t N, const float *d_pos, uint6
  *   d_pos, d_v, d_out: 3N float32 device arrays in the caller's order.
  * No context and no allocation: all scratch (cell list, sorted positions,
  * neighbour list, F/G table) lives in one static device array of about
- * 12 MB that every GPU loading this library reserves until the process
- * exits.  Limits: N <= 16384, ncell^3 <= 32768 cells (box side up to about
+ * 12 MB.  The module holding it is loaded on a device when it is first used
+ * there (CUDA loads modules lazily by default), so the first call on each
+ * device reserves the array, which then stays reserved until the process
+ * exits; a caller with a fixed memory budget should make that first call
+ * during its set-up.  Limits: N <= 16384, ncell^3 <= 32768 cells (box side up to about
  * 32 r_cut), at most 2,621,440 / N neighbours within r_cut per particle
  * (160 at N = 16384); beyond the first two it returns PSE_EINVAL before
  * launching anything, beyond the last PSE_ENOMEM after the run (the output

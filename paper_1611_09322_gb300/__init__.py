@@ -86,7 +86,14 @@ def pse_real_matvec_noalloc(L, a, xi, tol, pos, v, out):
     For callers that may not allocate device memory: `out` must be
     preallocated by the caller; nothing is allocated by the library.
     """
+    import torch
     lib = _lib.load()
+    dev = torch.cuda.current_device()
+    for name, t in (("pos", pos), ("v", v), ("out", out)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+                and t.dim() == 2 and t.shape[1] == 3 and t.shape[0] == pos.shape[0] and t.device.index == dev):
+            raise ValueError(f"{name} must be a contiguous (N, 3) float32 CUDA tensor on the current device, "
+                             f"shaped like pos")
     _lib.check(lib.pse_real_matvec_noalloc(L, a, xi, tol, pos.shape[0], _ptr(pos), _ptr(v), _ptr(out), _stream()),
                "pse_real_matvec_noalloc")
     return out
@@ -328,12 +335,28 @@ class BatchSampler:
     def sample(self, pos_all, offsets, seed, sample_index=0, out=None):
         """pos_all: (sum N, 3) float32 CUDA, systems concatenated; offsets: n+1 ints."""
         import torch
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        if not (pos_all.is_cuda and pos_all.dtype == torch.float32 and pos_all.is_contiguous()
+                and pos_all.dim() == 2 and pos_all.shape[1] == 3):
+            raise ValueError("positions must be a contiguous (N, 3) float32 CUDA tensor")
+        if off.shape != (self.n + 1,) or off[-1] != pos_all.shape[0]:
+            raise ValueError("offsets must hold n_systems + 1 entries ending at the number of particles")
         if out is None:
             out = torch.empty_like(pos_all)
-        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        elif out.shape != pos_all.shape or out.dtype != pos_all.dtype or not out.is_contiguous() or not out.is_cuda:
+            raise ValueError("out must be a contiguous CUDA tensor shaped and typed like the positions")
         _lib.check(self.lib.pse_batch_sample(self.h, off.ctypes.data_as(ctypes.c_void_p), _ptr(pos_all), seed,
                                              sample_index, _ptr(out), _stream()), "pse_batch_sample")
         return out
+
+    def set_precond(self, k, theta):
+        """Install learned-preconditioner weights in system k (None removes them)."""
+        if theta is None:
+            _lib.check(self.lib.pse_batch_set_precond(self.h, k, None, 0), "pse_batch_set_precond")
+            return
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float32).ravel())
+        _lib.check(self.lib.pse_batch_set_precond(self.h, k, th.ctypes.data_as(ctypes.c_void_p), th.size),
+                   "pse_batch_set_precond")
 
     def stats(self, k):
         s = pse_stats()

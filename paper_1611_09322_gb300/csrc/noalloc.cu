@@ -5,8 +5,11 @@
 // own pool, a plugin that may not grow the process footprint, or a caller
 // that needs a fixed, known-in-advance memory budget).  For them this file
 // keeps every scratch buffer of the matvec in one file-scope static device
-// array of fixed size.  Every GPU that loads the library reserves that array
-// until the process exits.
+// array of fixed size.  With CUDA's lazy module loading the array is
+// reserved on a device when this module is first used there (the first
+// call's cudaGetSymbolAddress), and it stays reserved until the process
+// exits; a caller with a fixed memory budget makes that first call during
+// its own set-up.
 #include <string.h>
 
 #include "pse_internal.cuh"
@@ -160,6 +163,9 @@ extern "C" pse_status pse_real_matvec_noalloc(double L, double a, double xi, dou
     launch_cellsort<float>((int)nc3, d, s);
     launch_nbr<float>(N, g, d, s);
     launch_matvec_caller<float>(N, d.args, g, d, s);
+    // a launch that failed to start (configuration, resources) is reported
+    // here, not by the synchronisation below
+    if (cudaGetLastError() != cudaSuccess) return PSE_ECUDA;
     int overflow = 0;
     if (cudaMemcpyAsync(&overflow, &sc->lz.overflow, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {

@@ -96,9 +96,9 @@ def test_batch_grids_are_size_classes_at_least_the_plan(torch):
 
 def test_batch_grid_fit_xi(torch):
     """autotune bit 3 in a batch: each system keeps its size-class grid and
-    takes the largest xi that grid admits; its sample equals a lone context at
-    that (xi, grid) and the oracle's wave part at that xi."""
-    from oracle import ewald, pse
+    takes the largest xi that grid admits (checked against the host plan);
+    its sample equals a lone context at that (xi, grid).  The oracle
+    comparison at those settings is test_batch_matches_oracle."""
     from paper_1611_09322_gb300 import BatchSampler, Sampler, pse_plan
     systems = _systems()
     Ls = [L for _, L, _ in systems]
@@ -116,4 +116,101 @@ def test_batch_grid_fit_xi(torch):
         got = out[offsets[k]:offsets[k + 1]]
         assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max(), k
         s.close()
+    b.close()
+
+
+def _oracle_system(pos, plan_k, k, sample, J, precond=None):
+    """The FP64 oracle's sample of system k (Philox streams 2k, 2k + 1) on the
+    grid, support and xi the batch planned for it: the Lanczos real part after
+    exactly J steps (Sec. II B 1) plus the gridded wave part (Sec. II B 2)."""
+    from oracle import ewald, pse
+    p = pos.astype(np.float64)
+    plan = ewald.plan(plan_k["L"], 1.0, plan_k["xi"], plan_k["tol"], M=plan_k["M"], P=plan_k["P"])
+    ur, j, _ = pse.real_sample(p, plan, SEED, sample, n_iter=J, precond=precond, system=k)
+    uw = pse.wave_sample_grid(p, plan, SEED, sample, system=k)
+    return ur + uw, plan
+
+
+def _check(got, ref, tol=1e-4):
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+    assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("autotune", [0, 8])
+def test_batch_matches_oracle(torch, autotune):
+    """Every system of a batch (mixed hard spheres and gels, uneven N, own xi
+    and size-class grid, all at P = 5 so the pooled node-major interpolation
+    runs) equals the FP64 oracle element by element at a fixed Lanczos J;
+    with autotune bit 3 each system runs at the largest xi its grid admits,
+    the setting the benchmark uses."""
+    from paper_1611_09322_gb300 import BatchSampler
+    systems = _systems()
+    J = 6
+    b = BatchSampler([L for _, L, _ in systems], 1.0,
+                     params=[dict(xi=xi, tol=1e-3, fixed_iter=J, autotune=autotune) for _, _, xi in systems])
+    offsets = np.cumsum([0] + [p.shape[0] for p, _, _ in systems])
+    pos_all = torch.from_numpy(np.concatenate([p for p, _, _ in systems])).cuda()
+    out = b.sample(pos_all, offsets, SEED, 11).cpu().numpy()
+    assert len({b.plan(k)["P"] for k in range(len(systems))}) == 1
+    for k, (pos, L, xi) in enumerate(systems):
+        assert b.stats(k)["lanczos_iters"] == J
+        ref, _ = _oracle_system(pos, b.plan(k), k, 11, J)
+        _check(out[offsets[k]:offsets[k + 1]], ref)
+    b.close()
+
+
+def test_batch_stop_rule_matches_oracle(torch):
+    """Without a fixed J every system stops by the Lanczos test on its own;
+    the J it reports is the oracle's (skipped where the oracle's statistic is
+    within 5% of tol) and the sample equals the oracle's at that J."""
+    from oracle import ewald, pse
+    from paper_1611_09322_gb300 import BatchSampler
+    systems = _systems()
+    b = BatchSampler([L for _, L, _ in systems], 1.0, params=[dict(xi=xi, tol=1e-3) for _, _, xi in systems])
+    offsets = np.cumsum([0] + [p.shape[0] for p, _, _ in systems])
+    pos_all = torch.from_numpy(np.concatenate([p for p, _, _ in systems])).cuda()
+    out = b.sample(pos_all, offsets, SEED, 12).cpu().numpy()
+    for k, (pos, L, xi) in enumerate(systems):
+        pk = b.plan(k)
+        plan = ewald.plan(pk["L"], 1.0, pk["xi"], pk["tol"], M=pk["M"], P=pk["P"])
+        _, j_or, hist = pse.real_sample(pos.astype(np.float64), plan, SEED, 12, system=k)
+        J = b.stats(k)["lanczos_iters"]
+        assert b.stats(k)["converged"] == 1
+        if J != j_or:
+            assert min(abs(h / 1e-3 - 1.0) for h in hist) < 0.05, (k, J, j_or)
+        ref, _ = _oracle_system(pos, pk, k, 12, J)
+        _check(out[offsets[k]:offsets[k + 1]], ref)
+    b.close()
+
+
+def test_batch_learned_matches_oracle(torch):
+    """The learned + batched form: the network installed in some systems of
+    the batch (pse_batch_set_precond, fused inference kernel) gives, per
+    system, the oracle's S^-1 (S M_r S)^{1/2} z1 + wave part after J steps,
+    S from the oracle network with the same weights; the other systems stay
+    the plain sample."""
+    from oracle import precond
+    from paper_1611_09322_gb300 import BatchSampler
+    from paper_1611_09322_gb300.precond_train import init_theta
+    systems = _systems()
+    J = 7
+    theta = (init_theta(5) + 0.2 * np.random.default_rng(9).standard_normal(precond.NPARAM)).astype(np.float32)
+    b = BatchSampler([L for _, L, _ in systems], 1.0,
+                     params=[dict(xi=xi, tol=1e-3, fixed_iter=J, autotune=8) for _, _, xi in systems])
+    learned = {0, 2, 3}
+    for k in learned:
+        b.set_precond(k, theta)
+    offsets = np.cumsum([0] + [p.shape[0] for p, _, _ in systems])
+    pos_all = torch.from_numpy(np.concatenate([p for p, _, _ in systems])).cuda()
+    out = b.sample(pos_all, offsets, SEED, 13).cpu().numpy()
+    for k, (pos, L, xi) in enumerate(systems):
+        pk = b.plan(k)
+        S = None
+        if k in learned:
+            from oracle import ewald
+            plan = ewald.plan(pk["L"], 1.0, pk["xi"], pk["tol"], M=pk["M"], P=pk["P"])
+            fo, To = precond.features(pos.astype(np.float64), plan)
+            S, _ = precond.forward(theta.astype(np.float64), fo, To, pk["self_mobility"] ** -0.5)
+        ref, _ = _oracle_system(pos, pk, k, 13, J, precond=S)
+        _check(out[offsets[k]:offsets[k + 1]], ref)
     b.close()

@@ -106,26 +106,53 @@ def test_training_and_preconditioned_sample(torch):
     s.close()
 
 
-def test_iteration_counts_with_and_without(torch):
-    """What the trained network changes: Lanczos iterations to reach tol (same
-    stop rule), plain vs learned, over several samples; both samples are
-    converged to the same tolerance.  The gain is recorded, not assumed."""
+def test_learned_form_never_costs_time_without_a_gain(torch):
+    """What the trained network changes, and the fallback that keeps it
+    honest: the mean Lanczos count over held-out configurations without and
+    with the network decides.  If the network cuts it by at least one
+    iteration it is kept and must do so on a fresh configuration too;
+    otherwise the preconditioner falls back to P = I, and the learned form
+    then runs exactly the plain sampler's kernels: the same J, the same
+    sample bit for bit, and no more time (within 10% timing noise)."""
     from paper_1611_09322_gb300 import Sampler, precond_train, workloads
-    theta, _ = precond_train.train(sets=[("hs", 4000, 0.3, 21), ("hs", 3000, 0.4, 22)], steps=400, lr=3e-3)
-    pos, L, _ = workloads.hard_spheres(5000, 0.3, 23)
+    theta, info = precond_train.train_or_fallback(xi=0.5, tol=1e-3, sets=[("hs", 4000, 0.3, 21),
+                                                                           ("hs", 3000, 0.4, 22)],
+                                                  steps=400, lr=3e-3)
+    print(f"\nheld-out Lanczos iterations at tol 1e-3: plain {info['iters_plain']:.2f}, "
+          f"learned {info['iters_learned']:.2f}, fallback {info['fallback']}")
+    assert info["fallback"] == (info["gain"] < 1.0)
+    pos, L, _ = workloads.hard_spheres(20000, 0.3, 23)
     d = torch.from_numpy(pos).cuda()
     plain = Sampler(L, 1.0, xi=0.5, tol=1e-3)
     learned = Sampler(L, 1.0, xi=0.5, tol=1e-3)
     learned.precond_set_weights(theta)
     jp, jl = [], []
     for k in range(5):
-        plain.sample(d, SEED, k)
-        learned.sample(d, SEED, k)
+        up = plain.sample(d, SEED, k).clone()
+        ul = learned.sample(d, SEED, k)
         sp, sl = plain.stats(), learned.stats()
         assert sp["converged"] == 1 and sl["converged"] == 1
         jp.append(sp["lanczos_iters"])
         jl.append(sl["lanczos_iters"])
-    print(f"\nLanczos iterations at tol 1e-3, phi 0.3: plain {np.mean(jp):.2f}, learned {np.mean(jl):.2f}")
-    assert np.mean(jl) <= np.mean(jp) + 1.0
+        if theta is None:
+            assert torch.equal(up, ul)
+    if theta is not None:
+        assert np.mean(jl) <= np.mean(jp) - 1.0
+        return
+
+    def t(s):
+        out = torch.empty_like(d)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for i in range(5):
+            s.sample(d, SEED, 100 + i, out=out)
+        ev[0].record()
+        for i in range(40):
+            s.sample(d, SEED, 200 + i, out=out)
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1])
+    tp, tl = min(t(plain) for _ in range(3)), min(t(learned) for _ in range(3))
+    print(f"plain {tp / 40:.4f} ms, learned (fallback P = I) {tl / 40:.4f} ms per sample")
+    assert jl == jp and tl <= 1.10 * tp
     plain.close()
     learned.close()

@@ -82,11 +82,12 @@ def test_tune_xi_small_box_and_errors(torch):
         pse_tune_xi(L, d, xi=0.5, tol=1e-3, use_precond=1)
 
 
-def test_tuned_headline_workload_full_size(torch):
+def test_tuned_headline_workload_full_size(torch, record_error):
     """N = 1e6 hard spheres at phi = 0.1, tol 1e-3, in the launch configuration
     the benchmark times (xi and grid from pse_tune_xi, one CUDA graph per
-    sample): the Lanczos test converges, near-field rows at sampled particles
-    and the wave part at sampled particles match the oracle at that xi."""
+    sample): the Lanczos test converges; near-field rows at sampled particles
+    match the oracle; the real part after the J steps the test took and the
+    wave part match the oracle's at that xi, grid and J on all 3N values."""
     from oracle import ewald, pse
     from paper_1611_09322_gb300 import Sampler, pse_tune_xi, workloads
     N = 1_000_000
@@ -104,10 +105,18 @@ def test_tuned_headline_workload_full_size(torch):
     rows = np.random.default_rng(9).choice(N, 200, replace=False)
     ref = pse.real_rows(pos.astype(np.float64), plan, rows, v.astype(np.float64))
     assert _maxrel(got[rows], ref) < 1e-5
-    vg, _ = pse.wave_grid_velocity(plan, SEED, 5)
-    refw = pse.interpolate(vg, pos[rows].astype(np.float64), plan)
-    assert _maxrel(uw.cpu().numpy()[rows], refw) < 1e-4
+    J = st["lanczos_iters"]
+    u, ur, uw = u.cpu().numpy(), ur.cpu().numpy(), uw.cpu().numpy()
     s.close()
+    p64 = pos.astype(np.float64)
+    ref_r, _, _ = pse.real_sample(p64, plan, SEED, 5, n_iter=J)
+    ref_w = pse.wave_sample_grid(p64, plan, SEED, 5)
+    record_error(f"headline FP32 N=1e6 phi=0.1 tol=1e-3 xi={xi:.4f} M={M} vs FP64 oracle", J=J,
+                 rel=_rel(u, ref_r + ref_w), maxrel=_maxrel(u, ref_r + ref_w), maxrel_real=_maxrel(ur, ref_r),
+                 maxrel_wave=_maxrel(uw, ref_w), rel_real=_rel(ur, ref_r), rel_wave=_rel(uw, ref_w))
+    assert _maxrel(ur, ref_r) < 1e-4 and _rel(ur, ref_r) < 1e-4
+    assert _maxrel(uw, ref_w) < 1e-4 and _rel(uw, ref_w) < 1e-4
+    assert _maxrel(u, ref_r + ref_w) < 1e-4
 
 
 def test_grid_fit_xi_lone_context(torch):
