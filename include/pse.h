@@ -323,6 +323,30 @@ pse_status pse_bd_step(pse_ctx *ctx, int64_t N, float *d_pos, const float *d_fex
 pse_status pse_bd_step_f64(pse_ctx *ctx, int64_t N, double *d_pos, const double *d_fext, double dt, double kT,
                            double k_rep, uint64_t seed, uint64_t step, void *stream);
 
+/* The comparison method of Sec. IV (Fig. timing, Fig. RelLanc): a Brownian
+ * sample M^{1/2} z drawn by Lanczos applied to the WHOLE mobility M = M_r +
+ * M_w, each iteration one product M q_j -- the near-field M_r q_j (eq.
+ * Mreal) plus the gridded wave product M_w q_j (spread q_j, forward FFT, the
+ * per-mode factor h^3 B(k) (I - kk) of eq. Mwave with the Gaussian
+ * deconvolution, inverse FFT, interpolate: the M F of Sec. III) -- with the
+ * Chow & Saad stop rule and the FP64 Lanczos scalars of pse_sample.  z is
+ * the z1 of pse_sample for the same (seed, sample_index) and the context's
+ * system index.  The paper reports that PSE sampling beats this method by
+ * more than an order of magnitude, its iteration count growing with N.
+ *   d_pos, d_out: 3N float32 device arrays in the caller's order (d_out may
+ *   not alias d_pos).
+ * The iteration count and whether the test passed are reported by
+ * pse_get_stats (PSE_ENOTCONVERGED at the cap max_iter, with the last
+ * iterate written).  The spreading uses float atomics, so the last bits may
+ * differ from call to call.  Contexts with the learned preconditioner
+ * installed return PSE_ENOTSUPPORTED (the method runs on M itself). */
+pse_status pse_sample_full_lanczos(pse_ctx *ctx, int64_t N, const float *d_pos, uint64_t seed,
+                                   uint64_t sample_index, float *d_out, void *stream);
+
+/* FP64 context form of pse_sample_full_lanczos (float64 arrays). */
+pse_status pse_sample_full_lanczos_f64(pse_ctx *ctx, int64_t N, const double *d_pos, uint64_t seed,
+                                       uint64_t sample_index, double *d_out, void *stream);
+
 /* The deterministic product d_out = M d_force alone (pse_sample_with_forces
  * with c_det = 1, c_noise = 0), FP32 context. */
 pse_status pse_mobility_apply(pse_ctx *ctx, int64_t N, const float *d_pos, const float *d_force, float *d_out,

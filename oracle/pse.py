@@ -500,6 +500,21 @@ def real_sample(pos, plan, seed, sample, n_iter=None, lanczos_tol=None, precond=
     return np.linalg.solve(S, x[..., None])[..., 0], j, hist
 
 
+def full_sample(pos, plan, seed, sample, n_iter=None, lanczos_tol=None, system=0, max_iter=100):
+    """The comparison method of Sec. IV (Fig. timing, Fig. RelLanc): Lanczos
+    applied to the whole mobility, M^{1/2} z by the same Chow & Saad
+    iteration and stop rule as the real part, every step one product
+    M q = M_r q + gridded M_w q (``mobility_apply``, the M F of Sec. III).
+    z is the real-space noise z1 of (seed, sample, system).
+    Returns (x (N, 3), j, history of relative changes)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    A = RealOperator(pos, plan)
+    z = real_noise(pos.shape[0], seed, sample, system)
+    tol = plan.tol if lanczos_tol is None else lanczos_tol
+    return lanczos_sqrt(lambda v: mobility_apply(v, pos, plan, op=A), z, tol=tol, n_iter=n_iter,
+                        max_iter=max_iter)
+
+
 def pse_sample(pos, L, a, xi, tol, seed, sample, n_iter=None, M=None, P=None, precond=None):
     """Full PSE sample (N, 3) = real (Lanczos) + wave (gridded NUFFT), FP64.
 

@@ -238,6 +238,17 @@ class Sampler:
                       _stream()), "pse_bd_step")
         return pos
 
+    def sample_full_lanczos(self, pos, seed, sample_index=0, out=None):
+        """M^{1/2} z by Lanczos on the whole mobility (pse_sample_full_lanczos: Sec. IV's comparison method)."""
+        import torch
+        self._check_pos(pos)
+        if out is None:
+            out = torch.empty_like(pos)
+        fn = self.lib.pse_sample_full_lanczos_f64 if self.fp64 else self.lib.pse_sample_full_lanczos
+        _lib.check(fn(self.ctx, pos.shape[0], _ptr(pos), seed, sample_index, _ptr(out), _stream()),
+                   "pse_sample_full_lanczos")
+        return out
+
     def mobility_apply(self, pos, force, out=None):
         """The deterministic product M F (c_det = 1, c_noise = 0)."""
         return self.sample_with_forces(pos, force, 0, 0, 1.0, 0.0, out=out)

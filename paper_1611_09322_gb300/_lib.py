@@ -98,6 +98,8 @@ SIGNATURES = {
     "pse_sample_with_forces_f64": (_ST, [_VP, _I64, _VP, _VP, _U64, _U64, ctypes.c_double, ctypes.c_double, _VP,
                                          _VP]),
     "pse_mobility_apply": (_ST, [_VP, _I64, _VP, _VP, _VP, _VP]),
+    "pse_sample_full_lanczos": (_ST, [_VP, _I64, _VP, _U64, _U64, _VP, _VP]),
+    "pse_sample_full_lanczos_f64": (_ST, [_VP, _I64, _VP, _U64, _U64, _VP, _VP]),
     "pse_bd_step": (_ST, [_VP, _I64, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, _U64, _U64, _VP]),
     "pse_bd_step_f64": (_ST, [_VP, _I64, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, _U64, _U64,
                               _VP]),

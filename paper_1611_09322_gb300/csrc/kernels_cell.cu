@@ -119,10 +119,25 @@ __global__ void k_cellsort(int ncell3, const int *start, V4<T> *pos_sorted, V4<T
 // ncell = 2 the same cell appears under two offsets; r_cut < L/2 leaves at
 // most one image of each pair inside r_cut, so the distance test keeps the
 // right one.  Lists longer than K are cut and flag an overflow.
+// A float32 pair distance within rounding of r_cut (|r^2 - r_cut^2| below
+// 4e-6 r_cut^2, a few ulps of the cell-offset arithmetic) does not decide
+// the pair: it is decided again in float64 from the wrapped positions with
+// the nearest periodic image, so the truncation of eq. Mreal keeps exactly
+// the pairs with r < r_cut in float64, whatever rounding the float path saw.
+__device__ __forceinline__ bool pair_inside_f64(const V4<float> *__restrict__ pos, int64_t s, int t, double L,
+                                                double invL, double rc2) {
+    const V4<float> a = pos[s], b = pos[t];
+    double dx = (double)a.x - (double)b.x, dy = (double)a.y - (double)b.y, dz = (double)a.z - (double)b.z;
+    dx -= L * rint(dx * invL);
+    dy -= L * rint(dy * invL);
+    dz -= L * rint(dz * invL);
+    return dx * dx + dy * dy + dz * dz < rc2;
+}
+
 template <typename T>
 __device__ __forceinline__ int nbr_elem(int64_t s, int64_t N, const Geom<T> &g, const V4<T> *__restrict__ loc,
-                                        const int *__restrict__ cell_start, int *count, int *nbr, int K,
-                                        int *overflow) {
+                                        const V4<T> *__restrict__ pos, const int *__restrict__ cell_start,
+                                        int *count, int *nbr, int K, int *overflow) {
     int cnt = 0;
     {
         const V4<T> li = loc[s];
@@ -157,7 +172,12 @@ __device__ __forceinline__ int nbr_elem(int64_t s, int64_t N, const Geom<T> &g, 
                         const T dy = (li.y - lt.y) - sy;
                         const T dz = (li.z - lt.z) - sz;
                         const T r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 < g.rc2) {
+                        bool in = r2 < g.rc2;
+                        if constexpr (sizeof(T) == 4) {
+                            if (fabsf(r2 - g.rc2) <= 4e-6f * g.rc2)
+                                in = pair_inside_f64(pos, s, t, g.L_d, g.invL_d, g.rc2_d);
+                        }
+                        if (in) {
                             if (cnt < K) {
                                 *dst = (t << 6) | code;
                                 dst += N;
@@ -179,10 +199,11 @@ __device__ __forceinline__ int nbr_elem(int64_t s, int64_t N, const Geom<T> &g, 
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_nbr(int64_t N, Geom<T> g, const V4<T> *__restrict__ loc,
-                                             const int *__restrict__ cell_start, int *count, int *nbr, int K,
-                                             int *overflow, unsigned long long *n_pairs) {
+                                             const V4<T> *__restrict__ pos, const int *__restrict__ cell_start,
+                                             int *count, int *nbr, int K, int *overflow,
+                                             unsigned long long *n_pairs) {
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int cnt = s < N ? nbr_elem<T>(s, N, g, loc, cell_start, count, nbr, K, overflow) : 0;
+    const int cnt = s < N ? nbr_elem<T>(s, N, g, loc, pos, cell_start, count, nbr, K, overflow) : 0;
     // pair total for the statistics: one atomic per warp
     int tot = cnt;
 #pragma unroll
@@ -260,8 +281,8 @@ __global__ void __launch_bounds__(128, 8) k_nbr_batch(const BSys *__restrict__ s
     PSE_BATCH_SYS(BK_NBR);
     for (int64_t s0 = lb * (int64_t)blockDim.x; s0 < S.N; s0 += stride) {  // uniform per block
         const int64_t s = s0 + threadIdx.x;
-        const int cnt = s < S.N ? nbr_elem<float>(s, S.N, S.g, S.d.loc_sorted, S.d.cell_start, S.d.nbr_count,
-                                                   S.d.nbr, S.K, &S.d.lz->overflow)
+        const int cnt = s < S.N ? nbr_elem<float>(s, S.N, S.g, S.d.loc_sorted, S.d.pos_sorted, S.d.cell_start,
+                                                   S.d.nbr_count, S.d.nbr, S.K, &S.d.lz->overflow)
                                 : 0;
         int tot = cnt;
 #pragma unroll
@@ -382,7 +403,7 @@ template <typename T> void launch_cellsort(int ncell3, const Dev<T> &d, cudaStre
 }
 
 template <typename T> void launch_nbr(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
-    k_nbr<T><<<nblk(N, 128), 128, 0, s>>>(N, g, d.loc_sorted, d.cell_start, d.nbr_count, d.nbr,
+    k_nbr<T><<<nblk(N, 128), 128, 0, s>>>(N, g, d.loc_sorted, d.pos_sorted, d.cell_start, d.nbr_count, d.nbr,
                                           nbr_k(N, d.nbr_cap), &d.lz->overflow, &d.lz->n_pairs);
 }
 

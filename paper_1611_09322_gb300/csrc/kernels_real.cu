@@ -228,7 +228,8 @@ __device__ __forceinline__ void lz_matvec_body(int64_t N, int K, const Geom<T> &
                                                const int *__restrict__ count, const int *__restrict__ nbr,
                                                const V4<T> *__restrict__ table, V4<T> *u, double *partials,
                                                LzState *lz, const float *__restrict__ pc,
-                                               const V4<T> *__restrict__ basis, int bidx, int nblk, double *sh) {
+                                               const V4<T> *__restrict__ basis, const V4<T> *__restrict__ add,
+                                               int bidx, int nblk, double *sh) {
     const int j = lz->iter;
     if (j > PSE_MAXIT || !lz->active) return;  // uniform across the system's blocks
     typename Part<T>::type part = 0;
@@ -250,6 +251,12 @@ __device__ __forceinline__ void lz_matvec_body(int64_t N, int K, const Geom<T> &
             o.y = ay + g.self_m * qi.y;
             o.z = az + g.self_m * qi.z;
             o.w = T(0);
+            if (add) {  // full-mobility Lanczos: the wave product M_w q_j of the same vector
+                const V4<T> aw = add[s];
+                o.x += aw.x;
+                o.y += aw.y;
+                o.z += aw.z;
+            }
             if constexpr (sizeof(T) == 4) {
                 if (pc) {  // A = S M_r S: the record holds S q, apply S to the row, dot with q
                     T x, y, z;
@@ -283,17 +290,18 @@ __global__ void __launch_bounds__(128) k_lz_matvec(int64_t N, int K, Geom<T> g, 
                                                    const int *__restrict__ count, const int *__restrict__ nbr,
                                                    const V4<T> *__restrict__ table, const V4<T> *__restrict__ table_c,
                                                    V4<T> *u, double *partials, LzState *lz,
-                                                   const float *__restrict__ pc, const V4<T> *__restrict__ basis) {
+                                                   const float *__restrict__ pc, const V4<T> *__restrict__ basis,
+                                                   const V4<T> *__restrict__ add) {
     __shared__ double sh[32];
     if constexpr (sizeof(T) == 4) {
         __shared__ V4<float> tab_s[PSE_TABLEC_N];
         for (int i = threadIdx.x; i < PSE_TABLEC_N; i += blockDim.x) tab_s[i] = table_c[i];
         __syncthreads();
-        lz_matvec_body<T, TPP, ILP, true>(N, K, g, rec, count, nbr, tab_s, u, partials, lz, pc, basis, blockIdx.x,
-                                          gridDim.x, sh);
+        lz_matvec_body<T, TPP, ILP, true>(N, K, g, rec, count, nbr, tab_s, u, partials, lz, pc, basis, add,
+                                          blockIdx.x, gridDim.x, sh);
     } else {
-        lz_matvec_body<T, TPP, ILP, false>(N, K, g, rec, count, nbr, table, u, partials, lz, pc, basis, blockIdx.x,
-                                           gridDim.x, sh);
+        lz_matvec_body<T, TPP, ILP, false>(N, K, g, rec, count, nbr, table, u, partials, lz, pc, basis, add,
+                                           blockIdx.x, gridDim.x, sh);
     }
 }
 
@@ -305,7 +313,8 @@ __global__ void __launch_bounds__(128) k_lz_matvec_batch(const LzSys *__restrict
     for (int i = threadIdx.x; i < PSE_TABLEC_N; i += blockDim.x) tab_s[i] = S.table_c[i];
     __syncthreads();
     lz_matvec_body<float, PSE_BATCH_MV_TPP, 4, true>(S.N, S.K, S.g, S.rec, S.count, S.nbr, tab_s, S.u, S.part_mv,
-                                                     S.lz, S.pc, S.basis, blockIdx.x - S.blk_mv, S.nblk_mv, sh);
+                                                     S.lz, S.pc, S.basis, nullptr, blockIdx.x - S.blk_mv, S.nblk_mv,
+                                                     sh);
 }
 
 template <typename T>
@@ -771,7 +780,7 @@ void matvec_prepare() {
 template <typename T, int TPP, int ILP> void mv_launch(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
     k_lz_matvec<T, TPP, ILP><<<pgrid(N, 128 / TPP, mv_blocks_per_sm<T, TPP, ILP>()), 128, 0, s>>>(
         N, nbr_k(N, d.nbr_cap), g, d.rec, d.nbr_count, d.nbr, d.table, d.table_c, d.u, d.partials, d.lz,
-        sizeof(T) == 4 ? d.pc_on : nullptr, d.basis);
+        sizeof(T) == 4 ? d.pc_on : nullptr, d.basis, d.mv_add);
 }
 template <typename T> void launch_lz_matvec(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
     switch (g.mv) {

@@ -213,8 +213,16 @@ __device__ __forceinline__ void support(float x, const WaveGeom<float> &w, int &
     const float th = hi - 0.5f * (float)w.P;  // exact: P/2 lies on the ulp grid of hi
     float fl = floorf(th);
     float rem = (th - fl) + lo;
-    if (rem < 0.f) { fl -= 1.f; rem += 1.f; }
-    if (rem >= 1.f) { fl += 1.f; rem -= 1.f; }
+    // rem = s - P/2 - fl to float rounding; its sign decides the floor.  A
+    // tiny negative rem moves the support down one node, and rem + 1 may
+    // round to 1: keep it just below 1 so that it does not move back.
+    if (rem < 0.f) {
+        fl -= 1.f;
+        rem = fminf(rem + 1.f, 0.99999994f);
+    } else if (rem >= 1.f) {
+        fl += 1.f;
+        rem -= 1.f;
+    }
     i0 = (int)fl + 1;
     u = rem + 0.5f * (float)w.P - 1.f;
 }
@@ -224,8 +232,13 @@ __device__ __forceinline__ void support(double x, const WaveGeom<double> &w, int
     const double th = hi - 0.5 * w.P;
     double fl = floor(th);
     double rem = (th - fl) + lo;
-    if (rem < 0.0) { fl -= 1.0; rem += 1.0; }
-    if (rem >= 1.0) { fl += 1.0; rem -= 1.0; }
+    if (rem < 0.0) {  // as in the float form: a tiny negative rem must not round back to 1
+        fl -= 1.0;
+        rem = fmin(rem + 1.0, 0.99999999999999989);
+    } else if (rem >= 1.0) {
+        fl += 1.0;
+        rem -= 1.0;
+    }
     i0 = (int)fl + 1;
     u = rem + 0.5 * w.P - 1.0;
 }
@@ -271,7 +284,8 @@ template <typename T> __device__ __forceinline__ int64_t caller_of(T w) {
 template <typename T>
 __global__ void __launch_bounds__(PSE_SPREAD_THREADS)
     k_spread(WaveGeom<T> w, Geom<T> g, SpreadTile st, const int *__restrict__ orig, const V4<T> *__restrict__ pos_sorted,
-             const int *__restrict__ cell_start, const SampleArgs<T> *args, T *grid, T *scratch) {
+             const int *__restrict__ cell_start, const SampleArgs<T> *args, T *grid, T *scratch,
+             const Rec<T> *__restrict__ src) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int E = st.E, E2 = E * E, E3 = E2 * E, P = w.P, CP = st.CP, G = st.G, M = w.M;
     const int64_t M3 = (int64_t)M * M * M;
@@ -330,8 +344,8 @@ __global__ void __launch_bounds__(PSE_SPREAD_THREADS)
                     if (coff[mid] <= k) lo = mid;
                     else hi = mid - 1;
                 }
-                const V4<T> p = pos_sorted[cst[lo] + (k - coff[lo])];
-                const T *F = args->vin + 3 * caller_of(p.w);
+                const int64_t si = cst[lo] + (k - coff[lo]);
+                const V4<T> p = pos_sorted[si];
                 int i0x, i0y, i0z;
                 T ux, uy, uz;
                 support(p.x, w, i0x, ux);
@@ -345,7 +359,13 @@ __global__ void __launch_bounds__(PSE_SPREAD_THREADS)
                     wv[2 * P + q] = exp_t(-w.ch2 * dz * dz);
                 }
                 T *f = fv + threadIdx.x * 3;
-                f[0] = F[0]; f[1] = F[1]; f[2] = F[2];
+                if (src) {  // a sorted-order vector (the Lanczos vector of the full-mobility iteration)
+                    const V4<T> q = src[si].q;
+                    f[0] = q.x; f[1] = q.y; f[2] = q.z;
+                } else {
+                    const T *F = args->vin + 3 * caller_of(p.w);
+                    f[0] = F[0]; f[1] = F[1]; f[2] = F[2];
+                }
                 const int lx = i0x - ox, ly = i0y - oy, lz = i0z - oz;
                 const bool inside = lx >= 0 && ly >= 0 && lz >= 0 && lx + P <= E && ly + P <= E && lz + P <= E;
                 base[threadIdx.x] = inside ? (lx * E + ly) * E + lz : -1;
@@ -746,12 +766,13 @@ template <typename T> cudaError_t spread_prepare(size_t *max_dynamic) {
 // with atomics.
 template <typename T>
 cudaError_t launch_spread(WaveGeom<T> w, Geom<T> g, SpreadTile st, const int *orig, const int2 *cover,
-                          const int *cover_cnt, T *scratch, const Dev<T> &d, cudaStream_t s) {
+                          const int *cover_cnt, T *scratch, const Dev<T> &d, cudaStream_t s,
+                          const Rec<T> *src) {
     const size_t smem = spread_smem_bytes(st, w.P, sizeof(T));
     const unsigned tiles = (unsigned)st.ntx * st.ntx * st.ntx;
     const bool two_phase = scratch && cover && cover_cnt;
     k_spread<T><<<tiles, PSE_SPREAD_THREADS, smem, s>>>(w, g, st, orig, d.pos_sorted, d.cell_start, d.args, d.grid,
-                                                         two_phase ? scratch : nullptr);
+                                                         two_phase ? scratch : nullptr, src);
     if (two_phase) {
         const int64_t M3 = (int64_t)w.M * w.M * w.M;
         k_spread_gather<T><<<nbw(M3, 256), 256, 0, s>>>(w.M, st.E, st.ntx, cover, cover_cnt, scratch, d.grid);
@@ -1039,7 +1060,7 @@ void launch_fused_fft(const WaveGeom<float> &w, const SampleArgs<float> *args, i
     template void launch_wave_apply<T>(WaveGeom<T>, const SampleArgs<T> *, int, void *, int, int, cudaStream_t); \
     template void launch_grid_noise<T>(WaveGeom<T>, const SampleArgs<T> *, int, T *, cudaStream_t);   \
     template cudaError_t launch_spread<T>(WaveGeom<T>, Geom<T>, SpreadTile, const int *, const int2 *, const int *, \
-                                          T *, const Dev<T> &, cudaStream_t);                                      \
+                                          T *, const Dev<T> &, cudaStream_t, const Rec<T> *);                                      \
     template cudaError_t spread_prepare<T>(size_t *);
 PSE_INST(float)
 PSE_INST(double)

@@ -132,6 +132,9 @@ extern "C" pse_status pse_real_matvec_noalloc(double L, double a, double xi, dou
     g.xi = (float)plan.xi;
     g.nc = plan.ncell;
     g.nb = bricks_per_side(plan.ncell);
+    g.rc2_d = plan.r_cut * plan.r_cut;
+    g.L_d = plan.L;
+    g.invL_d = 1.0 / plan.L;
 
     Dev<float> d{};
     d.pos_sorted = sc->pos_sorted;

@@ -41,9 +41,9 @@ struct pse_ctx {
     bool fft_made = false;
     cudaStream_t s_main = nullptr, s_wave = nullptr, s_body = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};  // fork of the wave branch; its join
-    cudaGraph_t graph[5] = {};            // per graph mode (GM_*)
-    cudaGraphExec_t exec[5] = {};
-    cudaGraphConditionalHandle cond[5] = {};
+    cudaGraph_t graph[6] = {};            // per graph mode (GM_*)
+    cudaGraphExec_t exec[6] = {};
+    cudaGraphConditionalHandle cond[6] = {};
     cufftHandle fft_r2c = 0;                            // forward FFT (spreading / grid noise)
     bool r2c_made = false;
     bool fused_fft = false;                             // sample path: our noise + C2R kernels (FP32, M = 2^k)
@@ -155,8 +155,10 @@ void free_list(std::vector<void *> &list) {
 
 // Graph modes: a plain sample; the forces path with and without noise; a
 // Brownian step (overlap forces computed in the graph, positions advanced)
-// with and without noise.
-enum { GM_SAMPLE = 0, GM_FORCES_NOISE = 1, GM_FORCES = 2, GM_BD_NOISE = 3, GM_BD = 4, GM_COUNT = 5 };
+// with and without noise; Lanczos on the whole mobility (the comparison
+// method of Sec. IV).
+enum { GM_SAMPLE = 0, GM_FORCES_NOISE = 1, GM_FORCES = 2, GM_BD_NOISE = 3, GM_BD = 4, GM_FULL = 5, GM_COUNT = 6 };
+static_assert(GM_COUNT == sizeof(pse_ctx::exec) / sizeof(cudaGraphExec_t), "graph mode table size");
 static inline bool gm_noise(int m) { return m == GM_SAMPLE || m == GM_FORCES_NOISE || m == GM_BD_NOISE; }
 static inline bool gm_bd(int m) { return m == GM_BD_NOISE || m == GM_BD; }
 
@@ -215,6 +217,9 @@ template <typename T> void fill_geom(pse_ctx *c) {
     g.nc = p.ncell;
     g.nb = bricks_per_side(p.ncell);
     g.mv = c->params.matvec_shape > 0 ? c->params.matvec_shape - 1 : 0;
+    g.rc2_d = p.r_cut * p.r_cut;
+    g.L_d = p.L;
+    g.invL_d = 1.0 / p.L;
     geom<T>(c) = g;
     WaveGeom<T> w{};
     w.M = p.M;
@@ -430,11 +435,12 @@ template <typename T> pse_status set_spread_tile(pse_ctx *c, const SpreadTile &t
     return PSE_OK;
 }
 
-template <typename T> cudaError_t run_spread(pse_ctx *c, const SpreadTile &t, cudaStream_t s) {
+template <typename T>
+cudaError_t run_spread(pse_ctx *c, const SpreadTile &t, cudaStream_t s, const Rec<T> *src = nullptr) {
     Dev<T> &d = dev<T>(c);
     const bool tp = c->sp_two_phase;
     return launch_spread<T>(wgeom<T>(c), geom<T>(c), t, c->sp_orig, tp ? c->sp_cover : nullptr,
-                            tp ? c->sp_cnt : nullptr, tp ? (T *)c->sp_scratch : nullptr, d, s);
+                            tp ? c->sp_cnt : nullptr, tp ? (T *)c->sp_scratch : nullptr, d, s, src);
 }
 
 // Default: the largest tile that holds all three components, else the
@@ -666,10 +672,72 @@ template <typename T> pse_status capture_sample(pse_ctx *c, int mode) {
     return e == cudaSuccess ? PSE_OK : PSE_ECUDA;
 }
 
+// One step of Lanczos on the whole mobility M = M_r + M_w (Sec. IV's
+// comparison method), on `s`: the wave product of the current vector q_j
+// (spread from the matvec records, forward FFT, the deterministic mode
+// factor of Sec. III, inverse FFT, interpolation into uwave), then the
+// near-field matvec with uwave added to its rows (so alpha_j = q_j . M q_j),
+// the three-term update and the eigen-solve with the stop test.
+template <typename T> pse_status full_step(pse_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h) {
+    const int64_t N = c->N;
+    Dev<T> &d = dev<T>(c);
+    const WaveGeom<T> &w = wgeom<T>(c);
+    const int64_t M3 = (int64_t)w.M * w.M * w.M;
+    const double ltol = c->params.lanczos_tol > 0 ? c->params.lanczos_tol : c->plan.tol;
+    CK(cudaMemsetAsync(d.grid, 0, sizeof(T) * 3 * M3, s));
+    CK(run_spread<T>(c, c->spread, s, d.rec));
+    CKF(cufftSetStream(c->fft_r2c, s));
+    if constexpr (sizeof(T) == 4) {
+        CKF(cufftExecR2C(c->fft_r2c, (cufftReal *)d.grid, (cufftComplex *)d.spec));
+    } else {
+        CKF(cufftExecD2Z(c->fft_r2c, (cufftDoubleReal *)d.grid, (cufftDoubleComplex *)d.spec));
+    }
+    launch_wave_apply<T>(w, d.args, c->params.system, d.spec, WAVE_MODE_DET, 0, s);
+    CKF(cufftSetStream(c->fft, s));
+    if constexpr (sizeof(T) == 4) {
+        CKF(cufftExecC2R(c->fft, (cufftComplex *)d.spec, (cufftReal *)d.grid));
+    } else {
+        CKF(cufftExecZ2D(c->fft, (cufftDoubleComplex *)d.spec, (cufftDoubleReal *)d.grid));
+    }
+    interp<T>(c, N, s);
+    Dev<T> da = d;
+    da.mv_add = d.uwave;
+    launch_lz_matvec<T>(N, geom<T>(c), da, s);
+    launch_lz_update<T>(N, c->max_iter, d, s);
+    launch_lz_eig(d.lz, c->max_iter, c->params.fixed_iter, ltol, h, s);
+    return PSE_OK;
+}
+
+// The full-mobility sample on c->s_main (capturing): cell and neighbour
+// lists, q_1 = z1, a WHILE node whose body is one full_step, and the final
+// combination x = ||z1|| V_J T_J^{1/2} e_1 in caller order.
+template <typename T> pse_status capture_full(pse_ctx *c) {
+    const int64_t N = c->N;
+    Dev<T> &d = dev<T>(c);
+    cudaStream_t s = c->s_main;
+    pre<T>(c, N, s);
+    launch_nbr<T>(N, geom<T>(c), d, s);
+    launch_lz_init<T>(N, d.args, c->params.system, d, s);
+    cudaGraph_t body = nullptr;
+    pse_status st = PSE_OK;
+    cudaError_t e = add_while(s, &c->cond[GM_FULL], &body);
+    if (e == cudaSuccess) {
+        e = cudaStreamBeginCaptureToGraph(c->s_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            st = full_step<T>(c, c->s_body, c->cond[GM_FULL]);
+            cudaGraph_t body_out = nullptr;
+            e = cudaStreamEndCapture(c->s_body, &body_out);
+        }
+    }
+    launch_lz_final<T>(N, d.args, d, false, s);
+    if (st != PSE_OK) return st;
+    return e == cudaSuccess ? PSE_OK : PSE_ECUDA;
+}
+
 template <typename T> pse_status build_graph(pse_ctx *c, int mode) {
     cudaStream_t s = c->s_main;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    const pse_status st = capture_sample<T>(c, mode);
+    const pse_status st = mode == GM_FULL ? capture_full<T>(c) : capture_sample<T>(c, mode);
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
     if (st != PSE_OK || e2 != cudaSuccess) {
@@ -719,6 +787,26 @@ template <typename T> pse_status run_plain(pse_ctx *c, cudaStream_t s, int mode)
     if (mode == GM_SAMPLE) launch_lz_final<T>(N, d.args, d, true, s);
     else launch_lz_final_forces<T>(N, d.args, d, s);
     if (gm_bd(mode)) launch_advance<T>(N, geom<T>(c), d, s);
+    return PSE_OK;
+}
+
+// The full-mobility sample with plain launches and a host-side loop (one
+// synchronisation per iteration): use_graph = -1.
+template <typename T> pse_status run_full_plain(pse_ctx *c, cudaStream_t s) {
+    const int64_t N = c->N;
+    Dev<T> &d = dev<T>(c);
+    pre<T>(c, N, s);
+    launch_nbr<T>(N, geom<T>(c), d, s);
+    launch_lz_init<T>(N, d.args, c->params.system, d, s);
+    for (int it = 0; it < c->max_iter + 2; ++it) {
+        const pse_status st = full_step<T>(c, s, 0);
+        if (st != PSE_OK) return st;
+        int cont = 0;
+        CK(cudaMemcpyAsync(&cont, &d.lz->cont, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (!cont) break;
+    }
+    launch_lz_final<T>(N, d.args, d, false, s);
     return PSE_OK;
 }
 
@@ -796,6 +884,39 @@ pse_status sample_impl(pse_ctx *c, int64_t N, const T *pos, uint64_t seed, uint6
         CK(cudaGraphLaunch(c->exec[GM_SAMPLE], s));
     } else {
         st = run_plain<T>(c, s, GM_SAMPLE);
+        if (st != PSE_OK) return st;
+    }
+    c->last_stream = s;
+    CK(cudaGetLastError());
+    return PSE_OK;
+}
+
+template <typename T>
+pse_status full_impl(pse_ctx *c, int64_t N, const T *pos, uint64_t seed, uint64_t sample, T *out, cudaStream_t s) {
+    if (!pos || !out || N < 1) return PSE_EINVAL;
+    if (c->pc_enabled) return PSE_ENOTSUPPORTED;  // the comparison method runs on M itself
+    DeviceGuard guard(c->device);
+    pse_status st = ensure<T>(c, N);
+    if (st != PSE_OK) return st;
+    if ((st = ensure_r2c<T>(c)) != PSE_OK) return st;
+    if ((st = choose_spread<T>(c)) != PSE_OK) return st;
+    SampleArgs<T> a{};
+    a.pos = pos;
+    a.out = out;
+    a.seed = seed;
+    a.sample = sample;
+    a.c_det = 1.0;  // the mode factor of the wave product, unscaled
+    a.c_noise = 0.0;
+    CK(push_args(c, dev<T>(c).args, &a, sizeof(a), s));
+    const bool use_graph = c->params.use_graph >= 0;
+    if (use_graph && !c->exec[GM_FULL]) {
+        st = build_graph<T>(c, GM_FULL);
+        if (st != PSE_OK) return st;
+    }
+    if (use_graph) {
+        CK(cudaGraphLaunch(c->exec[GM_FULL], s));
+    } else {
+        st = run_full_plain<T>(c, s);
         if (st != PSE_OK) return st;
     }
     c->last_stream = s;
@@ -1160,6 +1281,18 @@ pse_status pse_bd_step_f64(pse_ctx *c, int64_t N, double *d_pos, const double *d
                            double k_rep, uint64_t seed, uint64_t step, void *stream) {
     if (!c || c->plan.precision != PSE_FP64) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
     return bd_impl<double>(c, N, d_pos, d_fext, dt, kT, k_rep, seed, step, (cudaStream_t)stream);
+}
+
+pse_status pse_sample_full_lanczos(pse_ctx *c, int64_t N, const float *d_pos, uint64_t seed, uint64_t sample_index,
+                                   float *d_out, void *stream) {
+    if (!c || c->plan.precision != PSE_FP32) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
+    return full_impl<float>(c, N, d_pos, seed, sample_index, d_out, (cudaStream_t)stream);
+}
+
+pse_status pse_sample_full_lanczos_f64(pse_ctx *c, int64_t N, const double *d_pos, uint64_t seed,
+                                       uint64_t sample_index, double *d_out, void *stream) {
+    if (!c || c->plan.precision != PSE_FP64) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
+    return full_impl<double>(c, N, d_pos, seed, sample_index, d_out, (cudaStream_t)stream);
 }
 
 pse_status pse_mobility_apply(pse_ctx *c, int64_t N, const float *d_pos, const float *d_force, float *d_out,

@@ -68,6 +68,9 @@ template <typename T> struct Geom {
     // compact table: PSE_TABLEC_A uniform knots on [0, tc_split), the rest
     // uniform on [tc_split, r_cut]; tc_split = min(2a, r_cut)
     T tc_split, tc_invA, tc_invB;
+    // float64 r_cut^2 and box side: a pair whose float32 distance lies within
+    // rounding of r_cut is decided again in float64 from the positions
+    double rc2_d, L_d, invL_d;
 };
 #define PSE_MV_VARIANTS 4
 
@@ -316,6 +319,8 @@ template <typename T> struct Dev {
     const float *pc_on;  // == pc while the learned preconditioner is active, else null
     float *pc_theta;     // network parameters (PSE_PRECOND_NPARAM)
     V4<T> *u;            // matvec output
+    const V4<T> *mv_add; // added to every Lanczos matvec row (the wave product of the
+                         // full-mobility Lanczos), or null
     V4<T> *uwave;        // wave part at sorted particles
     V4<T> *udet;         // M_r F at sorted particles (forces path)
     T *bd_force;         // 3N, caller order: forces of a Brownian step
@@ -441,9 +446,12 @@ template <typename T>
 void launch_grid_noise(WaveGeom<T> w, const SampleArgs<T> *args, int system, T *grid, cudaStream_t s);
 size_t spread_smem_bytes(SpreadTile st, int P, size_t elem);
 #define PSE_COVER 8  // tile blocks that may cover one grid node along one axis
+// src: the vector to spread in sorted order (its q field), or null for the
+// caller-order forces args->vin
 template <typename T>
 cudaError_t launch_spread(WaveGeom<T> w, Geom<T> g, SpreadTile st, const int *orig, const int2 *cover,
-                          const int *cover_cnt, T *scratch, const Dev<T> &d, cudaStream_t s);
+                          const int *cover_cnt, T *scratch, const Dev<T> &d, cudaStream_t s,
+                          const Rec<T> *src = nullptr);
 template <typename T> cudaError_t spread_prepare(size_t *max_dynamic);
 template <typename T> void launch_matvec_sorted(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s);
 template <typename T> void launch_gather_vec(int64_t N, const SampleArgs<T> *args, const Dev<T> &d, cudaStream_t s);

@@ -23,6 +23,10 @@ def _maxrel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
 def _grid_fits(L, xi, M, tol=1e-3):
     from paper_1611_09322_gb300 import PseError, pse_plan
     try:

@@ -156,3 +156,27 @@ def test_bd_step_without_noise_is_the_mobility_product():
     assert j == 0
     assert np.allclose(dx, 1e-3 * pse.mobility_apply(F, pos, plan), rtol=1e-12, atol=1e-16)
     assert np.allclose(new, np.mod(pos + dx, L))
+
+
+def test_full_mobility_lanczos_converges_to_the_square_root_of_the_gridded_mobility():
+    """The full-mobility Lanczos of Sec. IV: with a tight stop rule its result
+    is A^{1/2} z for the matrix A of the M F product it applies (built column
+    by column from unit forces, symmetric and positive definite), computed by
+    a dense eigendecomposition; and A itself is the dense Ewald-summed RPY
+    mobility to within the method's tolerance (20 tol of the Stokes scale
+    1/(6 pi a), eq. Mwave + eq. Mreal)."""
+    N = 40
+    pos, L = _hs(N, 0.1, 21)
+    plan = ewald.plan(L, 1.0, 0.5, 1e-3)
+    A = np.stack([pse.mobility_apply(e.reshape(N, 3), pos, plan).ravel() for e in np.eye(3 * N)], axis=1)
+    assert np.abs(A - A.T).max() < 1e-12 * np.abs(A).max()
+    lam, Q = np.linalg.eigh(0.5 * (A + A.T))
+    assert lam.min() > 0
+    z = pse.real_noise(N, 3, 4).ravel()
+    exact = Q @ (np.sqrt(lam) * (Q.T @ z))
+    x, j, _ = pse.full_sample(pos, plan, 3, 4, lanczos_tol=1e-11)
+    assert np.linalg.norm(x.ravel() - exact) < 1e-8 * np.linalg.norm(exact)
+    x4, j4, _ = pse.full_sample(pos, plan, 3, 4, n_iter=4)
+    assert j4 == 4 and np.linalg.norm(x4.ravel() - exact) > 1e-6 * np.linalg.norm(exact)
+    Md, _, _ = ewald.mobility_dense(pos, L, 1.0, 0.5, tol=1e-12)
+    assert np.abs(A - Md).max() * 6 * math.pi < 20 * 1e-3
