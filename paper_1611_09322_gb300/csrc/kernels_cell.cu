@@ -121,94 +121,156 @@ __global__ void k_cellsort(int ncell3, const int *start, V4<T> *pos_sorted, V4<T
 // right one.  Lists longer than K are cut and flag an overflow.
 // A float32 pair distance within rounding of r_cut (|r^2 - r_cut^2| below
 // 4e-6 r_cut^2, a few ulps of the cell-offset arithmetic) does not decide
-// the pair: it is decided again in float64 from the wrapped positions with
-// the nearest periodic image, so the truncation of eq. Mreal keeps exactly
-// the pairs with r < r_cut in float64, whatever rounding the float path saw.
-__device__ __forceinline__ bool pair_inside_f64(const V4<float> *__restrict__ pos, int64_t s, int t, double L,
-                                                double invL, double rc2) {
-    const V4<float> a = pos[s], b = pos[t];
-    double dx = (double)a.x - (double)b.x, dy = (double)a.y - (double)b.y, dz = (double)a.z - (double)b.z;
-    dx -= L * rint(dx * invL);
-    dy -= L * rint(dy * invL);
-    dz -= L * rint(dz * invL);
-    return dx * dx + dy * dy + dz * dz < rc2;
-}
-
-template <typename T>
-__device__ __forceinline__ int nbr_elem(int64_t s, int64_t N, const Geom<T> &g, const V4<T> *__restrict__ loc,
-                                        const V4<T> *__restrict__ pos, const int *__restrict__ cell_start,
-                                        int *count, int *nbr, int K, int *overflow) {
+// the pair.  The search only notes that a particle met one; such particles
+// (a few per 10^5) walk their cells a second time, off the main loop, and
+// record each pair in that band (s, t, code, list slot or -1) in a small
+// edge buffer; k_nbr_edges then decides it again in float64 from the wrapped
+// positions with the nearest periodic image, removing the entry (set to -1,
+// which every list reader skips) or appending it.  The lists then hold
+// exactly the pairs with r < r_cut in float64, as the oracle's do.
+//
+// One walk over the 27 stencil cells.  RECORD = false: fill the ELL row and
+// flag a pair in the band; RECORD = true: write nothing but the band's pairs
+// to the edge buffer, with the list slot the first walk gave them.
+template <typename T, bool RECORD>
+__device__ __forceinline__ int nbr_walk(int64_t s, int64_t N, const Geom<T> &g, const V4<T> *__restrict__ loc,
+                                        const int *__restrict__ cell_start, int *nbr, int K, bool &band,
+                                        int4 *edge, int *edge_n, int edge_cap) {
     int cnt = 0;
-    {
-        const V4<T> li = loc[s];
-        const int c = (int)w_bits(li.w);
-        const int nc = g.nc;
-        int cx, cy, cz;
-        cell_xyz(c, g.nb, cx, cy, cz);
-        int *dst = nbr + s;  // ELL column cnt of row s
-        for (int ox = -1; ox <= 1; ++ox) {
-            int ax = cx + ox;
-            ax += ax < 0 ? nc : 0;
-            ax -= ax >= nc ? nc : 0;
-            const T sx = T(ox) * g.cs + T(ox) * g.cs_lo;
-            for (int oy = -1; oy <= 1; ++oy) {
-                int ay = cy + oy;
-                ay += ay < 0 ? nc : 0;
-                ay -= ay >= nc ? nc : 0;
-                const T sy = T(oy) * g.cs + T(oy) * g.cs_lo;
-                for (int oz = -1; oz <= 1; ++oz) {
-                    int az = cz + oz;
-                    az += az < 0 ? nc : 0;
-                    az -= az >= nc ? nc : 0;
-                    const T sz = T(oz) * g.cs + T(oz) * g.cs_lo;
-                    const int code = ((ox + 1) << 4) | ((oy + 1) << 2) | (oz + 1);
-                    const int c2 = cell_id(ax, ay, az, g.nb);
-                    const int b = cell_start[c2], e = cell_start[c2 + 1];
-                    const int self = code == 21 ? (int)s : -1;  // the particle itself, in its own cell
-                    for (int t = b; t < e; ++t) {
-                        if (t == self) continue;
-                        const V4<T> lt = loc[t];
-                        const T dx = (li.x - lt.x) - sx;
-                        const T dy = (li.y - lt.y) - sy;
-                        const T dz = (li.z - lt.z) - sz;
-                        const T r2 = dx * dx + dy * dy + dz * dz;
-                        bool in = r2 < g.rc2;
-                        if constexpr (sizeof(T) == 4) {
-                            if (fabsf(r2 - g.rc2) <= 4e-6f * g.rc2)
-                                in = pair_inside_f64(pos, s, t, g.L_d, g.invL_d, g.rc2_d);
-                        }
-                        if (in) {
-                            if (cnt < K) {
+    const V4<T> li = loc[s];
+    const int c = (int)w_bits(li.w);
+    const int nc = g.nc;
+    int cx, cy, cz;
+    cell_xyz(c, g.nb, cx, cy, cz);
+    int *dst = nbr + s;  // ELL column cnt of row s
+    for (int ox = -1; ox <= 1; ++ox) {
+        int ax = cx + ox;
+        ax += ax < 0 ? nc : 0;
+        ax -= ax >= nc ? nc : 0;
+        const T sx = T(ox) * g.cs + T(ox) * g.cs_lo;
+        for (int oy = -1; oy <= 1; ++oy) {
+            int ay = cy + oy;
+            ay += ay < 0 ? nc : 0;
+            ay -= ay >= nc ? nc : 0;
+            const T sy = T(oy) * g.cs + T(oy) * g.cs_lo;
+            for (int oz = -1; oz <= 1; ++oz) {
+                int az = cz + oz;
+                az += az < 0 ? nc : 0;
+                az -= az >= nc ? nc : 0;
+                const T sz = T(oz) * g.cs + T(oz) * g.cs_lo;
+                const int code = ((ox + 1) << 4) | ((oy + 1) << 2) | (oz + 1);
+                const int c2 = cell_id(ax, ay, az, g.nb);
+                const int b = cell_start[c2], e = cell_start[c2 + 1];
+                const int self = code == 21 ? (int)s : -1;  // the particle itself, in its own cell
+                for (int t = b; t < e; ++t) {
+                    if (t == self) continue;
+                    const V4<T> lt = loc[t];
+                    const T dx = (li.x - lt.x) - sx;
+                    const T dy = (li.y - lt.y) - sy;
+                    const T dz = (li.z - lt.z) - sz;
+                    const T r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 < g.rc2_hi) {
+                        const bool in = r2 < g.rc2;
+                        if constexpr (RECORD) {
+                            if (r2 >= g.rc2_lo) {
+                                const int k = atomicAdd(edge_n, 1);
+                                if (k < edge_cap)
+                                    edge[k] = make_int4((int)s, t, code, in ? (cnt < K ? cnt : -2) : -1);
+                            }
+                        } else {
+                            band |= r2 >= g.rc2_lo;
+                            if (in && cnt < K) {
                                 *dst = (t << 6) | code;
                                 dst += N;
                             }
-                            ++cnt;
                         }
+                        cnt += in;
                     }
                 }
             }
         }
-        if (cnt > K) {
-            atomicExch(overflow, 1);
-            cnt = K;
-        }
-        count[s] = cnt;
     }
     return cnt;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_nbr(int64_t N, Geom<T> g, const V4<T> *__restrict__ loc,
-                                             const V4<T> *__restrict__ pos, const int *__restrict__ cell_start,
-                                             int *count, int *nbr, int K, int *overflow,
-                                             unsigned long long *n_pairs) {
+__device__ __forceinline__ int nbr_elem(int64_t s, int64_t N, const Geom<T> &g, const V4<T> *__restrict__ loc,
+                                        const int *__restrict__ cell_start, int *count, int *nbr, int K,
+                                        int *overflow, int4 *edge, int *edge_n, int edge_cap) {
+    bool band = false;
+    int cnt = nbr_walk<T, false>(s, N, g, loc, cell_start, nbr, K, band, edge, edge_n, edge_cap);
+    if constexpr (sizeof(T) == 4) {
+        if (band) nbr_walk<T, true>(s, N, g, loc, cell_start, nbr, K, band, edge, edge_n, edge_cap);
+    }
+    if (cnt > K) {
+        atomicExch(overflow, 1);
+        cnt = K;
+    }
+    count[s] = cnt;
+    return cnt;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128, 12) k_nbr(int64_t N, Geom<T> g, const V4<T> *__restrict__ loc,
+                                             const int *__restrict__ cell_start, int *count, int *nbr, int K,
+                                             int *overflow, unsigned long long *n_pairs, int4 *edge, int *edge_n,
+                                             int edge_cap) {
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int cnt = s < N ? nbr_elem<T>(s, N, g, loc, pos, cell_start, count, nbr, K, overflow) : 0;
+    const int cnt = s < N ? nbr_elem<T>(s, N, g, loc, cell_start, count, nbr, K, overflow, edge, edge_n, edge_cap)
+                          : 0;
     // pair total for the statistics: one atomic per warp
     int tot = cnt;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
     if ((threadIdx.x & 31) == 0 && tot) atomicAdd(n_pairs, (unsigned long long)tot);
+}
+
+// The float64 decision for the pairs k_nbr recorded within rounding of
+// r_cut (one block; a few per 10^5 particles).  Entry (s, t, code, slot):
+// slot >= 0 the float search stored the pair there, -2 it accepted it with a
+// full list, -1 it rejected it.  Clears the edge count for the next search.
+__device__ __forceinline__ bool pair_inside_f64(const V4<float> &a, const V4<float> &b, const Geom<float> &g) {
+    double dx = (double)a.x - (double)b.x, dy = (double)a.y - (double)b.y, dz = (double)a.z - (double)b.z;
+    dx -= g.L_d * rint(dx * g.invL_d);
+    dy -= g.L_d * rint(dy * g.invL_d);
+    dz -= g.L_d * rint(dz * g.invL_d);
+    return dx * dx + dy * dy + dz * dz < g.rc2_d;
+}
+
+__device__ __forceinline__ void nbr_edges_body(int64_t N, const Geom<float> &g, const V4<float> *__restrict__ pos,
+                                               int *count, int *nbr, int K, int *overflow,
+                                               unsigned long long *n_pairs, const int4 *edge, int *edge_n,
+                                               int edge_cap) {
+    const int n = min(*edge_n, edge_cap);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int4 e = edge[i];
+        const int64_t s = e.x;
+        const bool in32 = e.w != -1, in64 = pair_inside_f64(pos[s], pos[e.y], g);
+        if (in32 && !in64) {
+            if (e.w >= 0) {
+                nbr[(int64_t)e.w * N + s] = -1;
+                atomicAdd(n_pairs, ~0ull);  // - 1
+            }
+        } else if (!in32 && in64) {
+            const int k = atomicAdd(count + s, 1);
+            if (k < K) {
+                nbr[(int64_t)k * N + s] = (e.y << 6) | e.z;
+                atomicAdd(n_pairs, 1ull);
+            } else {
+                atomicSub(count + s, 1);
+                atomicExch(overflow, 1);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *edge_n = 0;
+}
+
+__global__ void __launch_bounds__(256) k_nbr_edges(int64_t N, Geom<float> g, const V4<float> *__restrict__ pos,
+                                                   int *count, int *nbr, int K, int *overflow,
+                                                   unsigned long long *n_pairs, const int4 *edge, int *edge_n,
+                                                   int edge_cap) {
+    nbr_edges_body(N, g, pos, count, nbr, K, overflow, n_pairs, edge, edge_n, edge_cap);
 }
 
 // ------------------------------------------------------------------ fused multi-system kernels
@@ -281,8 +343,9 @@ __global__ void __launch_bounds__(128, 8) k_nbr_batch(const BSys *__restrict__ s
     PSE_BATCH_SYS(BK_NBR);
     for (int64_t s0 = lb * (int64_t)blockDim.x; s0 < S.N; s0 += stride) {  // uniform per block
         const int64_t s = s0 + threadIdx.x;
-        const int cnt = s < S.N ? nbr_elem<float>(s, S.N, S.g, S.d.loc_sorted, S.d.pos_sorted, S.d.cell_start,
-                                                   S.d.nbr_count, S.d.nbr, S.K, &S.d.lz->overflow)
+        const int cnt = s < S.N ? nbr_elem<float>(s, S.N, S.g, S.d.loc_sorted, S.d.cell_start, S.d.nbr_count,
+                                                   S.d.nbr, S.K, &S.d.lz->overflow, S.d.edge, S.d.edge_n,
+                                                   S.d.edge_cap)
                                 : 0;
         int tot = cnt;
 #pragma unroll
@@ -300,8 +363,16 @@ void launch_batch_prologue_cells(const BSys *sys, int nsys, int *const *tab, con
     k_scatter_batch<<<tab_blocks(nblk, BK_SCATTER), 256, 0, s>>>(sys, tab[BK_SCATTER]);
     k_cellsort_batch<<<tab_blocks(nblk, BK_SORT), 256, 0, s>>>(sys, tab[BK_SORT]);
 }
-void launch_batch_nbr(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s) {
+// one block per system for the float64 decisions at r_cut
+__global__ void __launch_bounds__(256) k_nbr_edges_batch(const BSys *__restrict__ sys) {
+    const BSys &S = sys[blockIdx.x];
+    nbr_edges_body(S.N, S.g, S.d.pos_sorted, S.d.nbr_count, S.d.nbr, S.K, &S.d.lz->overflow, &S.d.lz->n_pairs,
+                   S.d.edge, S.d.edge_n, S.d.edge_cap);
+}
+
+void launch_batch_nbr(const BSys *sys, int nsys, int *const *tab, const int *nblk, cudaStream_t s) {
     k_nbr_batch<<<tab_blocks(nblk, BK_NBR), 128, 0, s>>>(sys, tab[BK_NBR]);
+    k_nbr_edges_batch<<<nsys, 256, 0, s>>>(sys);
 }
 
 // ------------------------------------------------------------------ exclusive scan
@@ -403,8 +474,12 @@ template <typename T> void launch_cellsort(int ncell3, const Dev<T> &d, cudaStre
 }
 
 template <typename T> void launch_nbr(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
-    k_nbr<T><<<nblk(N, 128), 128, 0, s>>>(N, g, d.loc_sorted, d.pos_sorted, d.cell_start, d.nbr_count, d.nbr,
-                                          nbr_k(N, d.nbr_cap), &d.lz->overflow, &d.lz->n_pairs);
+    k_nbr<T><<<nblk(N, 128), 128, 0, s>>>(N, g, d.loc_sorted, d.cell_start, d.nbr_count, d.nbr,
+                                          nbr_k(N, d.nbr_cap), &d.lz->overflow, &d.lz->n_pairs, d.edge, d.edge_n,
+                                          d.edge_cap);
+    if constexpr (sizeof(T) == 4)
+        k_nbr_edges<<<1, 256, 0, s>>>(N, g, d.pos_sorted, d.nbr_count, d.nbr, nbr_k(N, d.nbr_cap), &d.lz->overflow,
+                                      &d.lz->n_pairs, d.edge, d.edge_n, d.edge_cap);
 }
 
 #define PSE_INST(T)                                                                                       \

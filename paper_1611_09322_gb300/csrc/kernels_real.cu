@@ -285,8 +285,10 @@ __device__ __forceinline__ void lz_matvec_body(int64_t N, int K, const Geom<T> &
 // Float contexts stage the compact F, G table (16 KB) in shared memory:
 // table lookups then cost shared-memory wavefronts instead of scattered L1
 // lines.  The FP64 path uses the uniform table (r < 0.2a) and the closed form.
-template <typename T, int TPP, int ILP>
-__global__ void __launch_bounds__(128) k_lz_matvec(int64_t N, int K, Geom<T> g, const Rec<T> *__restrict__ rec,
+// BS threads per block: with large blocks fewer copies of the table share an
+// SM, leaving more of its on-chip memory to the L1 that caches the records.
+template <typename T, int TPP, int ILP, int BS = 128>
+__global__ void __launch_bounds__(BS) k_lz_matvec(int64_t N, int K, Geom<T> g, const Rec<T> *__restrict__ rec,
                                                    const int *__restrict__ count, const int *__restrict__ nbr,
                                                    const V4<T> *__restrict__ table, const V4<T> *__restrict__ table_c,
                                                    V4<T> *u, double *partials, LzState *lz,
@@ -635,6 +637,7 @@ __global__ void k_repulsion(int64_t N, Geom<T> g, const SampleArgs<T> *args, con
     const int cnt = count[s];
     for (int q = 0; q < cnt; ++q) {
         const int e = nbr[(int64_t)q * N + s];
+        if (e < 0) continue;  // a pair removed by the float64 decision at r_cut
         const V4<T> lt = rec[e >> 6].l;
         const int ox = ((e >> 4) & 3) - 1, oy = ((e >> 2) & 3) - 1, oz = (e & 3) - 1;
         const T dx = (li.x - lt.x) - (T(ox) * g.cs + T(ox) * g.cs_lo);
@@ -740,14 +743,14 @@ void launch_lz_init(int64_t N, const SampleArgs<T> *args, int system, const Dev<
 // selected by Geom::mv; the sampler may time them all and keep the fastest.
 // Persistent grid: one wave of resident blocks (at most 16 per SM), so that
 // no second, partly filled wave of equal-work blocks trails the first.
-template <typename T, int TPP, int ILP> int mv_blocks_per_sm() {
+template <typename T, int TPP, int ILP, int BS = 128> int mv_blocks_per_sm() {
     static int per_sm = 0;
     if (per_sm == 0) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lz_matvec<T, TPP, ILP>, 128, 0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lz_matvec<T, TPP, ILP, BS>, BS, 0) != cudaSuccess ||
             nb < 1) {
             cudaGetLastError();
-            nb = 16;
+            nb = BS >= 1024 ? 1 : 2048 / BS;
         }
         per_sm = nb < 16 ? nb : 16;
     }
@@ -769,16 +772,22 @@ template <typename T> int up_blocks_per_sm() {
 }
 int update_blocks_per_sm() { return up_blocks_per_sm<float>(); }
 // occupancy of every matvec shape, queried once outside any stream capture
+template <typename T> void mv_prepare_all() {
+    mv_blocks_per_sm<T, 4, 4>(); mv_blocks_per_sm<T, 8, 2>();
+    mv_blocks_per_sm<T, 16, 1>(); mv_blocks_per_sm<T, 4, 2>();
+    mv_blocks_per_sm<T, 4, 4, 1024>(); mv_blocks_per_sm<T, 4, 4, 512>();
+    mv_blocks_per_sm<T, 8, 2, 1024>(); mv_blocks_per_sm<T, 4, 2, 1024>();
+    mv_blocks_per_sm<T, 1, 4, 1024>(); mv_blocks_per_sm<T, 2, 4, 1024>();
+}
 void matvec_prepare() {
-    mv_blocks_per_sm<float, 4, 4>(); mv_blocks_per_sm<float, 8, 2>();
-    mv_blocks_per_sm<float, 16, 1>(); mv_blocks_per_sm<float, 4, 2>();
-    mv_blocks_per_sm<double, 4, 4>(); mv_blocks_per_sm<double, 8, 2>();
-    mv_blocks_per_sm<double, 16, 1>(); mv_blocks_per_sm<double, 4, 2>();
+    mv_prepare_all<float>();
+    mv_prepare_all<double>();
     up_blocks_per_sm<float>(); up_blocks_per_sm<double>();
 }
 
-template <typename T, int TPP, int ILP> void mv_launch(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
-    k_lz_matvec<T, TPP, ILP><<<pgrid(N, 128 / TPP, mv_blocks_per_sm<T, TPP, ILP>()), 128, 0, s>>>(
+template <typename T, int TPP, int ILP, int BS = 128>
+void mv_launch(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
+    k_lz_matvec<T, TPP, ILP, BS><<<pgrid(N, BS / TPP, mv_blocks_per_sm<T, TPP, ILP, BS>()), BS, 0, s>>>(
         N, nbr_k(N, d.nbr_cap), g, d.rec, d.nbr_count, d.nbr, d.table, d.table_c, d.u, d.partials, d.lz,
         sizeof(T) == 4 ? d.pc_on : nullptr, d.basis, d.mv_add);
 }
@@ -787,6 +796,12 @@ template <typename T> void launch_lz_matvec(int64_t N, Geom<T> g, const Dev<T> &
         case 1: mv_launch<T, 8, 2>(N, g, d, s); break;
         case 2: mv_launch<T, 16, 1>(N, g, d, s); break;
         case 3: mv_launch<T, 4, 2>(N, g, d, s); break;
+        case 4: mv_launch<T, 4, 4, 1024>(N, g, d, s); break;
+        case 5: mv_launch<T, 4, 4, 512>(N, g, d, s); break;
+        case 6: mv_launch<T, 8, 2, 1024>(N, g, d, s); break;
+        case 7: mv_launch<T, 4, 2, 1024>(N, g, d, s); break;
+        case 8: mv_launch<T, 1, 4, 1024>(N, g, d, s); break;
+        case 9: mv_launch<T, 2, 4, 1024>(N, g, d, s); break;
         default: mv_launch<T, 4, 4>(N, g, d, s); break;
     }
 }

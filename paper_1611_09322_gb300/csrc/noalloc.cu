@@ -20,6 +20,7 @@ namespace {
 constexpr int64_t kNoAllocMaxN = 16384;              // particles
 constexpr int64_t kNoAllocMaxCells = 32768;          // cell slots (ncell <= 32)
 constexpr int64_t kNoAllocMaxPairs = kNoAllocMaxN * 160;  // directed neighbour entries
+constexpr int kNoAllocEdges = 4096;                        // pairs decided again in float64 at r_cut
 
 struct NoAllocScratch {
     V4<float> pos_sorted[kNoAllocMaxN];
@@ -33,6 +34,8 @@ struct NoAllocScratch {
     int cell_start[kNoAllocMaxCells + 1];
     int scan_sums[PSE_SCAN_ITEMS];
     int nbr[kNoAllocMaxPairs];
+    int4 edge[kNoAllocEdges];
+    int edge_n;  // zero at load; the float64 decision kernel clears it after each use
     SampleArgs<float> args;
     LzState lz;
 };
@@ -135,6 +138,8 @@ extern "C" pse_status pse_real_matvec_noalloc(double L, double a, double xi, dou
     g.rc2_d = plan.r_cut * plan.r_cut;
     g.L_d = plan.L;
     g.invL_d = 1.0 / plan.L;
+    g.rc2_lo = (float)(g.rc2_d * (1.0 - 4e-6));
+    g.rc2_hi = (float)(g.rc2_d * (1.0 + 4e-6));
 
     Dev<float> d{};
     d.pos_sorted = sc->pos_sorted;
@@ -146,6 +151,9 @@ extern "C" pse_status pse_real_matvec_noalloc(double L, double a, double xi, dou
     d.nbr_count = sc->nbr_count;
     d.nbr = sc->nbr;
     d.nbr_cap = kNoAllocMaxPairs;
+    d.edge = sc->edge;
+    d.edge_n = &sc->edge_n;
+    d.edge_cap = kNoAllocEdges;
     d.scan_sums = sc->scan_sums;
     d.rec = sc->rec;
     d.table = sc->table;

@@ -45,6 +45,7 @@ __device__ void pc_features(int64_t N, int64_t s, const Geom<float> &g, const Re
     const int cnt = count[s];
     for (int k = 0; k < cnt; ++k) {
         const int e = __ldg(nbr + (int64_t)k * N + s);
+        if (e < 0) continue;  // a pair removed by the float64 decision at r_cut
         const int t = e >> 6;
         const int ox = ((e >> 4) & 3) - 1, oy = ((e >> 2) & 3) - 1, oz = (e & 3) - 1;
         const V4<float> lt = rec[t].l;
@@ -186,6 +187,7 @@ __global__ void __launch_bounds__(128) k_pc_targets(int64_t N, Geom<float> g, co
         const int cnt = count[s];
         for (int k = 0; k < cnt; ++k) {
             const int e = nbr[(int64_t)k * N + s];
+            if (e < 0) continue;  // a pair removed by the float64 decision at r_cut
             const int t = e >> 6;
             const int ox = ((e >> 4) & 3) - 1, oy = ((e >> 2) & 3) - 1, oz = (e & 3) - 1;
             const V4<float> lt = rec[t].l;

@@ -216,10 +216,16 @@ template <typename T> void fill_geom(pse_ctx *c) {
     g.xi = (T)p.xi;
     g.nc = p.ncell;
     g.nb = bricks_per_side(p.ncell);
-    g.mv = c->params.matvec_shape > 0 ? c->params.matvec_shape - 1 : 0;
+    // default launch shape: FP32 4 x 4 in blocks of 1024 threads (one copy
+    // of the shared-memory table per SM leaves more of it to the L1: 88 vs
+    // 95 us per matvec at N = 1e6), FP64 4 x 4 in blocks of 128
+    g.mv = c->params.matvec_shape > 0 ? c->params.matvec_shape - 1 : (sizeof(T) == 4 ? 4 : 0);
     g.rc2_d = p.r_cut * p.r_cut;
     g.L_d = p.L;
     g.invL_d = 1.0 / p.L;
+    // the float path's band of float64 decisions at r_cut (none in FP64)
+    g.rc2_lo = sizeof(T) == 4 ? (T)(g.rc2_d * (1.0 - 4e-6)) : g.rc2;
+    g.rc2_hi = sizeof(T) == 4 ? (T)(g.rc2_d * (1.0 + 4e-6)) : g.rc2;
     geom<T>(c) = g;
     WaveGeom<T> w{};
     w.M = p.M;
@@ -478,7 +484,8 @@ template <typename T> pse_status ensure(pse_ctx *c, int64_t N) {
     const pse_plan_info &p = c->plan;
     const int64_t nc3 = cell_slots(p.ncell);
     c->ncell3 = (int)nc3;
-    if (nc3 + 1 > PSE_MAX_SCAN || N + 1 > PSE_MAX_SCAN || N >= (1 << 26)) return PSE_EINVAL;
+    // list entries are (sorted index << 6) | stencil code, non-negative below 2^25 particles
+    if (nc3 + 1 > PSE_MAX_SCAN || N + 1 > PSE_MAX_SCAN || N >= (1 << 25)) return PSE_EINVAL;
     // neighbour capacity: spheres of radius a within r_cut + a, at most a
     // close-packed fraction of that ball, plus slack for small overlaps
     const double rr = p.r_cut / p.a + 1.0;
@@ -497,6 +504,10 @@ template <typename T> pse_status ensure(pse_ctx *c, int64_t N) {
     A(d.cell_start, sizeof(int) * (nc3 + 1));
     A(d.nbr_count, sizeof(int) * N);
     A(d.nbr, sizeof(int) * cap);
+    d.edge_cap = (int)(4096 + N / 128);
+    A(d.edge, sizeof(int4) * d.edge_cap);
+    A(d.edge_n, sizeof(int));
+    CK(cudaMemset(d.edge_n, 0, sizeof(int)));
     A(d.basis, sizeof(V4<T>) * N * (c->max_iter + 2));
     A(d.u, sizeof(V4<T>) * N);
     A(d.rec, sizeof(Rec<T>) * N);
@@ -2073,7 +2084,7 @@ static pse_status batch_prologue(pse_batch *b, cudaStream_t s) {
     }
     launch_batch_interp(b->d_bsys, b->d_btab, b->bnblk, b->p4, b->wave);
     cudaEventRecord(b->ev_wave, b->wave);
-    launch_batch_nbr(b->d_bsys, b->d_btab, b->bnblk, s);
+    launch_batch_nbr(b->d_bsys, (int)b->sys.size(), b->d_btab, b->bnblk, s);
     launch_batch_pc_infer(b->d_bsys, b->d_btab, b->bnblk, s);
     launch_batch_init(b->d_bsys, b->d_btab, b->bnblk, s);
     return st;

@@ -64,15 +64,20 @@ template <typename T> struct Geom {
     T xi;         // splitting parameter
     int nc;       // cells per side
     int nb;       // bricks per side (4x4x4 cells each)
-    int mv;       // matvec launch shape (0: 4 threads x 4 gathers per particle, 1: 8 x 2, 2: 16 x 1, 3: 4 x 2)
+    int mv;       // matvec launch shape: threads x gathers per particle, threads per block
+                  // (0: 4 x 4, 128; 1: 8 x 2, 128; 2: 16 x 1, 128; 3: 4 x 2, 128;
+                  //  4: 4 x 4, 1024; 5: 4 x 4, 512; 6: 8 x 2, 1024; 7: 4 x 2, 1024;
+                  //  8: 1 x 4, 1024; 9: 2 x 4, 1024)
     // compact table: PSE_TABLEC_A uniform knots on [0, tc_split), the rest
     // uniform on [tc_split, r_cut]; tc_split = min(2a, r_cut)
     T tc_split, tc_invA, tc_invB;
-    // float64 r_cut^2 and box side: a pair whose float32 distance lies within
-    // rounding of r_cut is decided again in float64 from the positions
+    // a pair whose float32 r^2 lies in [rc2_lo, rc2_hi) (within rounding of
+    // r_cut^2; both rc2 in the FP64 path) is decided again in float64 from
+    // the positions with the float64 r_cut^2 and box side
+    T rc2_lo, rc2_hi;
     double rc2_d, L_d, invL_d;
 };
-#define PSE_MV_VARIANTS 4
+#define PSE_MV_VARIANTS 10
 
 // Wave-space parameters of one system.
 template <typename T> struct WaveGeom {
@@ -312,6 +317,9 @@ template <typename T> struct Dev {
     int *nbr;            // ELL, column-major: entry k of particle s at nbr[k * N + s],
                          // (t << 6) | stencil code (2 bits per axis, offset + 1)
     int64_t nbr_cap;     // total entries; per-particle capacity = nbr_cap / N
+    int4 *edge;          // pairs found within rounding of r_cut: (s, t, code, slot)
+    int *edge_n;         // their count (cleared by the float64 decision kernel)
+    int edge_cap;
     int *scan_sums;      // PSE_SCAN_ITEMS
     Rec<T> *rec;         // N: cell-local offsets + current q_j (matvec input)
     V4<T> *basis;        // (PSE_MAXIT + 2) * N, q_1 .. q_{J+1}
@@ -405,7 +413,7 @@ struct BSys {
     int b0[PSE_BK], nb[PSE_BK];
 };
 void launch_batch_prologue_cells(const BSys *sys, int nsys, int *const *tab, const int *nblk, cudaStream_t s);
-void launch_batch_nbr(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s);
+void launch_batch_nbr(const BSys *sys, int nsys, int *const *tab, const int *nblk, cudaStream_t s);
 void launch_batch_init(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s);
 void launch_batch_final(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s);
 void launch_batch_noise(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s);
