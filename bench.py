@@ -437,6 +437,31 @@ def variants_full_lanczos(dev, flush, stream, steps, xi, M):
     return out
 
 
+def variants_poly(dev, flush, stream, steps):
+    """Polydisperse suspension (Sec. V's size-dependent shape factor): N = 1e6
+    random non-overlapping spheres of radii 1 and 0.5 (half each) at total
+    volume fraction 0.1, xi a_max = 0.5, tol 1e-3, FFT size tuned; one
+    spectrum and grid per species."""
+    import numpy as np
+    import torch
+    from paper_1611_09322_gb300 import PolySampler, workloads
+    pos, species, L, info = workloads.polydisperse(N_PART, PHI, SEED_POS, (1.0, 0.5))
+    d = torch.from_numpy(pos).to(dev)
+    sp = torch.from_numpy(species.astype(np.int32)).to(dev)
+    o = torch.empty_like(d)
+    s = PolySampler(L, (1.0, 0.5), xi=XI, tol=TOL, autotune=1)
+    for i in range(3):
+        s.sample(d, sp, 1, i, out=o)
+    per = timed_steps(lambda i: s.sample(d, sp, 1, 700 + i, out=o), steps, flush, stream)
+    st = s.stats()
+    out = {"poly_bidisperse_N1e6": {"value": N_PART * steps / (sum(per) / 1e3), "ms_per_step": sum(per) / steps,
+                                    "unit": UNIT, "lanczos_iters": st["lanczos_iters"], "converged": st["converged"],
+                                    "n_pairs": st["n_pairs"], "xi": s.plan["xi"], "M": s.plan["M"], "L": L,
+                                    "workload": "N=1e6 spheres of radii 1 and 0.5 (half each), phi=0.1, tol 1e-3"}}
+    s.close()
+    return out
+
+
 def variants_learned_batched(dev, flush, stream, steps, xi, M):
     """The metric's comparison: learned preconditioner and batching vs plain."""
     import numpy as np
@@ -739,6 +764,7 @@ def main():
             for k in ("learned_N1e6", "batched_64sys_plain", "batched_64sys_learned", "batched_64sys_lone"):
                 line[k] = line["variants"][k]
             line["variants"].update(variants_full_lanczos(dev, flush, stream, 5, xi, M_grid))
+            line["variants"].update(variants_poly(dev, flush, stream, max(20, args.steps // 4)))
             line["variants"].update(variants_configs(dev, flush, stream, 10, peak))
         if not args.no_cpu_baseline and ws == 1:
             line["cpu_baseline"] = cpu_baseline(xi)

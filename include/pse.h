@@ -157,6 +157,16 @@ pse_status pse_plan(double L, double a, const pse_params *p, pse_plan_info *out)
  * xi > 0, a > 0; r, F, G: host arrays of n doubles (caller-owned). */
 pse_status pse_real_scalars(double xi, double a, int64_t n, const double *r, double *F, double *G);
 
+/* Host-only: real-space scalars of a polydisperse pair (Sec. V: the shape
+ * factor sinc(k a_i) sinc(k a_j) in the k-integral of eq. pairmobility),
+ * split by H(k, xi) as in eq. Mreal: M^(r)_ij = F (I - rr) + G rr in mobility
+ * units (eta = 1, no 6 pi a factor).  Computed as the free-space RPY tensor
+ * of two unequal spheres less the H-weighted k-integral (Gauss-Legendre on
+ * [0, 16 xi]); r = 0 gives the r -> 0 limit (the self term when ai = aj).
+ * xi, ai, aj > 0; r, F, G: host arrays of n doubles (caller-owned). */
+pse_status pse_real_scalars_poly(double xi, double ai, double aj, int64_t n, const double *r, double *F,
+                                 double *G);
+
 /* Create a sampler for a cube of side L and spheres of radius a with the
  * default parameters (FP32, graph, max_iter 64) -- Sec. II.
  * Allocates device memory on the current device lazily, at the first
@@ -360,6 +370,46 @@ pse_status pse_mobility_apply(pse_ctx *ctx, int64_t N, const float *d_pos, const
  * device arrays in the caller's order. */
 pse_status pse_real_matvec(pse_ctx *ctx, int64_t N, const float *d_pos, const float *d_v,
                            float *d_out, void *stream);
+
+/* ---------------------------------------------------------------- polydisperse suspensions
+ * Sec. V: polydispersity enters by making the shape factor size dependent.
+ * Spheres of radii a_i, a_j carry sinc(k a_i) sinc(k a_j) where equal
+ * spheres carry sinc^2(k a) in eq. pairmobility; the H(k, xi) split keeps
+ * both parts positive.  Wave part: one noise dW2, one spectrum per species
+ * scaled with that species' sinc(k a_s) (eq. Mwave's B^{1/2} otherwise
+ * unchanged), one inverse FFT per species, each particle interpolated from
+ * its species' grid -- the exact covariance sum_k sinc(k a_i) sinc(k a_j) ...
+ * of the gridded sampler.  Real part: Lanczos on M_r with per-pair scalars
+ * (pse_real_scalars_poly) tabulated per species pair and a per-species self
+ * term.  Up to PSE_MAX_SPECIES radii; FP32 with FP64 Lanczos scalars.  The
+ * Sec. II C parameters use the smallest radius (the strictest wave cutoff). */
+#define PSE_MAX_SPECIES 4
+
+/* Create a sampler for spheres of n_species radii (radii[0 .. n_species-1]
+ * > 0) in a cube of side L.  p as for pse_create_ex; n_species >= 2 needs
+ * precision FP32, wave_noise 0, wave_fft 0, interp_form 0, use_precond 0
+ * and a Gaussian support P in 3..10 (PSE_ENOTSUPPORTED otherwise).  One
+ * species is the monodisperse sampler at that radius.  Device memory: the
+ * spectrum and grids once per species. */
+pse_status pse_create_poly(pse_ctx **out, double L, int n_species, const double *radii, const pse_params *p);
+
+/* Number of species (0 for a context made by pse_create[_ex]) and their radii
+ * (host array of PSE_MAX_SPECIES doubles, may be NULL). */
+pse_status pse_get_species(const pse_ctx *ctx, int *n_species, double *radii);
+
+/* One polydisperse PSE sample (as pse_sample_parts): d_species holds the
+ * species index of every particle (N int32, device, caller order; values
+ * outside [0, n_species) are clamped into it).  d_out, d_real, d_wave: 3N
+ * float32 device arrays or NULL (at least one).  The monodisperse entry
+ * points, the forces, Brownian, full-mobility, profiling and
+ * preconditioner calls return PSE_ENOTSUPPORTED for contexts with two or
+ * more species. */
+pse_status pse_sample_poly(pse_ctx *ctx, int64_t N, const float *d_pos, const int *d_species, uint64_t seed,
+                           uint64_t sample_index, float *d_out, float *d_real, float *d_wave, void *stream);
+
+/* Polydisperse near-field product d_out = M_r d_v (arguments as above). */
+pse_status pse_real_matvec_poly(pse_ctx *ctx, int64_t N, const float *d_pos, const int *d_species,
+                                const float *d_v, float *d_out, void *stream);
 
 /* ---------------------------------------------------------------- learned preconditioner
  * Not in the paper.  The real-space Lanczos may run on S M_r S for any

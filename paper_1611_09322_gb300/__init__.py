@@ -14,7 +14,7 @@ import numpy as np
 from . import _lib
 from ._lib import PSE_FP32, PSE_FP64, PseError, pse_params, pse_plan_info, pse_stats
 
-__all__ = ["Sampler", "BatchSampler", "pse_plan", "pse_real_scalars", "pse_real_matvec_noalloc", "pse_precond_loss_grad",
+__all__ = ["Sampler", "PolySampler", "BatchSampler", "pse_plan", "pse_real_scalars", "pse_real_scalars_poly", "pse_real_matvec_noalloc", "pse_precond_loss_grad",
            "pse_precond_train", "pse_xi_model", "pse_tune_xi", "PseError", "PSE_FP32", "PSE_FP64", "make_params"]
 
 
@@ -59,6 +59,17 @@ def pse_real_scalars(r, xi, a=1.0):
     G = np.empty_like(r)
     vp = lambda x: x.ctypes.data_as(ctypes.c_void_p)
     _lib.check(lib.pse_real_scalars(xi, a, r.size, vp(r), vp(F), vp(G)), "pse_real_scalars")
+    return F, G
+
+
+def pse_real_scalars_poly(r, xi, ai, aj):
+    """Host-only real-space scalars (F, G) of a pair of spheres of radii ai, aj (mobility units)."""
+    lib = _lib.load()
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    F = np.empty_like(r)
+    G = np.empty_like(r)
+    vp = lambda x: x.ctypes.data_as(ctypes.c_void_p)
+    _lib.check(lib.pse_real_scalars_poly(xi, ai, aj, r.size, vp(r), vp(F), vp(G)), "pse_real_scalars_poly")
     return F, G
 
 
@@ -317,6 +328,55 @@ class Sampler:
         d = s.as_dict()
         d["status"] = _lib.STATUS.get(st, st)
         return d
+
+
+class PolySampler(Sampler):
+    """PSE sampler for spheres of several radii (species; pse_create_poly, pse_sample_poly)."""
+
+    def __init__(self, L, radii, **kw):
+        self.lib = _lib.load()
+        self.params = make_params(**kw)
+        self.L = L
+        self.radii = np.ascontiguousarray(radii, dtype=np.float64)
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.pse_create_poly(ctypes.byref(h), L, self.radii.size,
+                                            self.radii.ctypes.data_as(ctypes.c_void_p), ctypes.byref(self.params)),
+                   "pse_create_poly")
+        self.ctx = h
+        info = pse_plan_info()
+        _lib.check(self.lib.pse_get_plan(self.ctx, ctypes.byref(info)), "pse_get_plan")
+        self.plan = info.as_dict()
+        self.a = self.plan["a"]
+        self.fp64 = False
+
+    def _check_species(self, pos, species):
+        import torch
+        if not (species.is_cuda and species.dtype == torch.int32 and species.is_contiguous()
+                and species.shape == (pos.shape[0],)):
+            raise ValueError("species must be a contiguous (N,) int32 CUDA tensor")
+
+    def sample(self, pos, species, seed, sample_index=0, out=None, parts=False):
+        """u at `pos` for particles of the given species; with parts=True (u, u_real, u_wave)."""
+        import torch
+        self._check_pos(pos)
+        self._check_species(pos, species)
+        if out is None:
+            out = torch.empty_like(pos)
+        real = torch.empty_like(pos) if parts else None
+        wave = torch.empty_like(pos) if parts else None
+        _lib.check(self.lib.pse_sample_poly(self.ctx, pos.shape[0], _ptr(pos), _ptr(species), seed, sample_index,
+                                            _ptr(out), _ptr(real), _ptr(wave), _stream()), "pse_sample_poly")
+        return (out, real, wave) if parts else out
+
+    def real_matvec(self, pos, species, v, out=None):
+        import torch
+        self._check_pos(pos)
+        self._check_species(pos, species)
+        if out is None:
+            out = torch.empty_like(v)
+        _lib.check(self.lib.pse_real_matvec_poly(self.ctx, pos.shape[0], _ptr(pos), _ptr(species), _ptr(v),
+                                                 _ptr(out), _stream()), "pse_real_matvec_poly")
+        return out
 
 
 class BatchSampler:

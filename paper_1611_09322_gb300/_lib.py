@@ -115,6 +115,10 @@ SIGNATURES = {
                                 _VP]),
     "pse_precond_set_weights": (_ST, [_VP, _VP, ctypes.c_int]),
     "pse_precond_blocks": (_ST, [_VP, _I64, _VP, _VP, _VP]),
+    "pse_create_poly": (_ST, [ctypes.POINTER(_VP), ctypes.c_double, ctypes.c_int, _VP, ctypes.POINTER(pse_params)]),
+    "pse_get_species": (_ST, [_VP, ctypes.POINTER(ctypes.c_int), _VP]),
+    "pse_sample_poly": (_ST, [_VP, _I64, _VP, _VP, _U64, _U64, _VP, _VP, _VP, _VP]),
+    "pse_real_matvec_poly": (_ST, [_VP, _I64, _VP, _VP, _VP, _VP, _VP]),
     "pse_batch_create": (_ST, [ctypes.POINTER(_VP), ctypes.c_int, _VP, _VP, _VP]),
     "pse_batch_sample": (_ST, [_VP, _VP, _VP, _U64, _U64, _VP, _VP]),
     "pse_batch_get_stats": (_ST, [_VP, ctypes.c_int, ctypes.POINTER(pse_stats)]),
@@ -122,6 +126,7 @@ SIGNATURES = {
     "pse_batch_destroy": (None, [_VP]),
     "pse_batch_set_precond": (_ST, [_VP, ctypes.c_int, _VP, ctypes.c_int]),
     "pse_real_scalars": (_ST, [ctypes.c_double, ctypes.c_double, _I64, _VP, _VP, _VP]),
+    "pse_real_scalars_poly": (_ST, [ctypes.c_double, ctypes.c_double, ctypes.c_double, _I64, _VP, _VP, _VP]),
     "pse_xi_model": (_ST, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                            ctypes.POINTER(ctypes.c_double)]),
     "pse_tune_xi": (_ST, [ctypes.c_double, ctypes.c_double, ctypes.POINTER(pse_params), _I64, _VP, ctypes.c_double,

@@ -69,8 +69,16 @@ __device__ __forceinline__ void scatter_elem(int64_t i, const SampleArgs<T> *arg
     l.x = cell_offset(x, cx, g.cs, g.cs_lo);
     l.y = cell_offset(y, cy, g.cs, g.cs_lo);
     l.z = cell_offset(z, cz, g.cs, g.cs_lo);
-    if constexpr (sizeof(T) == 4) l.w = __int_as_float(c);
-    else l.w = __longlong_as_double((long long)c);
+    // polydisperse: the species (clamped to the context's species) rides in
+    // the high bits of the cell id
+    int cw = c;
+    if (args->species) {
+        int sp = args->species[i];
+        sp = sp < 0 ? 0 : (sp >= g.nspec ? g.nspec - 1 : sp);
+        cw |= sp << PSE_SPECIES_SHIFT;
+    }
+    if constexpr (sizeof(T) == 4) l.w = __int_as_float(cw);
+    else l.w = __longlong_as_double((long long)cw);
     loc_sorted[dst] = l;  // the per-cell sort copies the offsets into the matvec records
 }
 
@@ -138,7 +146,7 @@ __device__ __forceinline__ int nbr_walk(int64_t s, int64_t N, const Geom<T> &g, 
                                         int4 *edge, int *edge_n, int edge_cap) {
     int cnt = 0;
     const V4<T> li = loc[s];
-    const int c = (int)w_bits(li.w);
+    const int c = (int)(w_bits(li.w) & PSE_CELL_MASK);
     const int nc = g.nc;
     int cx, cy, cz;
     cell_xyz(c, g.nb, cx, cy, cz);

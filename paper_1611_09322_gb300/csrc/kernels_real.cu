@@ -157,9 +157,20 @@ __device__ __forceinline__ void pair_fg_c(T r, const Geom<T> &g, const V4<T> *ta
     GmF = tb.y + f * tb.w;
 }
 
+// Species index of a cell record (polydisperse contexts).
+template <typename T> __device__ __forceinline__ int spec_of(const V4<T> &l) {
+    return (int)((w_bits_r(l.w) >> PSE_SPECIES_SHIFT) & 3);
+}
+// Self mobility of species sp (selects, so that the parameter array is not
+// copied to local memory for a dynamic index).
+template <typename T> __device__ __forceinline__ T self_of(const Geom<T> &g, int sp) {
+    return sp == 0 ? g.self_s[0] : (sp == 1 ? g.self_s[1] : (sp == 2 ? g.self_s[2] : g.self_s[3]));
+}
+
 // Row s of M_r q without the self term, summed over the TPP-thread group.
 // CT: `table` is the compact table (pair_fg_c), else the uniform one.
-template <typename T, int TPP, int ILP, bool CT = false>
+// POLY: the uniform table holds one block per species pair (polydisperse).
+template <typename T, int TPP, int ILP, bool CT = false, bool POLY = false>
 __device__ __forceinline__ void mr_row_part(int64_t N, int64_t s, int lane_g, bool active, int K, const Geom<T> &g,
                                             const Rec<T> *__restrict__ rec, const int *__restrict__ count,
                                             const int *__restrict__ nbr, const V4<T> *__restrict__ table,
@@ -203,8 +214,14 @@ __device__ __forceinline__ void mr_row_part(int64_t N, int64_t s, int lane_g, bo
                 if constexpr (sizeof(T) == 4) rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
                 else rinv = r2 > 0.0 ? 1.0 / sqrt(r2) : 0.0;
                 T F, GmF;
-                if constexpr (CT) pair_fg_c(r2 * rinv, g, table, F, GmF);
-                else pair_fg(r2 * rinv, g, table, F, GmF);
+                if constexpr (CT) {
+                    pair_fg_c(r2 * rinv, g, table, F, GmF);
+                } else if constexpr (POLY) {
+                    const V4<T> *tb = table + (int64_t)pair_index(spec_of(li), spec_of(rt[u].l), g.nspec) * PSE_TABLE_N;
+                    pair_fg(r2 * rinv, g, tb, F, GmF);
+                } else {
+                    pair_fg(r2 * rinv, g, table, F, GmF);
+                }
                 const T hx = dx * rinv, hy = dy * rinv, hz = dz * rinv;
                 const T dot = GmF * (hx * rt[u].q.x + hy * rt[u].q.y + hz * rt[u].q.z);
                 ax += F * rt[u].q.x + dot * hx;
@@ -223,7 +240,7 @@ __device__ __forceinline__ void mr_row_part(int64_t N, int64_t s, int lane_g, bo
 
 // Body of one Lanczos matvec over the nblk blocks of one system (bidx = this
 // block's index among them).
-template <typename T, int TPP, int ILP, bool CT>
+template <typename T, int TPP, int ILP, bool CT, bool POLY = false>
 __device__ __forceinline__ void lz_matvec_body(int64_t N, int K, const Geom<T> &g, const Rec<T> *__restrict__ rec,
                                                const int *__restrict__ count, const int *__restrict__ nbr,
                                                const V4<T> *__restrict__ table, V4<T> *u, double *partials,
@@ -244,12 +261,13 @@ __device__ __forceinline__ void lz_matvec_body(int64_t N, int K, const Geom<T> &
         const bool active = s < end;
         V4<T> li, qi;
         T ax, ay, az;
-        mr_row_part<T, TPP, ILP, CT>(N, s, lane_g, active, K, g, rec, count, nbr, table, li, qi, ax, ay, az);
+        mr_row_part<T, TPP, ILP, CT, POLY>(N, s, lane_g, active, K, g, rec, count, nbr, table, li, qi, ax, ay, az);
         if (active && lane_g == 0) {
             V4<T> o;
-            o.x = ax + g.self_m * qi.x;
-            o.y = ay + g.self_m * qi.y;
-            o.z = az + g.self_m * qi.z;
+            const T self = POLY ? self_of(g, spec_of(li)) : g.self_m;
+            o.x = ax + self * qi.x;
+            o.y = ay + self * qi.y;
+            o.z = az + self * qi.z;
             o.w = T(0);
             if (add) {  // full-mobility Lanczos: the wave product M_w q_j of the same vector
                 const V4<T> aw = add[s];
@@ -305,6 +323,19 @@ __global__ void __launch_bounds__(BS) k_lz_matvec(int64_t N, int K, Geom<T> g, c
         lz_matvec_body<T, TPP, ILP, false>(N, K, g, rec, count, nbr, table, u, partials, lz, pc, basis, add,
                                            blockIdx.x, gridDim.x, sh);
     }
+}
+
+// Polydisperse contexts (FP32): 4 threads x 4 gathers per particle in blocks
+// of 1024, F and G from the uniform table block of each species pair.
+__global__ void __launch_bounds__(1024) k_lz_matvec_poly(int64_t N, int K, Geom<float> g,
+                                                         const Rec<float> *__restrict__ rec,
+                                                         const int *__restrict__ count, const int *__restrict__ nbr,
+                                                         const V4<float> *__restrict__ table, V4<float> *u,
+                                                         double *partials, LzState *lz,
+                                                         const V4<float> *__restrict__ basis) {
+    __shared__ double sh[32];
+    lz_matvec_body<float, 4, 4, false, true>(N, K, g, rec, count, nbr, table, u, partials, lz, nullptr, basis,
+                                             nullptr, blockIdx.x, gridDim.x, sh);
 }
 
 // Fused over the systems of a batch: block b works for system blk2sys[b].
@@ -684,7 +715,7 @@ __global__ void k_gather_vec(int64_t N, const SampleArgs<T> *args, const V4<T> *
     rec[s].q = v;
 }
 
-template <typename T, int TPP>
+template <typename T, int TPP, bool POLY = false>
 __global__ void __launch_bounds__(128) k_matvec_scatter(int64_t N, int K, const SampleArgs<T> *args, Geom<T> g,
                                                         const Rec<T> *rec, const int *count, const int *nbr,
                                                         const V4<T> *table, const V4<T> *pos_sorted) {
@@ -694,12 +725,13 @@ __global__ void __launch_bounds__(128) k_matvec_scatter(int64_t N, int K, const 
     const bool active = s < N;
     V4<T> li, qi;
     T ax, ay, az;
-    mr_row_part<T, TPP, 4>(N, s, lane_g, active, K, g, rec, count, nbr, table, li, qi, ax, ay, az);
+    mr_row_part<T, TPP, 4, false, POLY>(N, s, lane_g, active, K, g, rec, count, nbr, table, li, qi, ax, ay, az);
     if (!active || lane_g != 0) return;
     const int64_t i = 3 * w_bits_r(pos_sorted[s].w);
-    args->out[i] = ax + g.self_m * qi.x;
-    args->out[i + 1] = ay + g.self_m * qi.y;
-    args->out[i + 2] = az + g.self_m * qi.z;
+    const T self = POLY ? self_of(g, spec_of(li)) : g.self_m;
+    args->out[i] = ax + self * qi.x;
+    args->out[i + 1] = ay + self * qi.y;
+    args->out[i + 2] = az + self * qi.z;
 }
 
 // M_r v for v already gathered into the records; output in sorted order.
@@ -772,12 +804,25 @@ template <typename T> int up_blocks_per_sm() {
 }
 int update_blocks_per_sm() { return up_blocks_per_sm<float>(); }
 // occupancy of every matvec shape, queried once outside any stream capture
+static int mv_poly_blocks_per_sm() {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lz_matvec_poly, 1024, 0) != cudaSuccess || nb < 1) {
+            cudaGetLastError();
+            nb = 1;
+        }
+        per_sm = nb;
+    }
+    return per_sm;
+}
 template <typename T> void mv_prepare_all() {
     mv_blocks_per_sm<T, 4, 4>(); mv_blocks_per_sm<T, 8, 2>();
     mv_blocks_per_sm<T, 16, 1>(); mv_blocks_per_sm<T, 4, 2>();
     mv_blocks_per_sm<T, 4, 4, 1024>(); mv_blocks_per_sm<T, 4, 4, 512>();
     mv_blocks_per_sm<T, 8, 2, 1024>(); mv_blocks_per_sm<T, 4, 2, 1024>();
     mv_blocks_per_sm<T, 1, 4, 1024>(); mv_blocks_per_sm<T, 2, 4, 1024>();
+    if constexpr (sizeof(T) == 4) mv_poly_blocks_per_sm();
 }
 void matvec_prepare() {
     mv_prepare_all<float>();
@@ -792,6 +837,13 @@ void mv_launch(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
         sizeof(T) == 4 ? d.pc_on : nullptr, d.basis, d.mv_add);
 }
 template <typename T> void launch_lz_matvec(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4) {
+        if (g.nspec > 1) {
+            k_lz_matvec_poly<<<pgrid(N, 1024 / 4, mv_poly_blocks_per_sm()), 1024, 0, s>>>(
+                N, nbr_k(N, d.nbr_cap), g, d.rec, d.nbr_count, d.nbr, d.table, d.u, d.partials, d.lz, d.basis);
+            return;
+        }
+    }
     switch (g.mv) {
         case 1: mv_launch<T, 8, 2>(N, g, d, s); break;
         case 2: mv_launch<T, 16, 1>(N, g, d, s); break;
@@ -858,9 +910,14 @@ template <typename T> void launch_matvec_sorted(int64_t N, Geom<T> g, const Dev<
 template <typename T>
 void launch_matvec_caller(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
     k_gather_vec<T><<<nb(N, 256), 256, 0, s>>>(N, args, d.pos_sorted, d.rec);
-    k_matvec_scatter<T, kMvTpp><<<nb(N * kMvTpp, 128), 128, 0, s>>>(N, nbr_k(N, d.nbr_cap), args, g, d.rec,
-                                                                     d.nbr_count, d.nbr, d.table,
-                                                                    d.pos_sorted);
+    if (g.nspec > 1)
+        k_matvec_scatter<T, kMvTpp, true><<<nb(N * kMvTpp, 128), 128, 0, s>>>(N, nbr_k(N, d.nbr_cap), args, g, d.rec,
+                                                                              d.nbr_count, d.nbr, d.table,
+                                                                              d.pos_sorted);
+    else
+        k_matvec_scatter<T, kMvTpp><<<nb(N * kMvTpp, 128), 128, 0, s>>>(N, nbr_k(N, d.nbr_cap), args, g, d.rec,
+                                                                         d.nbr_count, d.nbr, d.table,
+                                                                         d.pos_sorted);
 }
 
 #define PSE_INST(T)                                                                                          \

@@ -114,20 +114,36 @@ __device__ __forceinline__ void wave_noise_elem(int64_t t, const WaveGeom<T> &w,
     const ModeIdx m = mode_of(t, w);
     C o0, o1, o2;
     o0.x = o0.y = o1.x = o1.y = o2.x = o2.y = T(0);
+    T pr[3] = {T(0), T(0), T(0)}, pi[3] = {T(0), T(0), T(0)};  // (I - kk) dW2
+    int n2 = 0;
+    T sc = T(0);
     if (m.live) {
         T wr[3], wi[3];
         mode_noise<T>(m, w.M, w.Mh1, 2u * system + 1u, args->seed, args->sample, wr, wi);
         T hx, hy, hz;
-        const T sc = mode_scale<T>(m, w, hx, hy, hz);
+        sc = mode_scale<T>(m, w, hx, hy, hz);
+        n2 = m.nx * m.nx + m.ny * m.ny + m.nz * m.nz;
         const T dr = hx * wr[0] + hy * wr[1] + hz * wr[2];
         const T di = hx * wi[0] + hy * wi[1] + hz * wi[2];
-        o0.x = sc * (wr[0] - hx * dr); o0.y = sc * (wi[0] - hx * di);
-        o1.x = sc * (wr[1] - hy * dr); o1.y = sc * (wi[1] - hy * di);
-        o2.x = sc * (wr[2] - hz * dr); o2.y = sc * (wi[2] - hz * di);
+        pr[0] = wr[0] - hx * dr; pi[0] = wi[0] - hx * di;
+        pr[1] = wr[1] - hy * dr; pi[1] = wi[1] - hy * di;
+        pr[2] = wr[2] - hz * dr; pi[2] = wi[2] - hz * di;
     }
+    o0.x = sc * pr[0]; o0.y = sc * pi[0];
+    o1.x = sc * pr[1]; o1.y = sc * pi[1];
+    o2.x = sc * pr[2]; o2.y = sc * pi[2];
     spec[t] = o0;
     spec[plane + t] = o1;
     spec[2 * plane + t] = o2;
+    // polydisperse: species s scales the same noise with its own shape factor
+    for (int sp = 1; sp < w.nspec; ++sp) {
+        const T scs = m.live ? w.sc_tab[sp * w.sc_stride + 2 * n2] : T(0);
+        C *o = spec + (int64_t)sp * 3 * plane;
+        C q;
+        q.x = scs * pr[0]; q.y = scs * pi[0]; o[t] = q;
+        q.x = scs * pr[1]; q.y = scs * pi[1]; o[plane + t] = q;
+        q.x = scs * pr[2]; q.y = scs * pi[2]; o[2 * plane + t] = q;
+    }
 }
 
 template <typename T>
@@ -573,7 +589,8 @@ __global__ void k_grid_aos(int64_t M3, const float *__restrict__ g, V4<float> *_
 template <int P>
 __device__ __forceinline__ void interp4_warp(int64_t warp0, int64_t N, const WaveGeom<float> &w,
                                              const V4<float> *__restrict__ pos_sorted,
-                                             const V4<float> *__restrict__ grid4, V4<float> *uwave) {
+                                             const V4<float> *__restrict__ grid4, V4<float> *uwave,
+                                             const V4<float> *__restrict__ loc = nullptr) {
     constexpr int R = 32 / P;  // particles per warp; lanes R P .. 31 idle
     const int lane = threadIdx.x & 31;
     const int g = lane / P, c = lane - (lane / P) * P;
@@ -582,6 +599,10 @@ __device__ __forceinline__ void interp4_warp(int64_t warp0, int64_t N, const Wav
     const int base = (g < R ? g : 0) * P;  // first lane of the group
     const V4<float> p = pos_sorted[act ? s : 0];
     const int M = w.M;
+    if (loc) {  // polydisperse: the grid of this particle's species
+        const int sp = (__float_as_int(loc[act ? s : 0].w) >> PSE_SPECIES_SHIFT) & 3;
+        grid4 += (int64_t)sp * M * M * M;
+    }
     int i0x, i0y, i0z;
     float ux, uy, uz;
     support(p.x, w, i0x, ux);
@@ -635,10 +656,11 @@ __device__ __forceinline__ void interp4_warp(int64_t warp0, int64_t N, const Wav
 template <int P>
 __global__ void __launch_bounds__(128) k_interp4(int64_t N, WaveGeom<float> w,
                                                  const V4<float> *__restrict__ pos_sorted,
-                                                 const V4<float> *__restrict__ grid4, V4<float> *uwave) {
+                                                 const V4<float> *__restrict__ grid4, V4<float> *uwave,
+                                                 const V4<float> *__restrict__ loc) {
     const int64_t warp0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * (32 / P);
     if (warp0 >= N) return;  // whole warps leave together
-    interp4_warp<P>(warp0, N, w, pos_sorted, grid4, uwave);
+    interp4_warp<P>(warp0, N, w, pos_sorted, grid4, uwave, loc);
 }
 
 // Fused over the systems of a batch: the node-major copy of every system's
@@ -673,7 +695,8 @@ static inline unsigned nbw(int64_t n, int b) { return (unsigned)((n + b - 1) / b
 template <int P>
 static void interp4(int64_t N, const WaveGeom<float> &w, const Dev<float> &d, cudaStream_t s) {
     const int64_t warps = (N + 32 / P - 1) / (32 / P);
-    k_interp4<P><<<nbw(warps * 32, 128), 128, 0, s>>>(N, w, d.pos_sorted, d.grid4, d.uwave);
+    k_interp4<P><<<nbw(warps * 32, 128), 128, 0, s>>>(N, w, d.pos_sorted, d.grid4, d.uwave,
+                                                      w.nspec > 1 ? d.loc_sorted : nullptr);
 }
 
 void launch_batch_noise(const BSys *sys, int *const *tab, const int *nblk, cudaStream_t s) {
@@ -706,7 +729,8 @@ template <typename T> void launch_grid_copy(WaveGeom<T> w, const Dev<T> &d, cuda
     if constexpr (sizeof(T) == 4) {
         if (w.interp_lanes == 0 && w.P >= 3 && w.P <= 10) {
             const int64_t M3 = (int64_t)w.M * w.M * w.M;
-            k_grid_aos<<<nbw(M3, 256), 256, 0, s>>>(M3, d.grid, d.grid4);
+            for (int sp = 0; sp < (w.nspec > 1 ? w.nspec : 1); ++sp)  // one grid per species
+                k_grid_aos<<<nbw(M3, 256), 256, 0, s>>>(M3, d.grid + (int64_t)sp * 3 * M3, d.grid4 + sp * M3);
         }
     }
 }

@@ -77,6 +77,8 @@ struct pse_ctx {
     std::vector<void *> per_ctx;                        // buffers freed at destroy
     bool pc_enabled = false;                            // learned preconditioner installed
     float pc_s0 = 0.f;                                  // self mobility^{-1/2}
+    int nspec = 0;                                      // polydisperse: species radii (0: monodisperse)
+    double radii[PSE_MAX_SPECIES] = {};
 };
 
 #define CK(call)                                            \
@@ -183,17 +185,25 @@ static void magic_div(uint32_t d, uint32_t *m, int *l) {
 // Noise scale per n^2 = nx^2 + ny^2 + nz^2 (FP64): (sc(k), 1/|n|) with k =
 // 2 pi |n| / L and sc(k) = V^{-1/2} sinc(ka)/k sqrt(1 + k^2/4xi^2)
 // exp(-(1 - eta) k^2/8xi^2) (eq. Mwave, the Gaussian's share removed).
-template <typename T> void build_scale_table(const pse_plan_info &p, std::vector<T> &tab) {
+template <typename T> int64_t scale_table_len(const pse_plan_info &p) {
+    const int h = p.M / 2;
+    return 2 * (3ll * h * h + 1);
+}
+// a: the sphere radius of the shape factor (a species' radius in a
+// polydisperse context); the table is appended to tab.
+template <typename T> void build_scale_table(const pse_plan_info &p, double a, std::vector<T> &tab) {
     const int h = p.M / 2;
     const int64_t n = 3ll * h * h + 1;
-    tab.assign(2 * n, T(0));
+    const size_t off = tab.size();
+    tab.resize(off + 2 * n, T(0));
+    T *out = tab.data() + off;
     const double ks = 2 * M_PI / p.L, inv_sqrtV = 1.0 / sqrt(p.L * p.L * p.L);
     for (int64_t n2 = 1; n2 < n; ++n2) {
-        const double k = ks * sqrt((double)n2), ka = k * p.a, k2 = k * k;
+        const double k = ks * sqrt((double)n2), ka = k * a, k2 = k * k;
         const double sc = inv_sqrtV * sin(ka) / (ka * k) * sqrt(1.0 + k2 / (4 * p.xi * p.xi)) *
                           exp(-(1 - p.eta) * k2 / (8 * p.xi * p.xi));
-        tab[2 * n2] = (T)sc;
-        tab[2 * n2 + 1] = (T)(1.0 / sqrt((double)n2));
+        out[2 * n2] = (T)sc;
+        out[2 * n2 + 1] = (T)(1.0 / sqrt((double)n2));
     }
 }
 
@@ -226,6 +236,8 @@ template <typename T> void fill_geom(pse_ctx *c) {
     // the float path's band of float64 decisions at r_cut (none in FP64)
     g.rc2_lo = sizeof(T) == 4 ? (T)(g.rc2_d * (1.0 - 4e-6)) : g.rc2;
     g.rc2_hi = sizeof(T) == 4 ? (T)(g.rc2_d * (1.0 + 4e-6)) : g.rc2;
+    g.nspec = c->nspec;
+    for (int sp = 0; sp < c->nspec; ++sp) g.self_s[sp] = (T)self_poly(p.xi, c->radii[sp]);
     geom<T>(c) = g;
     WaveGeom<T> w{};
     w.M = p.M;
@@ -248,6 +260,8 @@ template <typename T> void fill_geom(pse_ctx *c) {
     magic_div((uint32_t)p.M, &w.dv_M_m, &w.dv_M_l);
     // 0: node-major grid copy + one warp per particle (FP32, P in 3..10)
     w.interp_lanes = (sizeof(T) == 4 && c->params.interp_form == 0 && p.P >= 3 && p.P <= 10) ? 0 : 16;
+    w.nspec = c->nspec > 1 ? c->nspec : 1;
+    w.sc_stride = scale_table_len<T>(p);
     wgeom<T>(c) = w;
 }
 
@@ -258,23 +272,35 @@ template <typename T> pse_status init_ctx(pse_ctx *c) {
 
     Dev<T> &d = dev<T>(c);
     const pse_plan_info &p = c->plan;
-    // F, G table in FP64, stored (F, G-F, dF, d(G-F)) / (6 pi a) in T
+    // F, G table in FP64, stored (F, G-F, dF, d(G-F)) / (6 pi a) in T; a
+    // polydisperse context holds one block per species pair (mobility units)
+    const int S = c->nspec > 1 ? c->nspec : 1, npair = c->nspec > 1 ? S * (S + 1) / 2 : 1;
+    std::vector<V4<T>> tab((size_t)PSE_TABLE_N * npair);
     std::vector<double> F(PSE_TABLE_N), G(PSE_TABLE_N);
-    build_fg_table(p.r_cut, p.xi, p.a, PSE_TABLE_N, F.data(), G.data());
-    std::vector<V4<T>> tab(PSE_TABLE_N);
-    const double s = 1.0 / (6 * M_PI * p.a);
-    for (int i = 0; i < PSE_TABLE_N; ++i) {
-        const double f0 = F[i] * s, g0 = (G[i] - F[i]) * s;
-        const double f1 = (i + 1 < PSE_TABLE_N) ? F[i + 1] * s : f0;
-        const double g1 = (i + 1 < PSE_TABLE_N) ? (G[i + 1] - F[i + 1]) * s : g0;
-        tab[i].x = (T)f0;
-        tab[i].y = (T)g0;
-        tab[i].z = (T)(f1 - f0);
-        tab[i].w = (T)(g1 - g0);
-    }
+    for (int i0 = 0; i0 < S; ++i0)
+        for (int j0 = i0; j0 < S; ++j0) {
+            double s;
+            if (c->nspec > 1) {
+                build_fg_table_poly(p.r_cut, p.xi, c->radii[i0], c->radii[j0], PSE_TABLE_N, F.data(), G.data());
+                s = 1.0;
+            } else {
+                build_fg_table(p.r_cut, p.xi, p.a, PSE_TABLE_N, F.data(), G.data());
+                s = 1.0 / (6 * M_PI * p.a);
+            }
+            V4<T> *blk = tab.data() + (size_t)pair_index(i0, j0, S) * PSE_TABLE_N;
+            for (int i = 0; i < PSE_TABLE_N; ++i) {
+                const double f0 = F[i] * s, g0 = (G[i] - F[i]) * s;
+                const double f1 = (i + 1 < PSE_TABLE_N) ? F[i + 1] * s : f0;
+                const double g1 = (i + 1 < PSE_TABLE_N) ? (G[i + 1] - F[i + 1]) * s : g0;
+                blk[i].x = (T)f0;
+                blk[i].y = (T)g0;
+                blk[i].z = (T)(f1 - f0);
+                blk[i].w = (T)(g1 - g0);
+            }
+        }
     pse_status st;
-    if ((st = alloc(c->per_ctx, (void **)&d.table, sizeof(V4<T>) * PSE_TABLE_N)) != PSE_OK) return st;
-    CK(cudaMemcpy(d.table, tab.data(), sizeof(V4<T>) * PSE_TABLE_N, cudaMemcpyHostToDevice));
+    if ((st = alloc(c->per_ctx, (void **)&d.table, sizeof(V4<T>) * tab.size())) != PSE_OK) return st;
+    CK(cudaMemcpy(d.table, tab.data(), sizeof(V4<T>) * tab.size(), cudaMemcpyHostToDevice));
     {  // compact two-segment table for the shared-memory matvec
         const double split = 2 * p.a < p.r_cut ? 2 * p.a : p.r_cut;
         const double dA = split / PSE_TABLEC_A;
@@ -285,6 +311,7 @@ template <typename T> pse_status init_ctx(pse_ctx *c) {
             fg_at(r, p.xi, p.a, &Fc[i], &Gc[i]);
         }
         std::vector<V4<T>> tc(PSE_TABLEC_N);
+        const double s = 1.0 / (6 * M_PI * p.a);
         for (int i = 0; i < PSE_TABLEC_N; ++i) {
             const double f0 = Fc[i] * s, g0 = (Gc[i] - Fc[i]) * s;
             const double f1 = (i + 1 < PSE_TABLEC_N) ? Fc[i + 1] * s : f0;
@@ -299,8 +326,8 @@ template <typename T> pse_status init_ctx(pse_ctx *c) {
     }
     const int64_t M = p.M, plane = M * M * (M / 2 + 1);
     const size_t csize = sizeof(T) * 2;
-    if ((st = alloc(c->per_ctx, &d.spec, csize * 3 * plane)) != PSE_OK) return st;
-    if ((st = alloc(c->per_ctx, (void **)&d.grid, sizeof(T) * 3 * M * M * M)) != PSE_OK) return st;
+    if ((st = alloc(c->per_ctx, &d.spec, csize * 3 * plane * S)) != PSE_OK) return st;
+    if ((st = alloc(c->per_ctx, (void **)&d.grid, sizeof(T) * 3 * M * M * M * S)) != PSE_OK) return st;
     if constexpr (sizeof(T) == 4) {
         // power-of-two grids: the sample path's own inverse FFT (needs the
         // node-major grid of the interpolation)
@@ -321,7 +348,10 @@ template <typename T> pse_status init_ctx(pse_ctx *c) {
     }
     {
         std::vector<T> sct;
-        build_scale_table<T>(p, sct);
+        if (c->nspec > 1)
+            for (int sp = 0; sp < S; ++sp) build_scale_table<T>(p, c->radii[sp], sct);
+        else
+            build_scale_table<T>(p, p.a, sct);
         T *d_sct = nullptr;
         if ((st = alloc(c->per_ctx, (void **)&d_sct, sizeof(T) * sct.size())) != PSE_OK) return st;
         CK(cudaMemcpy(d_sct, sct.data(), sizeof(T) * sct.size(), cudaMemcpyHostToDevice));
@@ -329,7 +359,7 @@ template <typename T> pse_status init_ctx(pse_ctx *c) {
     }
     if constexpr (sizeof(T) == 4)
         if (c->params.interp_form == 0 && p.P >= 3 && p.P <= 10 &&
-            (st = alloc(c->per_ctx, (void **)&d.grid4, sizeof(V4<T>) * M * M * M)) != PSE_OK)
+            (st = alloc(c->per_ctx, (void **)&d.grid4, sizeof(V4<T>) * M * M * M * S)) != PSE_OK)
             return st;
     if ((st = alloc(c->per_ctx, (void **)&d.lz, sizeof(LzState))) != PSE_OK) return st;
     CK(cudaMemset(d.lz, 0, sizeof(LzState)));
@@ -339,7 +369,7 @@ template <typename T> pse_status init_ctx(pse_ctx *c) {
     c->pc_s0 = (float)(1.0 / sqrt(p.self_mobility));
     int n[3] = {(int)M, (int)M, (int)M};
     CKF(cufftPlanMany(&c->fft, 3, n, nullptr, 1, (int)plane, nullptr, 1, (int)(M * M * M),
-                      sizeof(T) == 4 ? CUFFT_C2R : CUFFT_Z2D, 3));
+                      sizeof(T) == 4 ? CUFFT_C2R : CUFFT_Z2D, 3 * S));
     c->fft_made = true;
     CK(cudaStreamCreateWithFlags(&c->s_main, cudaStreamNonBlocking));
     CK(cudaStreamCreateWithFlags(&c->s_copy, cudaStreamNonBlocking));
@@ -864,7 +894,7 @@ template <typename T> pse_status tune_matvec(pse_ctx *c, cudaStream_t s) {
 
 template <typename T>
 pse_status sample_impl(pse_ctx *c, int64_t N, const T *pos, uint64_t seed, uint64_t sample, T *out, T *real,
-                       T *wave, cudaStream_t s) {
+                       T *wave, cudaStream_t s, const int *species = nullptr) {
     if (!pos || N < 1) return PSE_EINVAL;
     if (!out && !real && !wave) return PSE_EINVAL;
     DeviceGuard guard(c->device);
@@ -886,8 +916,9 @@ pse_status sample_impl(pse_ctx *c, int64_t N, const T *pos, uint64_t seed, uint6
     a.sample = sample;
     a.c_det = 0.0;
     a.c_noise = 1.0;
+    a.species = species;
     CK(push_args(c, dev<T>(c).args, &a, sizeof(a), s));
-    if ((c->params.autotune & 4) && c->params.matvec_shape == 0 && !c->mv_tuned) {
+    if ((c->params.autotune & 4) && c->params.matvec_shape == 0 && !c->mv_tuned && c->nspec < 2) {
         if ((st = tune_matvec<T>(c, s)) != PSE_OK) return st;
         if (use_graph && (st = build_graph<T>(c, GM_SAMPLE)) != PSE_OK) return st;
     }
@@ -1154,13 +1185,16 @@ double xi_max_for_grid(double L, double a, const pse_params &p0, int M) {
     return lo;
 }
 
-pse_status create_impl(pse_ctx **out, double L, double a, const pse_params *p) {
+pse_status create_impl(pse_ctx **out, double L, double a, const pse_params *p, int nspec = 0,
+                       const double *radii = nullptr) {
     if (!out) return PSE_EINVAL;
     *out = nullptr;
     if (!p) return PSE_EINVAL;
     pse_ctx *c = new (std::nothrow) pse_ctx();
     if (!c) return PSE_ENOMEM;
     c->params = *p;
+    c->nspec = nspec;
+    for (int sp = 0; sp < nspec; ++sp) c->radii[sp] = radii[sp];
     pse_status st = pse_plan(L, a, p, &c->plan);
     if (st != PSE_OK) { delete c; return st; }
     if ((p->autotune & 1) && p->grid_M <= 0) {
@@ -1196,11 +1230,20 @@ pse_status create_impl(pse_ctx **out, double L, double a, const pse_params *p) {
         delete c;
         return PSE_EINVAL;
     }
+    if (nspec > 1 && (c->plan.P < 3 || c->plan.P > 10)) {  // species grids need the node-major interpolation
+        delete c;
+        return PSE_ENOTSUPPORTED;
+    }
     st = (p->precision == PSE_FP64) ? init_ctx<double>(c) : init_ctx<float>(c);
     if (st != PSE_OK) { pse_destroy(c); return st; }
     *out = c;
     return PSE_OK;
 }
+
+// Polydisperse contexts hold species tables and grids; the monodisperse
+// entry points (and the forces, Brownian, full-mobility and preconditioner
+// paths) are not available for them.
+inline bool poly_ctx(const pse_ctx *c) { return c && c->nspec > 1; }
 
 }  // namespace
 
@@ -1208,6 +1251,61 @@ extern "C" {
 
 pse_status pse_create_ex(pse_ctx **out, double L, double a, const pse_params *p) {
     return create_impl(out, L, a, p);
+}
+
+pse_status pse_create_poly(pse_ctx **out, double L, int n_species, const double *radii, const pse_params *p) {
+    if (!out) return PSE_EINVAL;
+    *out = nullptr;
+    if (!p || !radii || n_species < 1 || n_species > PSE_MAX_SPECIES) return PSE_EINVAL;
+    double amin = radii[0];
+    for (int sp = 0; sp < n_species; ++sp) {
+        if (!(radii[sp] > 0) || !isfinite(radii[sp])) return PSE_EINVAL;
+        amin = radii[sp] < amin ? radii[sp] : amin;
+    }
+    if (n_species > 1 && (p->precision != PSE_FP32 || p->wave_noise != 0 || p->wave_fft != 0 ||
+                          p->interp_form != 0 || p->use_precond != 0))
+        return PSE_ENOTSUPPORTED;
+    // one species is the monodisperse sampler at that radius
+    return create_impl(out, L, amin, p, n_species, radii);
+}
+
+pse_status pse_get_species(const pse_ctx *c, int *n_species, double *radii) {
+    if (!c || !n_species) return PSE_EINVAL;
+    *n_species = c->nspec;
+    for (int sp = 0; sp < c->nspec && radii; ++sp) radii[sp] = c->radii[sp];
+    return PSE_OK;
+}
+
+pse_status pse_sample_poly(pse_ctx *c, int64_t N, const float *d_pos, const int *d_species, uint64_t seed,
+                           uint64_t sample_index, float *d_out, float *d_real, float *d_wave, void *stream) {
+    if (!c || c->plan.precision != PSE_FP32) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
+    if (c->nspec < 1) return PSE_ENOTSUPPORTED;  // a monodisperse context: use pse_sample
+    if (!d_species) return PSE_EINVAL;
+    return sample_impl<float>(c, N, d_pos, seed, sample_index, d_out, d_real, d_wave, (cudaStream_t)stream,
+                              d_species);
+}
+
+pse_status pse_real_matvec_poly(pse_ctx *c, int64_t N, const float *d_pos, const int *d_species, const float *d_v,
+                                float *d_out, void *stream) {
+    if (!c) return PSE_EINVAL;
+    if (c->plan.precision != PSE_FP32 || c->nspec < 1) return PSE_ENOTSUPPORTED;
+    if (!d_pos || !d_species || !d_v || !d_out || N < 1) return PSE_EINVAL;
+    DeviceGuard guard(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    pse_status st = ensure<float>(c, N);
+    if (st != PSE_OK) return st;
+    SampleArgs<float> a{};
+    a.pos = d_pos;
+    a.out = d_out;
+    a.vin = d_v;
+    a.species = d_species;
+    CK(push_args(c, c->df.args, &a, sizeof(a), s));
+    pre<float>(c, N, s);
+    launch_nbr<float>(N, c->gf, c->df, s);
+    launch_matvec_caller<float>(N, c->df.args, c->gf, c->df, s);
+    c->last_stream = s;
+    CK(cudaGetLastError());
+    return PSE_OK;
 }
 
 pse_status pse_create(pse_ctx **out, double L, double a, double xi, double tol) {
@@ -1251,6 +1349,7 @@ pse_status pse_get_plan(const pse_ctx *c, pse_plan_info *out) {
 
 pse_status pse_sample(pse_ctx *c, int64_t N, const float *d_pos, uint64_t seed, uint64_t sample_index, float *d_out,
                       void *stream) {
+    if (poly_ctx(c)) return PSE_ENOTSUPPORTED;
     if (!c || c->plan.precision != PSE_FP32) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
     if (!d_out) return PSE_EINVAL;
     return sample_impl<float>(c, N, d_pos, seed, sample_index, d_out, nullptr, nullptr, (cudaStream_t)stream);
@@ -1258,6 +1357,7 @@ pse_status pse_sample(pse_ctx *c, int64_t N, const float *d_pos, uint64_t seed, 
 
 pse_status pse_sample_parts(pse_ctx *c, int64_t N, const float *d_pos, uint64_t seed, uint64_t sample_index,
                             float *d_out, float *d_real, float *d_wave, void *stream) {
+    if (poly_ctx(c)) return PSE_ENOTSUPPORTED;
     if (!c || c->plan.precision != PSE_FP32) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
     return sample_impl<float>(c, N, d_pos, seed, sample_index, d_out, d_real, d_wave, (cudaStream_t)stream);
 }
@@ -1270,6 +1370,7 @@ pse_status pse_sample_f64(pse_ctx *c, int64_t N, const double *d_pos, uint64_t s
 
 pse_status pse_sample_with_forces(pse_ctx *c, int64_t N, const float *d_pos, const float *d_force, uint64_t seed,
                                   uint64_t sample_index, double c_det, double c_noise, float *d_out, void *stream) {
+    if (poly_ctx(c)) return PSE_ENOTSUPPORTED;
     if (!c || c->plan.precision != PSE_FP32) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
     return forces_impl<float>(c, N, d_pos, d_force, seed, sample_index, c_det, c_noise, d_out, (cudaStream_t)stream);
 }
@@ -1284,6 +1385,7 @@ pse_status pse_sample_with_forces_f64(pse_ctx *c, int64_t N, const double *d_pos
 
 pse_status pse_bd_step(pse_ctx *c, int64_t N, float *d_pos, const float *d_fext, double dt, double kT,
                        double k_rep, uint64_t seed, uint64_t step, void *stream) {
+    if (poly_ctx(c)) return PSE_ENOTSUPPORTED;
     if (!c || c->plan.precision != PSE_FP32) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
     return bd_impl<float>(c, N, d_pos, d_fext, dt, kT, k_rep, seed, step, (cudaStream_t)stream);
 }
@@ -1296,6 +1398,7 @@ pse_status pse_bd_step_f64(pse_ctx *c, int64_t N, double *d_pos, const double *d
 
 pse_status pse_sample_full_lanczos(pse_ctx *c, int64_t N, const float *d_pos, uint64_t seed, uint64_t sample_index,
                                    float *d_out, void *stream) {
+    if (poly_ctx(c)) return PSE_ENOTSUPPORTED;
     if (!c || c->plan.precision != PSE_FP32) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
     return full_impl<float>(c, N, d_pos, seed, sample_index, d_out, (cudaStream_t)stream);
 }
@@ -1314,6 +1417,7 @@ pse_status pse_mobility_apply(pse_ctx *c, int64_t N, const float *d_pos, const f
 pse_status pse_sample_host(pse_ctx *c, int64_t N, const float *h_pos, uint64_t seed, uint64_t sample_index,
                            float *h_out, void *stream) {
     if (!c || c->plan.precision != PSE_FP32) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
+    if (poly_ctx(c)) return PSE_ENOTSUPPORTED;
     if (!h_pos || !h_out || N < 1) return PSE_EINVAL;
     DeviceGuard guard(c->device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -1331,7 +1435,7 @@ pse_status pse_sample_host(pse_ctx *c, int64_t N, const float *h_pos, uint64_t s
 pse_status pse_real_matvec(pse_ctx *c, int64_t N, const float *d_pos, const float *d_v, float *d_out,
                            void *stream) {
     if (!c) return PSE_EINVAL;
-    if (c->plan.precision != PSE_FP32) return PSE_ENOTSUPPORTED;
+    if (c->plan.precision != PSE_FP32 || poly_ctx(c)) return PSE_ENOTSUPPORTED;
     if (!d_pos || !d_v || !d_out || N < 1) return PSE_EINVAL;
     DeviceGuard guard(c->device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -1353,7 +1457,7 @@ pse_status pse_real_matvec(pse_ctx *c, int64_t N, const float *d_pos, const floa
 pse_status pse_profile_stages(pse_ctx *c, int64_t N, const float *d_pos, uint64_t seed, uint64_t sample_index,
                               float *d_out, double *ms, int *launches, void *stream) {
     if (!c) return PSE_EINVAL;
-    if (c->plan.precision != PSE_FP32) return PSE_ENOTSUPPORTED;
+    if (c->plan.precision != PSE_FP32 || poly_ctx(c)) return PSE_ENOTSUPPORTED;
     if (!d_pos || !d_out || !ms || !launches || N < 1) return PSE_EINVAL;
     DeviceGuard guard(c->device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -1615,6 +1719,7 @@ static pse_status pc_prepare(pse_ctx *c, int64_t N, const float *d_pos, cudaStre
 pse_status pse_precond_features(pse_ctx *c, int64_t N, const float *d_pos, float *d_feat, float *d_tens,
                                 void *stream) {
     if (!d_feat || !d_tens) return PSE_EINVAL;
+    if (poly_ctx(c)) return PSE_ENOTSUPPORTED;
     DeviceGuard guard(c ? c->device : 0);
     cudaStream_t s = (cudaStream_t)stream;
     pse_status st = pc_prepare(c, N, d_pos, s);
@@ -1627,6 +1732,7 @@ pse_status pse_precond_features(pse_ctx *c, int64_t N, const float *d_pos, float
 
 pse_status pse_precond_targets(pse_ctx *c, int64_t N, const float *d_pos, float *d_target, void *stream) {
     if (!d_target) return PSE_EINVAL;
+    if (poly_ctx(c)) return PSE_ENOTSUPPORTED;
     DeviceGuard guard(c ? c->device : 0);
     cudaStream_t s = (cudaStream_t)stream;
     pse_status st = pc_prepare(c, N, d_pos, s);
@@ -1639,7 +1745,7 @@ pse_status pse_precond_targets(pse_ctx *c, int64_t N, const float *d_pos, float 
 
 pse_status pse_precond_set_weights(pse_ctx *c, const float *h_theta, int nparam) {
     if (!c) return PSE_EINVAL;
-    if (c->plan.precision != PSE_FP32) return PSE_ENOTSUPPORTED;
+    if (c->plan.precision != PSE_FP32 || poly_ctx(c)) return PSE_ENOTSUPPORTED;
     if (h_theta && nparam != PSE_PRECOND_NPARAM) return PSE_EINVAL;
     DeviceGuard guard(c->device);
     CK(cudaDeviceSynchronize());
@@ -1667,6 +1773,7 @@ pse_status pse_precond_blocks(pse_ctx *c, int64_t N, const float *d_pos, float *
 pse_status pse_sample_host_async(pse_ctx *c, int64_t N, const float *h_pos, uint64_t seed, uint64_t sample_index,
                                  float *h_out, void *stream) {
     if (!c || c->plan.precision != PSE_FP32) return c ? PSE_ENOTSUPPORTED : PSE_EINVAL;
+    if (poly_ctx(c)) return PSE_ENOTSUPPORTED;
     if (!h_pos || !h_out || N < 1) return PSE_EINVAL;
     DeviceGuard guard(c->device);
     cudaStream_t s = (cudaStream_t)stream;

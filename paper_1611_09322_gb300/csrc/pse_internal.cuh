@@ -13,6 +13,8 @@
 #define PSE_TABLEC_N 1024     // entries of the compact table the Lanczos matvec stages in shared memory
 #define PSE_TABLEC_A 256      // of which on [0, 2a): knots at 2a, where F and G have a kink
 #define PSE_SCAN_ITEMS 4096   // elements per block of the device scan
+#define PSE_SPECIES_SHIFT 28  // species index in bits 28-29 of a cell record's w (cell ids < 2^24)
+#define PSE_CELL_MASK 0x0FFFFFFF
 #define PSE_MAX_SCAN (PSE_SCAN_ITEMS * PSE_SCAN_ITEMS)
 
 namespace pse {
@@ -76,7 +78,17 @@ template <typename T> struct Geom {
     // the positions with the float64 r_cut^2 and box side
     T rc2_lo, rc2_hi;
     double rc2_d, L_d, invL_d;
+    // polydisperse contexts (nspec >= 2): per-species self mobility; pair
+    // (s, t) reads table block pair_index(s, t, nspec) of PSE_TABLE_N entries
+    int nspec;
+    T self_s[PSE_MAX_SPECIES];
 };
+
+// Block of the (unordered) species pair (s, t) in a polydisperse table.
+PSE_HD inline int pair_index(int s, int t, int S) {
+    const int i = s < t ? s : t, j = s < t ? t : s;
+    return i * S - (i * (i - 1)) / 2 + (j - i);
+}
 #define PSE_MV_VARIANTS 10
 
 // Wave-space parameters of one system.
@@ -97,6 +109,8 @@ template <typename T> struct WaveGeom {
     int big;             // M^2 Mh1 >= 2^32: 64-bit mode ids
     const void *fft_tw;  // M/2 float2 e^{2 pi i k / M} (power-of-two grids, fused FFT path)
     int interp_lanes;    // lanes per particle in the interpolation (8, 16, 32; 0 = pick)
+    int nspec;           // spectra / grids, one per species (1: monodisperse)
+    int64_t sc_stride;   // entries of one species' block of sc_tab
 };
 
 // Per-sample arguments, read by the kernels from device memory so that one
@@ -114,6 +128,7 @@ template <typename T> struct SampleArgs {
     T *advance;     // Brownian step: positions advanced in place by out (3N), or null
     const T *fext;  // Brownian step: external force (3N) added to the repulsion, or null
     double k_rep;   // Brownian step: overlap repulsion stiffness
+    const int *species;  // polydisperse contexts: species index per caller particle, or null
 };
 
 // Tiling of the spreading kernel: tiles of G^3 cells, each spread into a
@@ -488,6 +503,10 @@ __device__ __forceinline__ void sym3_apply(const float *M, float x, float y, flo
 
 // host-side setup (FP64 arithmetic)
 void build_fg_table(double r_cut, double xi, double a, int n, double *F, double *G);
+// Polydisperse pair (radii ai, aj): real-space scalars in mobility units on
+// n uniform knots of [0, r_cut]; knot 0 holds the self term when ai = aj.
+void build_fg_table_poly(double r_cut, double xi, double ai, double aj, int n, double *F, double *G);
+double self_poly(double xi, double a);
 void fg_at(double r, double xi, double a, double *F, double *G);
 double self_real(double xi, double a);
 

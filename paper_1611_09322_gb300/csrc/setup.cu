@@ -3,6 +3,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <vector>
+
 #include "pse_internal.cuh"
 
 namespace pse {
@@ -77,6 +79,115 @@ void build_fg_table(double r_cut, double xi, double a, int n, double *F, double 
             fg_closed(r, xi, a, &F[i], &G[i]);
         }
     }
+}
+
+// ------------------------------------------------------------------ polydisperse pairs
+// The size-dependent shape factor of Sec. V: spheres of radii ai, aj carry
+// sinc(k ai) sinc(k aj) where equal spheres carry sinc^2(k a).  With weight 1
+// the k-integral of eq. pairmobility is the free-space RPY tensor of two
+// unequal spheres (Zuk, Wajnryb, Mizerski & Szymczak, J. Fluid Mech. 741,
+// R5, 2014); the real-space part (weight 1 - H) is that tensor minus the
+// H-weighted integral, which decays like a Gaussian in k and is evaluated by
+// Gauss-Legendre quadrature on [0, 16 xi].  Scalars in mobility units:
+// block = F (I - rr) + G rr.
+
+// Free-space RPY of spheres ai, aj at separation r > 0 as (F, G).
+static void rpy_pair(double r, double ai, double aj, double *F, double *G) {
+    const double s2 = ai * ai + aj * aj, d = ai - aj;
+    double A, B;
+    if (r > ai + aj) {
+        A = (1 + s2 / (3 * r * r)) / (8 * kPi * r);
+        B = (1 - s2 / (r * r)) / (8 * kPi * r);
+    } else if (r > fabs(d)) {
+        const double t = d * d + 3 * r * r, u = d * d - r * r;
+        A = (16 * r * r * r * (ai + aj) - t * t) / (32 * r * r * r) / (6 * kPi * ai * aj);
+        B = 3 * u * u / (32 * r * r * r) / (6 * kPi * ai * aj);
+    } else {
+        A = 1.0 / (6 * kPi * (ai > aj ? ai : aj));
+        B = 0.0;
+    }
+    *F = A;
+    *G = A + B;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1]: Newton iteration on P_n from
+// the usual Chebyshev-like initial guesses.
+static void gauss_legendre(int n, double *x, double *w) {
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = cos(kPi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        w[i] = w[n - 1 - i] = 2.0 / ((1 - z * z) * dp * dp);
+    }
+}
+
+// Quadrature of the H-weighted integral for one (xi, ai, aj).
+struct PolyQuad {
+    std::vector<double> k, base;
+    PolyQuad(double xi, double ai, double aj) {
+        const int nq = 400;
+        std::vector<double> t(nq), wq(nq);
+        gauss_legendre(nq, t.data(), wq.data());
+        k.resize(nq);
+        base.resize(nq);
+        const double kmax = 16.0 * xi;
+        for (int q = 0; q < nq; ++q) {
+            k[q] = 0.5 * kmax * (t[q] + 1.0);
+            const double kk = k[q], h = kk * kk / (4 * xi * xi);
+            const double si = kk * ai > 0 ? sin(kk * ai) / (kk * ai) : 1.0;
+            const double sj = kk * aj > 0 ? sin(kk * aj) / (kk * aj) : 1.0;
+            base[q] = 0.5 * kmax * wq[q] * (1 + h) * exp(-h) * si * sj;
+        }
+    }
+    void at(double r, double ai, double aj, double *F, double *G) const {
+        double sF = 0.0, sG = 0.0;
+        for (size_t q = 0; q < k.size(); ++q) {
+            const double x = k[q] * r;
+            double kF, kG;
+            if (x < 2e-2) {
+                const double x2 = x * x;
+                kF = 2.0 / 3.0 - 2.0 * x2 / 15.0 + x2 * x2 / 140.0;
+                kG = 1.0 / 3.0 - x2 / 30.0 + x2 * x2 / 840.0;
+            } else {
+                kF = (x * cos(x) + (x * x - 1) * sin(x)) / (x * x * x);
+                kG = (sin(x) - x * cos(x)) / (x * x * x);
+            }
+            sF += base[q] * kF;
+            sG += base[q] * kG;
+        }
+        double Fr, Gr;
+        if (r > 0) {
+            rpy_pair(r, ai, aj, &Fr, &Gr);
+        } else {  // r -> 0: 1/(6 pi max(ai, aj)) I
+            Fr = Gr = 1.0 / (6 * kPi * (ai > aj ? ai : aj));
+        }
+        *F = Fr - sF / (2 * kPi * kPi);
+        *G = Gr - sG / (kPi * kPi);
+    }
+};
+
+void build_fg_table_poly(double r_cut, double xi, double ai, double aj, int n, double *F, double *G) {
+    const PolyQuad pq(xi, ai, aj);
+    const double dr = r_cut / (n - 1);
+    for (int i = 0; i < n; ++i) pq.at(i * dr, ai, aj, &F[i], &G[i]);
+}
+
+double self_poly(double xi, double a) {
+    double F, G;
+    PolyQuad(xi, a, a).at(0.0, a, a, &F, &G);
+    return F;
 }
 
 // ------------------------------------------------------------------ Sec. II C parameters
@@ -181,6 +292,17 @@ extern "C" pse_status pse_real_scalars(double xi, double a, int64_t n, const dou
         } else {
             fg_closed(r[i], xi, a, &F[i], &G[i]);
         }
+    }
+    return PSE_OK;
+}
+
+extern "C" pse_status pse_real_scalars_poly(double xi, double ai, double aj, int64_t n, const double *r, double *F,
+                                            double *G) {
+    if (!(xi > 0) || !(ai > 0) || !(aj > 0) || n < 0 || (n > 0 && (!r || !F || !G))) return PSE_EINVAL;
+    const PolyQuad pq(xi, ai, aj);
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(r[i] >= 0) || !isfinite(r[i])) return PSE_EINVAL;
+        pq.at(r[i], ai, aj, &F[i], &G[i]);
     }
     return PSE_OK;
 }

@@ -5,6 +5,7 @@
  * CUDA path (via bench.py) and the test oracle draw their inputs from it.
  *
  *   wl_rsa      random sequential addition of non-overlapping spheres
+ *   wl_rsa_poly the same for spheres of unequal radii
  *   wl_relax    harmonic overlap relaxation (gradient descent) of spheres
  *   wl_cca_gel  fractal clusters built by tunable-dimension cluster-cluster
  *               aggregation (monomer contact at 2a), packed into the box
@@ -126,6 +127,41 @@ int64_t wl_rsa(int64_t N, double L, double diameter, uint64_t seed, int64_t max_
  * until the largest overlap is below `stop_overlap`.  Returns the final
  * largest overlap d - r_ij (0 if none).
  */
+/*
+ * Random sequential addition of spheres with radii[i]: a proposal for
+ * sphere n is kept if it overlaps no earlier sphere (distance >= r_n + r_j).
+ * Spheres are placed in the given order (largest first packs best).
+ * rmax bounds every radius.  Returns the number placed.
+ */
+int64_t wl_rsa_poly(int64_t N, double L, const double *radii, double rmax, uint64_t seed, int64_t max_trials,
+                    double *out) {
+    grid_t g;
+    if (grid_init(&g, L, 2.0 * rmax, N) != 0) return -1;
+    rng_t r = {seed * 0x2545F4914F6CDD1DULL + 7};
+    int64_t n = 0;
+    for (int64_t t = 0; t < max_trials && n < N; ++t) {
+        double q[3] = {rng_u01(&r) * L, rng_u01(&r) * L, rng_u01(&r) * L};
+        int cx = cell_of(&g, q[0]), cy = cell_of(&g, q[1]), cz = cell_of(&g, q[2]);
+        int span = g.nc >= 3 ? 1 : 0, hit = 0;
+        for (int dx = -span; dx <= span && !hit; ++dx)
+            for (int dy = -span; dy <= span && !hit; ++dy)
+                for (int dz = -span; dz <= span && !hit; ++dz) {
+                    if (g.nc < 3 && (dx || dy || dz)) continue;
+                    for (int64_t j = g.head[cell_id(&g, cx + dx, cy + dy, cz + dz)]; j >= 0; j = g.next[j]) {
+                        double ex = mind(q[0] - out[3 * j], L), ey = mind(q[1] - out[3 * j + 1], L),
+                               ez = mind(q[2] - out[3 * j + 2], L), dm = radii[n] + radii[j];
+                        if (ex * ex + ey * ey + ez * ez < dm * dm) { hit = 1; break; }
+                    }
+                }
+        if (hit) continue;
+        out[3 * n] = q[0]; out[3 * n + 1] = q[1]; out[3 * n + 2] = q[2];
+        grid_insert(&g, out + 3 * n, n);
+        ++n;
+    }
+    grid_free(&g);
+    return n;
+}
+
 double wl_relax(int64_t N, double L, double diameter, int64_t steps, double step, double stop_overlap,
                 double *pos) {
     double *f = (double *)malloc(sizeof(double) * 3 * N);

@@ -30,6 +30,9 @@ def _lib():
         lib.wl_rsa.restype = ctypes.c_int64
         lib.wl_rsa.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_uint64,
                                ctypes.c_int64, dp]
+        lib.wl_rsa_poly.restype = ctypes.c_int64
+        lib.wl_rsa_poly.argtypes = [ctypes.c_int64, ctypes.c_double, dp, ctypes.c_double, ctypes.c_uint64,
+                                    ctypes.c_int64, dp]
         lib.wl_relax.restype = ctypes.c_double
         lib.wl_relax.argtypes = [ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
                                  ctypes.c_double, ctypes.c_double, dp]
@@ -71,6 +74,30 @@ def hard_spheres(N, phi, seed, a=1.0, relax_steps=10000, rsa_phi_max=0.3):
     if d_rsa < 2 * a:
         worst = lib.wl_relax(N, L, 2 * a, relax_steps, 0.25, 1e-4 * a, dp)
     return _f32(out, L), L, {"max_overlap": worst, "rsa_diameter": d_rsa}
+
+
+def polydisperse(N, phi, seed, radii=(1.0, 0.5), fractions=None):
+    """Random non-overlapping spheres of several radii (species) at total volume fraction phi.
+
+    Species s holds round(fractions[s] N) spheres (equal numbers by default);
+    they are placed by RSA largest first.  Returns (float32 (N, 3) positions,
+    int32 (N,) species indices, L, info)."""
+    radii = np.asarray(radii, dtype=np.float64)
+    S = radii.size
+    fr = np.full(S, 1.0 / S) if fractions is None else np.asarray(fractions, dtype=np.float64)
+    counts = np.floor(fr / fr.sum() * N).astype(np.int64)
+    counts[np.argmax(radii)] += N - counts.sum()
+    order = np.argsort(-radii, kind="stable")
+    species = np.concatenate([np.full(counts[s], s, dtype=np.int32) for s in order])
+    rad = radii[species]
+    L = (np.sum(4.0 / 3.0 * math.pi * rad ** 3) / phi) ** (1.0 / 3.0)
+    out = np.zeros((N, 3), dtype=np.float64)
+    dp = out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    rp = np.ascontiguousarray(rad).ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    n = _lib().wl_rsa_poly(N, L, rp, float(radii.max()), seed, 400 * N + 1000, dp)
+    if n != N:
+        raise RuntimeError(f"polydisperse RSA placed {n} of {N} spheres (phi={phi})")
+    return _f32(out, L), species, L, {"radii": radii.tolist(), "counts": counts.tolist()}
 
 
 def gel(N, phi, seed, a=1.0, df=1.9, kf=1.3, csize=256):
