@@ -19,7 +19,9 @@ rpy      real-space scalar functions F, G (Appendix A), self term (eq. self),
 ewald    splitting function H, truncation / quadrature parameters (Sec. II C),
          dense real- and wave-space mobilities (eqs. Mreal, Mwave)
 philox   Philox4x32-10 counter-based generator and Box-Muller normals
-pse      real-space Lanczos sample and wave-space NUFFT sample (Sec. II B)
+pse      real-space Lanczos sample and wave-space NUFFT sample (Sec. II B);
+         Lanczos on the whole mobility (Sec. IV's comparison method)
+poly     polydisperse spheres: the size-dependent shape factor of Sec. V
 precond  block-diagonal preconditioner network (forward/backward in FP64)
 
 Parity status of every function is pinned by ``tests/test_oracle_*.py``

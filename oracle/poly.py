@@ -32,6 +32,7 @@ interpolate from it, so Cov(u_i, u_j) carries sinc(k a_i) sinc(k a_j).
 from __future__ import annotations
 
 import dataclasses
+import functools
 import math
 
 import numpy as np
@@ -73,6 +74,11 @@ def _sinc(x):
     return np.where(x != 0, np.sin(xs) / xs, 1.0)
 
 
+@functools.lru_cache(maxsize=8)
+def _leggauss(nq):
+    return np.polynomial.legendre.leggauss(nq)
+
+
 def wave_free(r, xi, ai, aj, nq=400):
     """The H-weighted continuous k-integral (F, G), mobility units:
     F = (1/2pi^2) int H sinc(k ai) sinc(k aj) kF(kr) dk, G = (1/pi^2) int ... kG(kr) dk,
@@ -81,7 +87,7 @@ def wave_free(r, xi, ai, aj, nq=400):
     ai = np.broadcast_to(np.asarray(ai, dtype=np.float64), r.shape)
     aj = np.broadcast_to(np.asarray(aj, dtype=np.float64), r.shape)
     kmax = 16.0 * xi
-    t, w = np.polynomial.legendre.leggauss(nq)
+    t, w = _leggauss(nq)
     k = 0.5 * kmax * (t + 1.0)
     w = 0.5 * kmax * w
     base = rpy._H(k, xi)[None, :] * w[None, :] * _sinc(np.outer(ai, k)) * _sinc(np.outer(aj, k))
@@ -128,8 +134,9 @@ def mobility_real_dense(pos, radii, L, xi, rc):
         rh = ewald.unit(d[ii, jj])
         outer = rh[:, :, None] * rh[:, None, :]
         Mr[ii, :, jj, :] += F[:, None, None] * (np.eye(3)[None] - outer) + G[:, None, None] * outer
+    selfs = {a: self_real(xi, a) for a in np.unique(radii)}
     for i in range(N):
-        Mr[i, :, i, :] += self_real(xi, radii[i]) * np.eye(3)
+        Mr[i, :, i, :] += selfs[radii[i]] * np.eye(3)
     return Mr.reshape(3 * N, 3 * N)
 
 
@@ -185,7 +192,8 @@ class RealOperator:
         self.i, self.j = i, j
         self.rh = ewald.unit(d) if r.size else d
         self.F, self.GmF = F, G - F
-        self.self_ = np.array([self_real(plan_.xi, a) for a in radii])
+        uniq = np.unique(radii)
+        self.self_ = np.array([self_real(plan_.xi, a) for a in uniq])[np.searchsorted(uniq, radii)]
 
     def __call__(self, v):
         v = np.asarray(v, dtype=np.float64).reshape(self.N, 3)
