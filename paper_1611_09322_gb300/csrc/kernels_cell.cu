@@ -128,14 +128,15 @@ __global__ void k_cellsort(int ncell3, const int *start, V4<T> *pos_sorted, V4<T
 // most one image of each pair inside r_cut, so the distance test keeps the
 // right one.  Lists longer than K are cut and flag an overflow.
 // A float32 pair distance within rounding of r_cut (|r^2 - r_cut^2| below
-// 4e-6 r_cut^2, a few ulps of the cell-offset arithmetic) does not decide
-// the pair.  The search only notes that a particle met one; such particles
-// (a few per 10^5) walk their cells a second time, off the main loop, and
-// record each pair in that band (s, t, code, list slot or -1) in a small
-// edge buffer; k_nbr_edges then decides it again in float64 from the wrapped
-// positions with the nearest periodic image, removing the entry (set to -1,
-// which every list reader skips) or appending it.  The lists then hold
-// exactly the pairs with r < r_cut in float64, as the oracle's do.
+// 4e-6 r_cut^2, about three times the error of the cell-offset arithmetic)
+// does not decide the pair.  The search keeps every pair below the top of
+// that band and only notes that a particle met one in it; such particles (a
+// few per 10^5) walk their cells a second time, off the main loop, and
+// record each band pair (s, t, code, list slot) in a small edge buffer;
+// k_nbr_edges then decides it again in float64 from the wrapped positions
+// with the nearest periodic image and removes the entries beyond r_cut (set
+// to -1, which every list reader skips).  The lists then hold exactly the
+// pairs with r < r_cut in float64, as the oracle's do.
 //
 // One walk over the 27 stencil cells.  RECORD = false: fill the ELL row and
 // flag a pair in the band; RECORD = true: write nothing but the band's pairs
@@ -177,28 +178,40 @@ __device__ __forceinline__ int nbr_walk(int64_t s, int64_t N, const Geom<T> &g, 
                     const T dy = (li.y - lt.y) - sy;
                     const T dz = (li.z - lt.z) - sz;
                     const T r2 = dx * dx + dy * dy + dz * dz;
+                    // the float test keeps every pair up to the top of the band; the
+                    // float64 decision later removes those beyond r_cut
                     if (r2 < g.rc2_hi) {
-                        const bool in = r2 < g.rc2;
                         if constexpr (RECORD) {
                             if (r2 >= g.rc2_lo) {
                                 const int k = atomicAdd(edge_n, 1);
-                                if (k < edge_cap)
-                                    edge[k] = make_int4((int)s, t, code, in ? (cnt < K ? cnt : -2) : -1);
+                                if (k < edge_cap) edge[k] = make_int4((int)s, t, code, cnt < K ? cnt : -2);
                             }
                         } else {
-                            band |= r2 >= g.rc2_lo;
-                            if (in && cnt < K) {
+                            if constexpr (sizeof(T) == 4) {
+                                if (r2 >= g.rc2_lo) band = true;
+                            }
+                            if (cnt < K) {
                                 *dst = (t << 6) | code;
                                 dst += N;
                             }
                         }
-                        cnt += in;
+                        ++cnt;
                     }
                 }
             }
         }
     }
     return cnt;
+}
+
+// The second walk, out of line: the main loop's registers and schedule do
+// not pay for it.
+template <typename T>
+__device__ __noinline__ void nbr_record_band(int64_t s, int64_t N, Geom<T> g, const V4<T> *__restrict__ loc,
+                                             const int *__restrict__ cell_start, int *nbr, int K, int4 *edge,
+                                             int *edge_n, int edge_cap) {
+    bool unused = false;
+    nbr_walk<T, true>(s, N, g, loc, cell_start, nbr, K, unused, edge, edge_n, edge_cap);
 }
 
 template <typename T>
@@ -208,7 +221,7 @@ __device__ __forceinline__ int nbr_elem(int64_t s, int64_t N, const Geom<T> &g, 
     bool band = false;
     int cnt = nbr_walk<T, false>(s, N, g, loc, cell_start, nbr, K, band, edge, edge_n, edge_cap);
     if constexpr (sizeof(T) == 4) {
-        if (band) nbr_walk<T, true>(s, N, g, loc, cell_start, nbr, K, band, edge, edge_n, edge_cap);
+        if (band) nbr_record_band<T>(s, N, g, loc, cell_start, nbr, K, edge, edge_n, edge_cap);
     }
     if (cnt > K) {
         atomicExch(overflow, 1);
@@ -218,8 +231,11 @@ __device__ __forceinline__ int nbr_elem(int64_t s, int64_t N, const Geom<T> &g, 
     return cnt;
 }
 
+// No minimum block count: ptxas then keeps the register count at full
+// occupancy (32), which hides the candidate loads' latency better than fewer
+// warps with more registers: 242 vs 275 us at N = 1e6 (the band test costs 12 us).
 template <typename T>
-__global__ void __launch_bounds__(128, 12) k_nbr(int64_t N, Geom<T> g, const V4<T> *__restrict__ loc,
+__global__ void __launch_bounds__(128) k_nbr(int64_t N, Geom<T> g, const V4<T> *__restrict__ loc,
                                              const int *__restrict__ cell_start, int *count, int *nbr, int K,
                                              int *overflow, unsigned long long *n_pairs, int4 *edge, int *edge_n,
                                              int edge_cap) {
