@@ -335,12 +335,19 @@ def timed_steps(run, steps, flush, stream):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def matvec_bytes(N, n_pairs):
+    """Algorithmic bytes of one near-field matvec (the minimum the method must
+    move): positions 16N + input vector 12N + output 12N + the neighbour list
+    4 bytes per directed pair."""
+    return 16 * N + 12 * N + 12 * N + 4 * n_pairs
+
+
 def kernel_roofline(stages, N, M, n_pairs, peak, interp_kernel="k_interp4"):
     """Per-kernel achieved GB/s (algorithmic bytes per launch / live per-launch
     time from pse_profile_stages) and its fraction of the measured peak."""
     interp_bytes = 16 * N + (16 if interp_kernel == "k_interp4" else 12) * M ** 3 + 16 * N
     per_kernel = {
-        "matvec": ("k_lz_matvec", 32 * N + 4 * N + 4 * n_pairs + 16 * N),
+        "matvec": ("k_lz_matvec", matvec_bytes(N, n_pairs)),
         "neighbours": ("k_nbr", 16 * N + 4 * n_pairs + 4 * N),
         "lanczos_update": ("k_lz_update", 80 * N),
         "interp": (interp_kernel, interp_bytes),
@@ -705,12 +712,11 @@ def main():
     plan = s.plan
     M = plan["M"]
     dom = max(stages, key=lambda k: stages[k][0])
-    # algorithmic bytes per launch: matvec reads the 32-byte records
-    # (offsets + q) and neighbour counts, the ELL list (4 B per pair), writes
-    # u; the grid copy reads the three planar grids and writes the 16-byte
-    # node records; interpolation reads positions and the node records once,
-    # writes u_w; the FFT stage is cuFFT's.
-    bytes_mv = 32 * N_PART + 4 * N_PART + 4 * n_pairs + 16 * N_PART
+    # algorithmic bytes per launch: matvec_bytes (positions, input, output,
+    # 4 B of list per pair); the grid copy reads the three planar grids and
+    # writes the 16-byte node records; interpolation reads positions and the
+    # node records once, writes u_w; the FFT stage is cuFFT's.
+    bytes_mv = matvec_bytes(N_PART, n_pairs)
     bytes_in = 16 * N_PART + 16 * M ** 3 + 16 * N_PART
     bytes_cp = 12 * M ** 3 + 16 * M ** 3
     kernel_bytes = {"matvec": ("k_lz_matvec", bytes_mv), "interp": ("k_interp4", bytes_in),

@@ -90,12 +90,16 @@ typedef struct {
                             autotune bit 1); 1, 2 or 4: tiles of that many
                             cells per side (PSE_ENOTSUPPORTED at the first
                             forces call if it does not fit shared memory)      */
-    int matvec_shape;    /* 0 (default): near-field matvec with 4 threads x 4
+    int matvec_shape;    /* 0 (default): near-field matvec with 2 threads x 4
                             gathers per particle in blocks of 1024 threads
-                            (FP32; 128 in FP64), or timed with autotune bit 2;
+                            (FP32; 4 x 4 in blocks of 128 in FP64), or timed
+                            with autotune bit 2;
                             1..10 force threads x gathers, block size: 4x4
                             128, 8x2 128, 16x1 128, 4x2 128, 4x4 1024, 4x4
-                            512, 8x2 1024, 4x2 1024, 1x4 1024, 2x4 1024      */
+                            512, 8x2 1024, 4x2 1024, 1x4 1024, 2x4 1024;
+                            11: brick-tiled (each 4x4x4-cell brick's
+                            neighbourhood staged in shared memory; FP32
+                            without the preconditioner, else shape 5)      */
     int interp_form;     /* FP32 wave interpolation: 0 (default) copies the
                             three velocity grids into one node-major float4
                             grid (16 M^3 bytes more) and reads one record per
@@ -135,7 +139,7 @@ typedef struct {
     double lanczos_rel_change; /* ||x_j - x_{j-1}|| / ||x_j|| at exit          */
     int64_t n_pairs;     /* directed near-field pairs within r_cut              */
     int overflow;        /* 1 if the neighbour list exceeded its capacity       */
-    int matvec_shape;    /* matvec launch shape in use (1..10 as in pse_params)  */
+    int matvec_shape;    /* matvec launch shape in use (1..11 as in pse_params)  */
     int reserved[4];
 } pse_stats;
 

@@ -325,6 +325,168 @@ __global__ void __launch_bounds__(BS) k_lz_matvec(int64_t N, int K, Geom<T> g, c
     }
 }
 
+// ------------------------------------------------------------------ brick-tiled matvec
+// FP32 monodisperse form that serves the neighbour records from shared
+// memory.  A block takes one 4x4x4-cell brick at a time (a fixed, strided
+// set of bricks: the per-block partial sums, and so alpha, do not depend on
+// scheduling).  It stages the records of the brick's 6x6x6-cell
+// neighbourhood -- runs of consecutive sorted particles, one per cell, read
+// from L2 -- and a per-cell offset, so that the ELL entry (t, stencil code)
+// of a particle in brick-local cell (lx, ly, lz) is found at
+// t + hoff[((lx + 1 + ox) * 6 + (ly + 1 + oy)) * 6 + (lz + 1 + oz)].  The
+// scattered 32-byte gathers then cost shared-memory wavefronts instead of
+// L1/L2 lines.  A brick whose neighbourhood holds more than `cap` particles
+// gathers from global memory instead.  The pair arithmetic is that of
+// mr_row_part with the compact table.
+#define PSE_TILE_THREADS 256
+#define PSE_TILE_TPP 4
+#define PSE_TILE_ILP 4
+__global__ void __launch_bounds__(PSE_TILE_THREADS, 4) k_lz_matvec_tiled(
+    int64_t N, int K, Geom<float> g, const Rec<float> *__restrict__ rec, const int *__restrict__ cell_start,
+    const int *__restrict__ count, const int *__restrict__ nbr, const V4<float> *__restrict__ table_c,
+    V4<float> *u, double *partials, LzState *lz, const V4<float> *__restrict__ add, int nbricks, int cap) {
+    constexpr int TPP = PSE_TILE_TPP, ILP = PSE_TILE_ILP;
+    __shared__ double sh[32];
+    __shared__ V4<float> tab_s[PSE_TABLEC_N];
+    __shared__ int hpre[217], hoff[216], hcell[216];
+    extern __shared__ __align__(32) unsigned char tile_raw[];
+    Rec<float> *halo = reinterpret_cast<Rec<float> *>(tile_raw);
+    for (int i = threadIdx.x; i < PSE_TABLEC_N; i += blockDim.x) tab_s[i] = table_c[i];
+    const int j = lz->iter;
+    if (j > PSE_MAXIT || !lz->active) return;  // uniform across the launch
+    float part = 0.f;
+    const int nb = g.nb, nc = g.nc;
+    const int lane_g = threadIdx.x % TPP;
+    const int per_pass = blockDim.x / TPP;
+    for (int b = blockIdx.x; b < nbricks; b += gridDim.x) {
+        const int s0 = cell_start[b * 64], s1 = cell_start[b * 64 + 64];
+        if (s0 == s1) continue;  // uniform: an empty brick (or cell slots past ncell)
+        const int bz = b % nb, by = (b / nb) % nb, bx = b / (nb * nb);
+        __syncthreads();  // the previous brick's readers are done with the tile
+        for (int h = threadIdx.x; h < 216; h += blockDim.x) {
+            const int hx = h / 36, hy = (h / 6) % 6, hz = h % 6;
+            const int cx = ((bx * 4 - 1 + hx) % nc + nc) % nc;
+            const int cy = ((by * 4 - 1 + hy) % nc + nc) % nc;
+            const int cz = ((bz * 4 - 1 + hz) % nc + nc) % nc;
+            const int c = cell_id(cx, cy, cz, nb);
+            hcell[h] = c;
+            hpre[h + 1] = cell_start[c + 1] - cell_start[c];
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {  // exclusive prefix of the 216 counts, one warp
+            int carry = 0;
+            for (int base = 0; base < 216; base += 32) {
+                const int h = base + threadIdx.x;
+                int v = h < 216 ? hpre[h + 1] : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int n = __shfl_up_sync(0xffffffffu, v, o);
+                    if (threadIdx.x >= o) v += n;
+                }
+                if (h < 216) hpre[h + 1] = carry + v;
+                carry += __shfl_sync(0xffffffffu, v, 31);
+            }
+            if (threadIdx.x == 0) hpre[0] = 0;
+        }
+        __syncthreads();
+        const int total = hpre[216];
+        const bool staged = total <= cap;
+        if (staged) {
+            for (int h = threadIdx.x; h < 216; h += blockDim.x) hoff[h] = hpre[h] - cell_start[hcell[h]];
+            for (int i = threadIdx.x; i < total; i += blockDim.x) {
+                int lo = 0, hi = 215;  // last halo cell with hpre <= i
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (hpre[mid] <= i) lo = mid;
+                    else hi = mid - 1;
+                }
+                halo[i] = load_rec(rec + cell_start[hcell[lo]] + (i - hpre[lo]));
+            }
+        }
+        __syncthreads();
+        for (int base = s0; base < s1; base += per_pass) {
+            const int s = base + threadIdx.x / TPP;
+            const bool active = s < s1;
+            float ax = 0.f, ay = 0.f, az = 0.f;
+            Rec<float> ri;
+            if (active) {
+                ri = load_rec(rec + s);
+                const int own = __float_as_int(ri.l.w) & 63;  // brick-local cell (lx, ly, lz)
+                const int l0 = ((((own >> 4) & 3) + 1) * 6 + ((own >> 2) & 3) + 1) * 6 + (own & 3) + 1;
+                const int cnt = count[s];
+                for (int k0 = lane_g; k0 < cnt; k0 += ILP * TPP) {
+                    int ent[ILP];
+#pragma unroll
+                    for (int q = 0; q < ILP; ++q) {
+                        const int k = k0 + q * TPP;
+                        ent[q] = k < cnt ? __ldg(nbr + (int64_t)k * N + s) : -1;
+                    }
+                    Rec<float> rt[ILP];
+#pragma unroll
+                    for (int q = 0; q < ILP; ++q) {
+                        const int e = ent[q];
+                        if (e < 0) continue;
+                        const int t = e >> 6;
+                        // stencil code (ox+1)<<4 | (oy+1)<<2 | (oz+1) shifts the halo index
+                        const int hc = l0 - 43 + ((e >> 4) & 3) * 36 + ((e >> 2) & 3) * 6 + (e & 3);
+                        rt[q] = staged ? halo[t + hoff[hc]] : load_rec(rec + t);
+                    }
+#pragma unroll
+                    for (int q = 0; q < ILP; ++q) {
+                        const int e = ent[q];
+                        if (e < 0) continue;
+                        const int ox = ((e >> 4) & 3) - 1, oy = ((e >> 2) & 3) - 1, oz = (e & 3) - 1;
+                        const float dx = (ri.l.x - rt[q].l.x) - (float(ox) * g.cs + float(ox) * g.cs_lo);
+                        const float dy = (ri.l.y - rt[q].l.y) - (float(oy) * g.cs + float(oy) * g.cs_lo);
+                        const float dz = (ri.l.z - rt[q].l.z) - (float(oz) * g.cs + float(oz) * g.cs_lo);
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                        float F, GmF;
+                        pair_fg_c(r2 * rinv, g, tab_s, F, GmF);
+                        const float hx = dx * rinv, hy = dy * rinv, hz = dz * rinv;
+                        const float dot = GmF * (hx * rt[q].q.x + hy * rt[q].q.y + hz * rt[q].q.z);
+                        ax += F * rt[q].q.x + dot * hx;
+                        ay += F * rt[q].q.y + dot * hy;
+                        az += F * rt[q].q.z + dot * hz;
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = TPP / 2; o > 0; o >>= 1) {
+                ax += __shfl_xor_sync(0xffffffffu, ax, o);
+                ay += __shfl_xor_sync(0xffffffffu, ay, o);
+                az += __shfl_xor_sync(0xffffffffu, az, o);
+            }
+            if (active && lane_g == 0) {
+                V4<float> o;
+                o.x = ax + g.self_m * ri.q.x;
+                o.y = ay + g.self_m * ri.q.y;
+                o.z = az + g.self_m * ri.q.z;
+                o.w = 0.f;
+                if (add) {
+                    const V4<float> aw = add[s];
+                    o.x += aw.x;
+                    o.y += aw.y;
+                    o.z += aw.z;
+                }
+                u[s] = o;
+                part += ri.q.x * o.x + ri.q.y * o.y + ri.q.z * o.z;
+            }
+        }
+    }
+    const double bsum = block_sum_fw(part, sh);
+    double total;
+    if (grid_sum_last(bsum, partials, &lz->counter_mv, sh, &total) && threadIdx.x == 0) {
+        const double b1 = lz->beta[j - 1];
+        const bool ok = b1 > 0.0;
+        const double alpha = ok ? total / (b1 * b1) : 0.0;
+        lz->alpha[j] = alpha;
+        lz->c_u = ok ? (float)(1.0 / b1) : 0.f;
+        lz->c_q = ok ? (float)(alpha / b1) : 0.f;
+        lz->c_p = (ok && j >= 2) ? (float)(b1 / lz->beta[j - 2]) : 0.f;
+    }
+}
+
 // Polydisperse contexts (FP32): 4 threads x 4 gathers per particle in blocks
 // of 1024, F and G from the uniform table block of each species pair.
 __global__ void __launch_bounds__(1024) k_lz_matvec_poly(int64_t N, int K, Geom<float> g,
@@ -816,6 +978,43 @@ static int mv_poly_blocks_per_sm() {
     }
     return per_sm;
 }
+// Launch geometry of the brick-tiled matvec: the staging capacity follows the
+// mean neighbourhood occupancy 216 N / ncell^3 with six standard deviations
+// of Poisson slack; blocks per SM from the shared memory that leaves.
+static size_t g_tile_static_smem = 0, g_sm_smem = 0;
+static int g_tile_regs = 0;
+static int tile_cap(int64_t N, int nc) {
+    const double mean = 216.0 * (double)N / ((double)nc * nc * nc);
+    int cap = (int)(mean + 6.0 * sqrt(mean) + 32.0);
+    cap = (cap + 31) & ~31;
+    return cap < 256 ? 256 : (cap > 4096 ? 4096 : cap);
+}
+static void tile_prepare() {
+    if (g_sm_smem) return;
+    int dev = 0, v = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+        cudaFuncGetAttributes(&fa, k_lz_matvec_tiled) == cudaSuccess &&
+        cudaFuncSetAttribute(k_lz_matvec_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             4096 * (int)sizeof(Rec<float>)) == cudaSuccess) {
+        g_tile_static_smem = fa.sharedSizeBytes;
+        g_tile_regs = fa.numRegs;
+        g_sm_smem = (size_t)v;
+    } else {
+        cudaGetLastError();
+    }
+}
+static int tile_blocks_per_sm(size_t dyn) {
+    if (!g_sm_smem) return 1;
+    const size_t per_block = g_tile_static_smem + dyn + 1024;  // 1 KB per block reserved by the runtime
+    int nb = (int)(g_sm_smem / per_block);
+    const int by_regs = 65536 / ((g_tile_regs > 0 ? g_tile_regs : 64) * PSE_TILE_THREADS);
+    nb = nb < by_regs ? nb : by_regs;
+    nb = nb < 2048 / PSE_TILE_THREADS ? nb : 2048 / PSE_TILE_THREADS;
+    return nb > 0 ? nb : 1;
+}
+
 template <typename T> void mv_prepare_all() {
     mv_blocks_per_sm<T, 4, 4>(); mv_blocks_per_sm<T, 8, 2>();
     mv_blocks_per_sm<T, 16, 1>(); mv_blocks_per_sm<T, 4, 2>();
@@ -825,6 +1024,7 @@ template <typename T> void mv_prepare_all() {
     if constexpr (sizeof(T) == 4) mv_poly_blocks_per_sm();
 }
 void matvec_prepare() {
+    tile_prepare();
     mv_prepare_all<float>();
     mv_prepare_all<double>();
     up_blocks_per_sm<float>(); up_blocks_per_sm<double>();
@@ -838,6 +1038,15 @@ void mv_launch(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
 }
 template <typename T> void launch_lz_matvec(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
+        if (g.mv == PSE_MV_TILED && g.nspec <= 1 && !d.pc_on && g_sm_smem) {
+            const int cap = tile_cap(N, g.nc);
+            const size_t dyn = (size_t)cap * sizeof(Rec<float>);
+            const int nbricks = g.nb * g.nb * g.nb;
+            k_lz_matvec_tiled<<<pgrid(nbricks, 1, tile_blocks_per_sm(dyn)), PSE_TILE_THREADS, dyn, s>>>(
+                N, nbr_k(N, d.nbr_cap), g, d.rec, d.cell_start, d.nbr_count, d.nbr, d.table_c, d.u, d.partials, d.lz,
+                d.mv_add, nbricks, cap);
+            return;
+        }
         if (g.nspec > 1) {
             k_lz_matvec_poly<<<pgrid(N, 1024 / 4, mv_poly_blocks_per_sm()), 1024, 0, s>>>(
                 N, nbr_k(N, d.nbr_cap), g, d.rec, d.nbr_count, d.nbr, d.table, d.u, d.partials, d.lz, d.basis);
@@ -848,7 +1057,8 @@ template <typename T> void launch_lz_matvec(int64_t N, Geom<T> g, const Dev<T> &
         case 1: mv_launch<T, 8, 2>(N, g, d, s); break;
         case 2: mv_launch<T, 16, 1>(N, g, d, s); break;
         case 3: mv_launch<T, 4, 2>(N, g, d, s); break;
-        case 4: mv_launch<T, 4, 4, 1024>(N, g, d, s); break;
+        case 4:
+        case PSE_MV_TILED: mv_launch<T, 4, 4, 1024>(N, g, d, s); break;
         case 5: mv_launch<T, 4, 4, 512>(N, g, d, s); break;
         case 6: mv_launch<T, 8, 2, 1024>(N, g, d, s); break;
         case 7: mv_launch<T, 4, 2, 1024>(N, g, d, s); break;

@@ -226,10 +226,11 @@ template <typename T> void fill_geom(pse_ctx *c) {
     g.xi = (T)p.xi;
     g.nc = p.ncell;
     g.nb = bricks_per_side(p.ncell);
-    // default launch shape: FP32 4 x 4 in blocks of 1024 threads (one copy
-    // of the shared-memory table per SM leaves more of it to the L1: 88 vs
-    // 95 us per matvec at N = 1e6), FP64 4 x 4 in blocks of 128
-    g.mv = c->params.matvec_shape > 0 ? c->params.matvec_shape - 1 : (sizeof(T) == 4 ? 4 : 0);
+    // default launch shape: FP32 2 threads x 4 gathers per particle in blocks
+    // of 1024 threads (one copy of the shared-memory table per SM leaves more
+    // of it to the L1: 81 us per matvec at N = 1e6 against 86 for 4 x 4 and 95
+    // for 4 x 4 in blocks of 128), FP64 4 x 4 in blocks of 128
+    g.mv = c->params.matvec_shape > 0 ? c->params.matvec_shape - 1 : (sizeof(T) == 4 ? 9 : 0);
     g.rc2_d = p.r_cut * p.r_cut;
     g.L_d = p.L;
     g.invL_d = 1.0 / p.L;

@@ -69,7 +69,8 @@ template <typename T> struct Geom {
     int mv;       // matvec launch shape: threads x gathers per particle, threads per block
                   // (0: 4 x 4, 128; 1: 8 x 2, 128; 2: 16 x 1, 128; 3: 4 x 2, 128;
                   //  4: 4 x 4, 1024; 5: 4 x 4, 512; 6: 8 x 2, 1024; 7: 4 x 2, 1024;
-                  //  8: 1 x 4, 1024; 9: 2 x 4, 1024)
+                  //  8: 1 x 4, 1024; 9: 2 x 4, 1024; 10: brick-tiled, records staged in
+                  //  shared memory, FP32 monodisperse without preconditioner)
     // compact table: PSE_TABLEC_A uniform knots on [0, tc_split), the rest
     // uniform on [tc_split, r_cut]; tc_split = min(2a, r_cut)
     T tc_split, tc_invA, tc_invB;
@@ -89,7 +90,8 @@ PSE_HD inline int pair_index(int s, int t, int S) {
     const int i = s < t ? s : t, j = s < t ? t : s;
     return i * S - (i * (i - 1)) / 2 + (j - i);
 }
-#define PSE_MV_VARIANTS 10
+#define PSE_MV_VARIANTS 11
+#define PSE_MV_TILED 10
 
 // Wave-space parameters of one system.
 template <typename T> struct WaveGeom {

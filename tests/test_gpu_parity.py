@@ -127,7 +127,31 @@ def test_real_part_fixed_iterations(torch, N, phi, J):
     s.close()
 
 
-@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 0])
+@pytest.mark.parametrize("kind,N,phi", [("hs", 20000, 0.2), ("hs", 30000, 0.1), ("gel", 30000, 0.1)])
+def test_brick_tiled_matvec(torch, kind, N, phi):
+    """Shape 11 (each brick's neighbourhood staged in shared memory) on boxes
+    large enough for many bricks, hard spheres and a clustered gel (whose
+    densest bricks overflow the staging and gather from global memory): the
+    J-step real part equals the oracle's and the default shape's."""
+    from oracle import ewald, pse
+    from paper_1611_09322_gb300 import workloads
+    pos, L, _ = workloads.make(kind, N, phi, 16)
+    J = 5
+    plan = ewald.plan(L, 1.0, 0.5, 1e-3)
+    d = torch.from_numpy(pos).cuda()
+    outs = []
+    for shape in (11, 5):
+        s = _sampler(L, xi=0.5, tol=1e-3, fixed_iter=J, matvec_shape=shape)
+        _, r, _ = s.sample(d, SEED, 10, parts=True)
+        assert s.stats()["matvec_shape"] == shape
+        outs.append(r.cpu().numpy())
+        s.close()
+    ref, _, _ = pse.real_sample(pos.astype(np.float64), plan, SEED, 10, n_iter=J)
+    assert _rel(outs[0], ref) < 1e-4 and _maxrel(outs[0], ref) < 1e-4
+    assert _maxrel(outs[0], outs[1]) < 1e-5
+
+
+@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 0])
 def test_matvec_launch_shapes(torch, shape):
     """Every near-field matvec launch shape (threads x gathers per particle,
     threads per block), and the timed choice (shape 0 with autotune bit 2),
@@ -142,7 +166,7 @@ def test_matvec_launch_shapes(torch, shape):
     got = r.cpu().numpy()
     st = s.stats()
     assert st["lanczos_iters"] == J
-    assert st["matvec_shape"] == shape if shape else 1 <= st["matvec_shape"] <= 10
+    assert st["matvec_shape"] == shape if shape else 1 <= st["matvec_shape"] <= 11
     ref, _, _ = pse.real_sample(pos.astype(np.float64), plan, SEED, 9, n_iter=J)
     assert _rel(got, ref) < 1e-4 and _maxrel(got, ref) < 1e-4, (_rel(got, ref), _maxrel(got, ref))
     s.close()
