@@ -596,72 +596,94 @@ __device__ __forceinline__ void lz_eig_body(LzState *lz, int max_iter, int fixed
     const int lane = threadIdx.x;
     if (!lz->active) return;  // this system has stopped (batched loop)
     const int k = lz->iter - 1;  // T_k is complete: alpha_k from the matvec, beta_k from the update
-    for (int i = lane; i < k; i += 32) {
-        d[i] = lz->alpha[i + 1];
-        e[i] = (i + 1 < k) ? lz->beta[i + 1] : 0.0;
-        for (int c = 0; c < k; ++c) Q[i][c] = (i == c) ? 1.0 : 0.0;
-    }
-    __syncwarp();
-    const double eps = 2.220446049250313e-16;
-    for (int l = 0; l < k; ++l) {
-        for (int sweep = 0; sweep < 60; ++sweep) {
-            int m = l;
-            for (; m < k - 1; ++m) {
-                const double dd = fabs(d[m]) + fabs(d[m + 1]);
-                if (fabs(e[m]) <= eps * dd) break;
+    // Every FP64 warp instruction costs many cycles of this GPU's FP64 pipe,
+    // active lanes or not, so T_1 and T_2 take closed forms: T_1^{1/2} e_1 =
+    // sqrt(alpha_1); for the SPD 2x2 T = [[a, b], [b, c]], T^{1/2} =
+    // (T + s I) / t with s = sqrt(det T), t = sqrt(tr T + 2 s) (Cayley-Hamilton),
+    // the same matrix the eigendecomposition gives, to rounding.
+    if (k <= 2) {
+        if (lane == 0) {
+            const double a = lz->alpha[1];
+            if (k == 1) {
+                y[0] = sqrt(fmax(a, 0.0));
+            } else {
+                const double c = lz->alpha[2], b = lz->beta[1];
+                const double sd = sqrt(fmax(fma(a, c, -b * b), 0.0)), t = sqrt(a + c + 2.0 * sd);
+                y[0] = (a + sd) / t;
+                y[1] = b / t;
             }
-            if (m == l) break;
-            // shift from the leading 2x2 block (entries are O(mobility), far
-            // from overflow, so plain square roots replace hypot)
-            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-            double r = sqrt(fma(g, g, 1.0));
-            g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
-            double s = 1.0, c = 1.0, p = 0.0;
-            int i = m - 1;
-            bool deflated = false;
-            for (; i >= l; --i) {
-                const double f = s * e[i], b = c * e[i];
-                r = sqrt(fma(f, f, g * g));
-                __syncwarp();
-                if (lane == 0) e[i + 1] = r;
-                __syncwarp();
-                if (r == 0.0) {
-                    if (lane == 0) { d[i + 1] -= p; e[m] = 0.0; }
-                    __syncwarp();
-                    deflated = true;
-                    break;
-                }
-                const double rinv = 1.0 / r;  // one division per rotation
-                s = f * rinv;
-                c = g * rinv;
-                g = d[i + 1] - p;
-                r = (d[i] - g) * s + 2.0 * c * b;
-                p = s * r;
-                __syncwarp();
-                if (lane == 0) d[i + 1] = g + p;
-                __syncwarp();
-                g = c * r - b;
-                for (int row = lane; row < k; row += 32) {
-                    const double qa = Q[row][i], qb = Q[row][i + 1];
-                    Q[row][i + 1] = s * qa + c * qb;
-                    Q[row][i] = c * qa - s * qb;
-                }
-                __syncwarp();
-            }
-            if (deflated && i >= l) continue;
-            __syncwarp();
-            if (lane == 0) { d[l] -= p; e[l] = g; e[m] = 0.0; }
-            __syncwarp();
         }
+        __syncwarp();
+    } else {
+        for (int i = lane; i < k; i += 32) {
+            d[i] = lz->alpha[i + 1];
+            e[i] = (i + 1 < k) ? lz->beta[i + 1] : 0.0;
+            for (int c = 0; c < k; ++c) Q[i][c] = (i == c) ? 1.0 : 0.0;
+        }
+        __syncwarp();
+        const double eps = 2.220446049250313e-16;
+        for (int l = 0; l < k; ++l) {
+            for (int sweep = 0; sweep < 60; ++sweep) {
+                int m = l;
+                for (; m < k - 1; ++m) {
+                    const double dd = fabs(d[m]) + fabs(d[m + 1]);
+                    if (fabs(e[m]) <= eps * dd) break;
+                }
+                if (m == l) break;
+                // shift from the leading 2x2 block (entries are O(mobility), far
+                // from overflow, so plain square roots replace hypot)
+                double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+                double r = sqrt(fma(g, g, 1.0));
+                g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
+                double s = 1.0, c = 1.0, p = 0.0;
+                int i = m - 1;
+                bool deflated = false;
+                for (; i >= l; --i) {
+                    const double f = s * e[i], b = c * e[i];
+                    r = sqrt(fma(f, f, g * g));
+                    __syncwarp();
+                    if (lane == 0) e[i + 1] = r;
+                    __syncwarp();
+                    if (r == 0.0) {
+                        if (lane == 0) { d[i + 1] -= p; e[m] = 0.0; }
+                        __syncwarp();
+                        deflated = true;
+                        break;
+                    }
+                    const double rinv = 1.0 / r;  // one division per rotation
+                    s = f * rinv;
+                    c = g * rinv;
+                    g = d[i + 1] - p;
+                    r = (d[i] - g) * s + 2.0 * c * b;
+                    p = s * r;
+                    __syncwarp();
+                    if (lane == 0) d[i + 1] = g + p;
+                    __syncwarp();
+                    g = c * r - b;
+                    for (int row = lane; row < k; row += 32) {
+                        const double qa = Q[row][i], qb = Q[row][i + 1];
+                        Q[row][i + 1] = s * qa + c * qb;
+                        Q[row][i] = c * qa - s * qb;
+                    }
+                    __syncwarp();
+                }
+                if (deflated && i >= l) continue;
+                __syncwarp();
+                if (lane == 0) { d[l] -= p; e[l] = g; e[m] = 0.0; }
+                __syncwarp();
+            }
+        }
+        __syncwarp();
+        // y = Q diag(sqrt(max(lambda, 0))) Q^T e_1, each square root taken once
+        for (int c = lane; c < k; c += 32) e[c] = sqrt(fmax(d[c], 0.0)) * Q[0][c];
+        __syncwarp();
+        for (int row = lane; row < k; row += 32) {
+            double acc = 0.0;
+            for (int c = 0; c < k; ++c) acc += Q[row][c] * e[c];
+            y[row] = acc;
+        }
+        __syncwarp();
     }
-    __syncwarp();
-    // y = Q diag(sqrt(max(lambda, 0))) Q^T e_1
-    for (int row = lane; row < k; row += 32) {
-        double acc = 0.0;
-        for (int c = 0; c < k; ++c) acc += Q[row][c] * sqrt(fmax(d[c], 0.0)) * Q[0][c];
-        y[row] = acc;
-    }
-    __syncwarp();
     double num = 0.0, den = 0.0;
     for (int row = lane; row < k; row += 32) {
         const double prev = (row < k - 1) ? lz->y[row] : 0.0;

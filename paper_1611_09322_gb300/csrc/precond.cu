@@ -42,10 +42,12 @@ __device__ void pc_features(int64_t N, int64_t s, const Geom<float> &g, const Re
     float t6[6] = {0, 0, 0, 0, 0, 0};
     float n25 = 0, n35 = 0, n45 = 0, nrc = 0, inv = 0;
     const float rc = sqrtf(g.rc2);
-    const int cnt = count[s];
-    for (int k = 0; k < cnt; ++k) {
+    const int slots = count[s];
+    int cnt = 0;  // neighbours, without the slots removed by the float64 decision at r_cut
+    for (int k = 0; k < slots; ++k) {
         const int e = __ldg(nbr + (int64_t)k * N + s);
-        if (e < 0) continue;  // a pair removed by the float64 decision at r_cut
+        if (e < 0) continue;
+        ++cnt;
         const int t = e >> 6;
         const int ox = ((e >> 4) & 3) - 1, oy = ((e >> 2) & 3) - 1, oz = (e & 3) - 1;
         const V4<float> lt = rec[t].l;
