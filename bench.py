@@ -483,8 +483,11 @@ def variants_learned_batched(dev, flush, stream, steps, xi, M):
     pos, L, _ = workloads.hard_spheres(N_PART, PHI, SEED_POS)
     d = torch.from_numpy(pos).to(dev)
     o = torch.empty_like(d)
-    for name, th in (("plain_N1e6", None), ("learned_N1e6", theta), ("learned_no_fallback_N1e6", theta_raw)):
-        s = Sampler(L, 1.0, xi=xi, tol=TOL, grid_M=M)
+    # list_free_N1e6: the plain sample with the list-free matvec (no
+    # neighbour list; every product walks the 27 stencil cells)
+    for name, th in (("plain_N1e6", None), ("learned_N1e6", theta), ("learned_no_fallback_N1e6", theta_raw),
+                     ("list_free_N1e6", None)):
+        s = Sampler(L, 1.0, xi=xi, tol=TOL, grid_M=M, matvec_shape=12 if name == "list_free_N1e6" else 0)
         if th is not None:
             s.precond_set_weights(th)
         for i in range(3):
@@ -493,7 +496,7 @@ def variants_learned_batched(dev, flush, stream, steps, xi, M):
         st = s.stats()
         out[name] = {"value": N_PART * steps / (sum(per) / 1e3), "ms_per_step": sum(per) / steps,
                      "lanczos_iters": st["lanczos_iters"], "converged": st["converged"],
-                     "preconditioner": "none" if name.startswith("plain") else
+                     "preconditioner": "none" if th is None and "learned" not in name else
                      ("network" if th is not None else "fallback P = I (no held-out iteration gain)")}
         s.close()
     # the forces path at the same workload: deterministic M F alone (the

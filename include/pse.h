@@ -99,7 +99,12 @@ typedef struct {
                             512, 8x2 1024, 4x2 1024, 1x4 1024, 2x4 1024;
                             11: brick-tiled (each 4x4x4-cell brick's
                             neighbourhood staged in shared memory; FP32
-                            without the preconditioner, else shape 5)      */
+                            without the preconditioner, else shape 5);
+                            12: list-free (one thread per particle walks
+                            its 27 stencil cells on every product; the
+                            sample builds no neighbour list and reports
+                            n_pairs 0; FP32 monodisperse without the
+                            preconditioner, else shape 1)                 */
     int interp_form;     /* FP32 wave interpolation: 0 (default) copies the
                             three velocity grids into one node-major float4
                             grid (16 M^3 bytes more) and reads one record per
@@ -139,7 +144,7 @@ typedef struct {
     double lanczos_rel_change; /* ||x_j - x_{j-1}|| / ||x_j|| at exit          */
     int64_t n_pairs;     /* directed near-field pairs within r_cut              */
     int overflow;        /* 1 if the neighbour list exceeded its capacity       */
-    int matvec_shape;    /* matvec launch shape in use (1..11 as in pse_params)  */
+    int matvec_shape;    /* matvec launch shape in use (1..12 as in pse_params)  */
     int reserved[4];
 } pse_stats;
 

@@ -253,14 +253,6 @@ __global__ void __launch_bounds__(128) k_nbr(int64_t N, Geom<T> g, const V4<T> *
 // r_cut (one block; a few per 10^5 particles).  Entry (s, t, code, slot):
 // slot >= 0 the float search stored the pair there, -2 it accepted it with a
 // full list, -1 it rejected it.  Clears the edge count for the next search.
-__device__ __forceinline__ bool pair_inside_f64(const V4<float> &a, const V4<float> &b, const Geom<float> &g) {
-    double dx = (double)a.x - (double)b.x, dy = (double)a.y - (double)b.y, dz = (double)a.z - (double)b.z;
-    dx -= g.L_d * rint(dx * g.invL_d);
-    dy -= g.L_d * rint(dy * g.invL_d);
-    dz -= g.L_d * rint(dz * g.invL_d);
-    return dx * dx + dy * dy + dz * dz < g.rc2_d;
-}
-
 __device__ __forceinline__ void nbr_edges_body(int64_t N, const Geom<float> &g, const V4<float> *__restrict__ pos,
                                                int *count, int *nbr, int K, int *overflow,
                                                unsigned long long *n_pairs, const int4 *edge, int *edge_n,

@@ -238,15 +238,80 @@ __device__ __forceinline__ void mr_row_part(int64_t N, int64_t s, int lane_g, bo
     }
 }
 
+// Row s of M_r q without the self term and without a neighbour list (FP32):
+// one thread walks the 27 stencil cells of its particle over the cell-sorted
+// records, which carry q beside the cell-local offsets.  A candidate is kept
+// by the neighbour search's own float32 test (below the top of the r_cut
+// band), and one inside the band by the float64 decision from the wrapped
+// positions, so the row sums exactly the pairs the neighbour list holds
+// (summation in stencil order).
+__device__ __forceinline__ void mr_row_nolist(int64_t s, bool active, const Geom<float> &g,
+                                              const Rec<float> *__restrict__ rec,
+                                              const int *__restrict__ cell_start,
+                                              const V4<float> *__restrict__ pos, const V4<float> *tab,
+                                              V4<float> &li, V4<float> &qi, float &ax, float &ay, float &az) {
+    ax = ay = az = 0.f;
+    if (!active) return;
+    const Rec<float> ri = load_rec(rec + s);
+    li = ri.l;
+    qi = ri.q;
+    const int c = (int)(w_bits_r(li.w) & PSE_CELL_MASK);
+    const int nc = g.nc;
+    int cx, cy, cz;
+    cell_xyz(c, g.nb, cx, cy, cz);
+    for (int ox = -1; ox <= 1; ++ox) {
+        int axc = cx + ox;
+        axc += axc < 0 ? nc : 0;
+        axc -= axc >= nc ? nc : 0;
+        const float sx = float(ox) * g.cs + float(ox) * g.cs_lo;
+        for (int oy = -1; oy <= 1; ++oy) {
+            int ayc = cy + oy;
+            ayc += ayc < 0 ? nc : 0;
+            ayc -= ayc >= nc ? nc : 0;
+            const float sy = float(oy) * g.cs + float(oy) * g.cs_lo;
+            for (int oz = -1; oz <= 1; ++oz) {
+                int azc = cz + oz;
+                azc += azc < 0 ? nc : 0;
+                azc -= azc >= nc ? nc : 0;
+                const float sz = float(oz) * g.cs + float(oz) * g.cs_lo;
+                const int c2 = cell_id(axc, ayc, azc, g.nb);
+                const int b = cell_start[c2], e = cell_start[c2 + 1];
+                const int self = (ox | oy | oz) == 0 ? (int)s : -1;
+                for (int t = b; t < e; ++t) {
+                    if (t == self) continue;
+                    const Rec<float> rt = load_rec(rec + t);
+                    const float dx = (li.x - rt.l.x) - sx;
+                    const float dy = (li.y - rt.l.y) - sy;
+                    const float dz = (li.z - rt.l.z) - sz;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 >= g.rc2_hi) continue;
+                    if (r2 >= g.rc2_lo && !pair_inside_f64(pos[s], pos[t], g)) continue;
+                    const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                    float F, GmF;
+                    pair_fg_c(r2 * rinv, g, tab, F, GmF);
+                    const float hx = dx * rinv, hy = dy * rinv, hz = dz * rinv;
+                    const float dot = GmF * (hx * rt.q.x + hy * rt.q.y + hz * rt.q.z);
+                    ax += F * rt.q.x + dot * hx;
+                    ay += F * rt.q.y + dot * hy;
+                    az += F * rt.q.z + dot * hz;
+                }
+            }
+        }
+    }
+}
+
 // Body of one Lanczos matvec over the nblk blocks of one system (bidx = this
-// block's index among them).
-template <typename T, int TPP, int ILP, bool CT, bool POLY = false>
+// block's index among them).  NOLIST: rows by mr_row_nolist (FP32, TPP 1),
+// which reads cell_start and the sorted positions instead of the list.
+template <typename T, int TPP, int ILP, bool CT, bool POLY = false, bool NOLIST = false>
 __device__ __forceinline__ void lz_matvec_body(int64_t N, int K, const Geom<T> &g, const Rec<T> *__restrict__ rec,
                                                const int *__restrict__ count, const int *__restrict__ nbr,
                                                const V4<T> *__restrict__ table, V4<T> *u, double *partials,
                                                LzState *lz, const float *__restrict__ pc,
                                                const V4<T> *__restrict__ basis, const V4<T> *__restrict__ add,
-                                               int bidx, int nblk, double *sh) {
+                                               int bidx, int nblk, double *sh,
+                                               const int *__restrict__ cell_start = nullptr,
+                                               const V4<T> *__restrict__ pos_sorted = nullptr) {
     const int j = lz->iter;
     if (j > PSE_MAXIT || !lz->active) return;  // uniform across the system's blocks
     typename Part<T>::type part = 0;
@@ -261,7 +326,12 @@ __device__ __forceinline__ void lz_matvec_body(int64_t N, int K, const Geom<T> &
         const bool active = s < end;
         V4<T> li, qi;
         T ax, ay, az;
-        mr_row_part<T, TPP, ILP, CT, POLY>(N, s, lane_g, active, K, g, rec, count, nbr, table, li, qi, ax, ay, az);
+        if constexpr (NOLIST) {
+            mr_row_nolist(s, active, g, rec, cell_start, pos_sorted, table, li, qi, ax, ay, az);
+        } else {
+            mr_row_part<T, TPP, ILP, CT, POLY>(N, s, lane_g, active, K, g, rec, count, nbr, table, li, qi, ax, ay,
+                                               az);
+        }
         if (active && lane_g == 0) {
             V4<T> o;
             const T self = POLY ? self_of(g, spec_of(li)) : g.self_m;
@@ -500,8 +570,24 @@ __global__ void __launch_bounds__(1024) k_lz_matvec_poly(int64_t N, int K, Geom<
                                              nullptr, blockIdx.x, gridDim.x, sh);
 }
 
+// List-free Lanczos matvec (FP32 monodisperse, no preconditioner): one
+// thread per particle in blocks of PSE_NOLIST_THREADS, compact table in
+// shared memory.  The sample then builds no neighbour list.
+__global__ void __launch_bounds__(PSE_NOLIST_THREADS) k_lz_matvec_nolist(
+    int64_t N, Geom<float> g, const Rec<float> *__restrict__ rec, const int *__restrict__ cell_start,
+    const V4<float> *__restrict__ pos_sorted, const V4<float> *__restrict__ table_c, V4<float> *u,
+    double *partials, LzState *lz, const V4<float> *__restrict__ add) {
+    __shared__ double sh[32];
+    __shared__ V4<float> tab_s[PSE_TABLEC_N];
+    for (int i = threadIdx.x; i < PSE_TABLEC_N; i += blockDim.x) tab_s[i] = table_c[i];
+    __syncthreads();
+    lz_matvec_body<float, 1, 1, true, false, true>(N, 0, g, rec, nullptr, nullptr, tab_s, u, partials, lz, nullptr,
+                                                   nullptr, add, blockIdx.x, gridDim.x, sh, cell_start, pos_sorted);
+}
+
 // Fused over the systems of a batch: block b works for system blk2sys[b].
-__global__ void __launch_bounds__(128) k_lz_matvec_batch(const LzSys *__restrict__ sys, const int *__restrict__ blk2sys) {
+__global__ void __launch_bounds__(PSE_BATCH_MV_THREADS) k_lz_matvec_batch(const LzSys *__restrict__ sys,
+                                                                          const int *__restrict__ blk2sys) {
     __shared__ double sh[32];
     __shared__ V4<float> tab_s[PSE_TABLEC_N];
     const LzSys &S = sys[blk2sys[blockIdx.x]];
@@ -972,7 +1058,8 @@ template <typename T, int TPP, int ILP, int BS = 128> int mv_blocks_per_sm() {
     }
     return per_sm;
 }
-int matvec_blocks_per_sm() { return mv_blocks_per_sm<float, 4, 4>(); }
+// the default FP32 shape, which the fused batch matvec shares
+int matvec_blocks_per_sm() { return mv_blocks_per_sm<float, PSE_BATCH_MV_TPP, 4, PSE_BATCH_MV_THREADS>(); }
 // the same for the Lanczos update (FP32 and FP64), at most 8 per SM
 template <typename T> int up_blocks_per_sm() {
     static int per_sm = 0;
@@ -993,6 +1080,20 @@ static int mv_poly_blocks_per_sm() {
     if (per_sm == 0) {
         int nb = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lz_matvec_poly, 1024, 0) != cudaSuccess || nb < 1) {
+            cudaGetLastError();
+            nb = 1;
+        }
+        per_sm = nb;
+    }
+    return per_sm;
+}
+static int mv_nolist_blocks_per_sm() {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lz_matvec_nolist, PSE_NOLIST_THREADS, 0) !=
+                cudaSuccess ||
+            nb < 1) {
             cudaGetLastError();
             nb = 1;
         }
@@ -1043,7 +1144,10 @@ template <typename T> void mv_prepare_all() {
     mv_blocks_per_sm<T, 4, 4, 1024>(); mv_blocks_per_sm<T, 4, 4, 512>();
     mv_blocks_per_sm<T, 8, 2, 1024>(); mv_blocks_per_sm<T, 4, 2, 1024>();
     mv_blocks_per_sm<T, 1, 4, 1024>(); mv_blocks_per_sm<T, 2, 4, 1024>();
-    if constexpr (sizeof(T) == 4) mv_poly_blocks_per_sm();
+    if constexpr (sizeof(T) == 4) {
+        mv_poly_blocks_per_sm();
+        mv_nolist_blocks_per_sm();
+    }
 }
 void matvec_prepare() {
     tile_prepare();
@@ -1067,6 +1171,11 @@ template <typename T> void launch_lz_matvec(int64_t N, Geom<T> g, const Dev<T> &
             k_lz_matvec_tiled<<<pgrid(nbricks, 1, tile_blocks_per_sm(dyn)), PSE_TILE_THREADS, dyn, s>>>(
                 N, nbr_k(N, d.nbr_cap), g, d.rec, d.cell_start, d.nbr_count, d.nbr, d.table_c, d.u, d.partials, d.lz,
                 d.mv_add, nbricks, cap);
+            return;
+        }
+        if (g.mv == PSE_MV_NOLIST && g.nspec <= 1 && !d.pc_on) {
+            k_lz_matvec_nolist<<<pgrid(N, PSE_NOLIST_THREADS, mv_nolist_blocks_per_sm()), PSE_NOLIST_THREADS, 0, s>>>(
+                N, g, d.rec, d.cell_start, d.pos_sorted, d.table_c, d.u, d.partials, d.lz, d.mv_add);
             return;
         }
         if (g.nspec > 1) {
@@ -1101,7 +1210,7 @@ void launch_batch_cond(LzState *const *lzs, int nsys, cudaGraphConditionalHandle
     k_batch_cond<<<1, 256, 0, s>>>(lzs, nsys, h, any_out);
 }
 void launch_lz_matvec_batch(const LzSys *sys, const int *blk2sys, int nblocks, cudaStream_t s) {
-    k_lz_matvec_batch<<<nblocks, 128, 0, s>>>(sys, blk2sys);
+    k_lz_matvec_batch<<<nblocks, PSE_BATCH_MV_THREADS, 0, s>>>(sys, blk2sys);
 }
 void launch_lz_update_batch(const LzSys *sys, const int *blk2sys, int nblocks, cudaStream_t s) {
     k_lz_update_batch<<<nblocks, 256, 0, s>>>(sys, blk2sys);

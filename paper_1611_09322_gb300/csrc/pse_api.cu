@@ -627,6 +627,13 @@ template <typename T> pse_status wave_branch(pse_ctx *c, int64_t N, cudaStream_t
 // list, preconditioner blocks and q_1.  The loop body is one Lanczos step
 // (matvec -> update -> eigen-solve of T_j, all on `sa`).  The
 // epilogue joins the wave branch and writes the output.
+// The list-free matvec (FP32 monodisperse sampling without preconditioner)
+// needs no neighbour list: the sample then builds none.
+template <typename T> bool nolist_sample(pse_ctx *c, int mode) {
+    const Geom<T> &g = geom<T>(c);
+    return sizeof(T) == 4 && mode == GM_SAMPLE && g.mv == PSE_MV_NOLIST && g.nspec <= 1 && !dev<T>(c).pc_on;
+}
+
 template <typename T> pse_status capture_pre(pse_ctx *c, int mode) {
     const int64_t N = c->N;
     Dev<T> &d = dev<T>(c);
@@ -640,7 +647,7 @@ template <typename T> pse_status capture_pre(pse_ctx *c, int mode) {
     cudaStreamWaitEvent(c->s_wave, c->ev[0], 0);
     const pse_status wst = wave_branch<T>(c, N, c->s_wave, mode);
     cudaEventRecord(c->ev[1], c->s_wave);
-    if (!gm_bd(mode)) launch_nbr<T>(N, geom<T>(c), d, s);
+    if (!gm_bd(mode) && !nolist_sample<T>(c, mode)) launch_nbr<T>(N, geom<T>(c), d, s);
     if (mode != GM_SAMPLE) {  // M_r F into udet (the records are overwritten by q_1 next)
         launch_gather_vec<T>(N, d.args, d, s);
         launch_matvec_sorted<T>(N, geom<T>(c), d, s);
@@ -1226,7 +1233,7 @@ pse_status create_impl(pse_ctx **out, double L, double a, const pse_params *p, i
     if (cudaGetDevice(&c->device) != cudaSuccess) { cudaGetLastError(); delete c; return PSE_ECUDA; }
     if (p->wave_noise < 0 || p->wave_noise > 1 ||
         !(p->spread_tile == 0 || p->spread_tile == 1 || p->spread_tile == 2 || p->spread_tile == 4) ||
-        p->matvec_shape < 0 || p->matvec_shape > PSE_MV_VARIANTS || p->interp_form < 0 || p->interp_form > 1 ||
+        p->matvec_shape < 0 || p->matvec_shape > PSE_MV_NOLIST + 1 || p->interp_form < 0 || p->interp_form > 1 ||
         p->wave_fft < 0 || p->wave_fft > 1) {
         delete c;
         return PSE_EINVAL;
@@ -2042,10 +2049,11 @@ extern "C" pse_status pse_batch_create(pse_batch **out, int nsys, const double *
 }
 
 // Descriptors and block tables of the fused loop kernels.  Each system gets
-// the block counts its own context would launch (one block per 32 particles
-// of the matvec, per 256 of the update, capped at 16 and 8 per SM), so its
-// reductions add the same partial sums in the same order and a batched
-// system's sample is bitwise that of a lone context.
+// the block counts its own context would launch with the default FP32
+// shapes (one block per 512 particles of the matvec, per 256 of the update,
+// capped at the resident blocks per SM), so its reductions add the same
+// partial sums in the same order and a batched system's sample is bitwise
+// that of a lone context in the default shape.
 static pse_status batch_descriptors(pse_batch *b) {
     const int S = (int)b->sys.size();
     const int64_t cap_mv = (int64_t)num_sms() * matvec_blocks_per_sm(),
@@ -2063,7 +2071,7 @@ static pse_status batch_descriptors(pse_batch *b) {
         d.N = N;
         d.K = nbr_k(N, c->df.nbr_cap);
         d.blk_mv = (int)blk_mv.size();
-        d.nblk_mv = blocks(128 / PSE_BATCH_MV_TPP, cap_mv);
+        d.nblk_mv = blocks(PSE_BATCH_MV_THREADS / PSE_BATCH_MV_TPP, cap_mv);
         d.blk_up = (int)blk_up.size();
         d.nblk_up = blocks(256, cap_up);
         blk_mv.insert(blk_mv.end(), d.nblk_mv, k);

@@ -70,7 +70,9 @@ template <typename T> struct Geom {
                   // (0: 4 x 4, 128; 1: 8 x 2, 128; 2: 16 x 1, 128; 3: 4 x 2, 128;
                   //  4: 4 x 4, 1024; 5: 4 x 4, 512; 6: 8 x 2, 1024; 7: 4 x 2, 1024;
                   //  8: 1 x 4, 1024; 9: 2 x 4, 1024; 10: brick-tiled, records staged in
-                  //  shared memory, FP32 monodisperse without preconditioner)
+                  //  shared memory, FP32 monodisperse without preconditioner;
+                  //  11: list-free, one thread per particle walking its 27 stencil
+                  //  cells, FP32 monodisperse without preconditioner)
     // compact table: PSE_TABLEC_A uniform knots on [0, tc_split), the rest
     // uniform on [tc_split, r_cut]; tc_split = min(2a, r_cut)
     T tc_split, tc_invA, tc_invB;
@@ -92,6 +94,19 @@ PSE_HD inline int pair_index(int s, int t, int S) {
 }
 #define PSE_MV_VARIANTS 11
 #define PSE_MV_TILED 10
+#define PSE_MV_NOLIST 11  // list-free matvec (not among the timed shapes)
+
+#ifdef __CUDACC__
+// The float64 r < r_cut decision for a pair whose float32 distance lies
+// within rounding of r_cut: wrapped positions, nearest periodic image.
+__device__ __forceinline__ bool pair_inside_f64(const V4<float> &a, const V4<float> &b, const Geom<float> &g) {
+    double dx = (double)a.x - (double)b.x, dy = (double)a.y - (double)b.y, dz = (double)a.z - (double)b.z;
+    dx -= g.L_d * rint(dx * g.invL_d);
+    dy -= g.L_d * rint(dy * g.invL_d);
+    dz -= g.L_d * rint(dz * g.invL_d);
+    return dx * dx + dy * dy + dz * dz < g.rc2_d;
+}
+#endif
 
 // Wave-space parameters of one system.
 template <typename T> struct WaveGeom {
@@ -411,7 +426,11 @@ struct LzSys {
     const float *pc;
     V4<float> *basis;
 };
-#define PSE_BATCH_MV_TPP 4
+// the fused batch matvec runs the default FP32 lone shape: 2 threads x 4
+// gathers per particle in blocks of 1024 threads
+#define PSE_BATCH_MV_TPP 2
+#define PSE_BATCH_MV_THREADS 1024
+#define PSE_NOLIST_THREADS 512  // threads per block of the list-free matvec
 
 // One system of a batch for the fused prologue / epilogue kernels (FP32):
 // sizes, geometry, buffers and, per fused kernel kind, the first block and

@@ -127,12 +127,15 @@ def test_real_part_fixed_iterations(torch, N, phi, J):
     s.close()
 
 
+@pytest.mark.parametrize("shape", [11, 12])
 @pytest.mark.parametrize("kind,N,phi", [("hs", 20000, 0.2), ("hs", 30000, 0.1), ("gel", 30000, 0.1)])
-def test_brick_tiled_matvec(torch, kind, N, phi):
-    """Shape 11 (each brick's neighbourhood staged in shared memory) on boxes
-    large enough for many bricks, hard spheres and a clustered gel (whose
-    densest bricks overflow the staging and gather from global memory): the
-    J-step real part equals the oracle's and the default shape's."""
+def test_brick_tiled_and_list_free_matvec(torch, kind, N, phi, shape):
+    """Shape 11 (each brick's neighbourhood staged in shared memory) and
+    shape 12 (no neighbour list: every product walks the 27 stencil cells) on
+    boxes large enough for many bricks, hard spheres and a clustered gel
+    (whose densest bricks overflow the staging and gather from global
+    memory): the J-step real part equals the oracle's and the default
+    shape's."""
     from oracle import ewald, pse
     from paper_1611_09322_gb300 import workloads
     pos, L, _ = workloads.make(kind, N, phi, 16)
@@ -140,10 +143,10 @@ def test_brick_tiled_matvec(torch, kind, N, phi):
     plan = ewald.plan(L, 1.0, 0.5, 1e-3)
     d = torch.from_numpy(pos).cuda()
     outs = []
-    for shape in (11, 5):
-        s = _sampler(L, xi=0.5, tol=1e-3, fixed_iter=J, matvec_shape=shape)
+    for sh in (shape, 5):
+        s = _sampler(L, xi=0.5, tol=1e-3, fixed_iter=J, matvec_shape=sh)
         _, r, _ = s.sample(d, SEED, 10, parts=True)
-        assert s.stats()["matvec_shape"] == shape
+        assert s.stats()["matvec_shape"] == sh
         outs.append(r.cpu().numpy())
         s.close()
     ref, _, _ = pse.real_sample(pos.astype(np.float64), plan, SEED, 10, n_iter=J)
@@ -151,7 +154,7 @@ def test_brick_tiled_matvec(torch, kind, N, phi):
     assert _maxrel(outs[0], outs[1]) < 1e-5
 
 
-@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 0])
+@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 0])
 def test_matvec_launch_shapes(torch, shape):
     """Every near-field matvec launch shape (threads x gathers per particle,
     threads per block), and the timed choice (shape 0 with autotune bit 2),
