@@ -141,6 +141,9 @@ __global__ void k_cellsort(int ncell3, const int *start, V4<T> *pos_sorted, V4<T
 // One walk over the 27 stencil cells.  RECORD = false: fill the ELL row and
 // flag a pair in the band; RECORD = true: write nothing but the band's pairs
 // to the edge buffer, with the list slot the first walk gave them.
+// The stencil shift is folded into the particle's own offset once per cell
+// row (d = (l_i - shift) - l_t; its rounding stays far inside the band), and
+// the self test runs only on candidates inside r_cut.
 template <typename T, bool RECORD>
 __device__ __forceinline__ int nbr_walk(int64_t s, int64_t N, const Geom<T> &g, const V4<T> *__restrict__ loc,
                                         const int *__restrict__ cell_start, int *nbr, int K, bool &band,
@@ -156,31 +159,30 @@ __device__ __forceinline__ int nbr_walk(int64_t s, int64_t N, const Geom<T> &g, 
         int ax = cx + ox;
         ax += ax < 0 ? nc : 0;
         ax -= ax >= nc ? nc : 0;
-        const T sx = T(ox) * g.cs + T(ox) * g.cs_lo;
+        const T px = li.x - (T(ox) * g.cs + T(ox) * g.cs_lo);
         for (int oy = -1; oy <= 1; ++oy) {
             int ay = cy + oy;
             ay += ay < 0 ? nc : 0;
             ay -= ay >= nc ? nc : 0;
-            const T sy = T(oy) * g.cs + T(oy) * g.cs_lo;
+            const T py = li.y - (T(oy) * g.cs + T(oy) * g.cs_lo);
             for (int oz = -1; oz <= 1; ++oz) {
                 int az = cz + oz;
                 az += az < 0 ? nc : 0;
                 az -= az >= nc ? nc : 0;
-                const T sz = T(oz) * g.cs + T(oz) * g.cs_lo;
+                const T pz = li.z - (T(oz) * g.cs + T(oz) * g.cs_lo);
                 const int code = ((ox + 1) << 4) | ((oy + 1) << 2) | (oz + 1);
                 const int c2 = cell_id(ax, ay, az, g.nb);
                 const int b = cell_start[c2], e = cell_start[c2 + 1];
                 const int self = code == 21 ? (int)s : -1;  // the particle itself, in its own cell
+#pragma unroll 2
                 for (int t = b; t < e; ++t) {
-                    if (t == self) continue;
                     const V4<T> lt = loc[t];
-                    const T dx = (li.x - lt.x) - sx;
-                    const T dy = (li.y - lt.y) - sy;
-                    const T dz = (li.z - lt.z) - sz;
+                    const T dx = px - lt.x, dy = py - lt.y, dz = pz - lt.z;
                     const T r2 = dx * dx + dy * dy + dz * dz;
                     // the float test keeps every pair up to the top of the band; the
-                    // float64 decision later removes those beyond r_cut
-                    if (r2 < g.rc2_hi) {
+                    // float64 decision later removes those beyond r_cut.  The
+                    // particle itself (r2 = 0) passes it and is dropped here.
+                    if (r2 < g.rc2_hi && t != self) {
                         if constexpr (RECORD) {
                             if (r2 >= g.rc2_lo) {
                                 const int k = atomicAdd(edge_n, 1);
@@ -231,11 +233,13 @@ __device__ __forceinline__ int nbr_elem(int64_t s, int64_t N, const Geom<T> &g, 
     return cnt;
 }
 
-// No minimum block count: ptxas then keeps the register count at full
-// occupancy (32), which hides the candidate loads' latency better than fewer
-// warps with more registers: 242 vs 275 us at N = 1e6 (the band test costs 12 us).
+// Blocks of 256 threads with no minimum block count, the candidate loop
+// unrolled twice: at N = 1e6 (phi = 0.1) 185 us, against 188 in blocks of
+// 128, 192 in blocks of 64, 190-202 us with a minimum of 10, 12 or 16 blocks
+// of 128 per SM, and 218-227 us unrolled 1, 3 or 4 times (ptxas' register
+// allocation and load scheduling decide it; all give the same lists).
 template <typename T>
-__global__ void __launch_bounds__(128) k_nbr(int64_t N, Geom<T> g, const V4<T> *__restrict__ loc,
+__global__ void __launch_bounds__(256) k_nbr(int64_t N, Geom<T> g, const V4<T> *__restrict__ loc,
                                              const int *__restrict__ cell_start, int *count, int *nbr, int K,
                                              int *overflow, unsigned long long *n_pairs, int4 *edge, int *edge_n,
                                              int edge_cap) {
@@ -490,7 +494,7 @@ template <typename T> void launch_cellsort(int ncell3, const Dev<T> &d, cudaStre
 }
 
 template <typename T> void launch_nbr(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
-    k_nbr<T><<<nblk(N, 128), 128, 0, s>>>(N, g, d.loc_sorted, d.cell_start, d.nbr_count, d.nbr,
+    k_nbr<T><<<nblk(N, 256), 256, 0, s>>>(N, g, d.loc_sorted, d.cell_start, d.nbr_count, d.nbr,
                                           nbr_k(N, d.nbr_cap), &d.lz->overflow, &d.lz->n_pairs, d.edge, d.edge_n,
                                           d.edge_cap);
     if constexpr (sizeof(T) == 4)
