@@ -675,10 +675,111 @@ __global__ void __launch_bounds__(256) k_lz_update_batch(const LzSys *__restrict
 // Loan, Sec. 8.3); every lane runs the scalar recurrences redundantly and
 // applies each plane rotation to its own rows of the eigenvector matrix.
 // Then y = Q diag(sqrt(lambda)) Q^T e_1.
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// T_k^{1/2} e_1 for a small SPD tridiagonal T_k (k <= KP, KP * KP <= 64) by
+// the coupled Newton-Schulz iteration for the matrix square root: with
+// A = T_k / c, where c = the Gershgorin bound >= lambda_max, Y_0 = A,
+// Z_0 = I and W_n = (3 I - Z_n Y_n) / 2, the iterates Y_{n+1} = Y_n W_n and
+// Z_{n+1} = W_n Z_n converge to A^{1/2} and A^{-1/2}; the residual
+// R_n = I - Z_n Y_n obeys R_{n+1} = (3 R_n^2 + R_n^3) / 4 and starts below
+// 1 - lambda_min / c < 1.  Only multiply-adds (no FP64 divisions or square
+// roots per step), the KP^2 entries spread over the warp's lanes; rows and
+// columns k..KP-1 are padded with the identity, which stays its own root.
+// Once max|R_n| < 1e-8 one more product gives Y to rounding (the next
+// residual is ~1e-16).  Writes y = c^{1/2} Y e_1 and returns true, or false
+// (y untouched) if the residual has not fallen below 1e-8 in 60 steps.
+template <int KP>
+__device__ bool tri_sqrt_e1_ns(int k, const double *alpha, const double *beta, double *y, double *sm) {
+    constexpr int NE = KP * KP, PER = (NE + 31) / 32;
+    double *Y = sm, *Z = sm + NE, *W = sm + 2 * NE;
+    const int lane = threadIdx.x;
+    double c = 0.0;
+    for (int i = lane; i < k; i += 32) {
+        const double r = alpha[i + 1] + (i > 0 ? fabs(beta[i]) : 0.0) + (i + 1 < k ? fabs(beta[i + 1]) : 0.0);
+        c = fmax(c, r);
+    }
+    c = warp_max_d(c);
+    if (!(c > 0.0)) return false;
+    const double ic = 1.0 / c;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int q = lane + 32 * u;
+        if (q < NE) {
+            const int i = q / KP, j = q % KP;
+            double a = i == j ? 1.0 : 0.0;
+            if (i < k && j < k) {
+                if (i == j) a = alpha[i + 1] * ic;
+                else if (i - j == 1 || j - i == 1) a = beta[i > j ? i : j] * ic;
+                else a = 0.0;
+            }
+            Y[q] = a;
+            Z[q] = i == j ? 1.0 : 0.0;
+        }
+    }
+    __syncwarp();
+    for (int it = 0; it < 60; ++it) {
+        double res = 0.0;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int q = lane + 32 * u;
+            if (q < NE) {
+                const int i = q / KP, j = q % KP;
+                double zy = 0.0;
+#pragma unroll
+                for (int l = 0; l < KP; ++l) zy = fma(Z[i * KP + l], Y[l * KP + j], zy);
+                const double r = (i == j ? 1.0 : 0.0) - zy;
+                res = fmax(res, fabs(r));
+                W[q] = 0.5 * ((i == j ? 3.0 : 0.0) - zy);
+            }
+        }
+        res = warp_max_d(res);
+        if (!(res < 1.0)) return false;  // diverging (not SPD) or NaN
+        __syncwarp();
+        const bool last = res < 1e-8;
+        double yn[PER], zn[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int q = lane + 32 * u;
+            yn[u] = zn[u] = 0.0;
+            if (q < NE) {
+                const int i = q / KP, j = q % KP;
+#pragma unroll
+                for (int l = 0; l < KP; ++l) {
+                    yn[u] = fma(Y[i * KP + l], W[l * KP + j], yn[u]);
+                    zn[u] = fma(W[i * KP + l], Z[l * KP + j], zn[u]);
+                }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int q = lane + 32 * u;
+            if (q < NE) {
+                Y[q] = yn[u];
+                Z[q] = zn[u];
+            }
+        }
+        __syncwarp();
+        if (last) {
+            const double sc = sqrt(c);
+            for (int i = lane; i < k; i += 32) y[i] = sc * Y[i * KP];
+            __syncwarp();
+            return true;
+        }
+    }
+    return false;
+}
+
 __device__ __forceinline__ void lz_eig_body(LzState *lz, int max_iter, int fixed_iter, double tol,
                                             cudaGraphConditionalHandle handle) {
     __shared__ double Q[PSE_MAXIT][PSE_MAXIT + 1];
     __shared__ double d[PSE_MAXIT + 1], e[PSE_MAXIT + 1], y[PSE_MAXIT + 1];
+    __shared__ double nsm[3 * 64];
     const int lane = threadIdx.x;
     if (!lz->active) return;  // this system has stopped (batched loop)
     const int k = lz->iter - 1;  // T_k is complete: alpha_k from the matvec, beta_k from the update
@@ -700,6 +801,10 @@ __device__ __forceinline__ void lz_eig_body(LzState *lz, int max_iter, int fixed
             }
         }
         __syncwarp();
+    } else if ((k <= 4 && tri_sqrt_e1_ns<4>(k, lz->alpha, lz->beta, y, nsm)) ||
+               (k > 4 && k <= 8 && tri_sqrt_e1_ns<8>(k, lz->alpha, lz->beta, y, nsm))) {
+        // T_3 .. T_8: multiply-add iteration (k_lz_eig's FP64 QL sweeps took
+        // ~20 and ~38 us for k = 3 and 4: divisions and square roots per rotation)
     } else {
         for (int i = lane; i < k; i += 32) {
             d[i] = lz->alpha[i + 1];
