@@ -50,19 +50,45 @@ __global__ void k_bin(int64_t N, const SampleArgs<T> *args, Geom<T> g, int *cell
     if (i < N) bin_elem<T>(i, args, g, cell_of, slot, count);
 }
 
+// Counting-sort scatter: slot start[c] + slot[i] gets the caller index i
+// (inside a cell the slots follow k_bin's atomics; the placement below makes
+// the order deterministic).
+__global__ void k_scatter(int64_t N, const int *__restrict__ cell_of, const int *__restrict__ slot,
+                          const int *__restrict__ start, int *perm) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < N) perm[start[cell_of[i]] + slot[i]] = (int)i;
+}
+
+template <typename T> __device__ __forceinline__ long long w_bits(T w) {
+    if constexpr (sizeof(T) == 4) return (long long)__float_as_int(w);
+    else return __double_as_longlong(w);
+}
+
+// Placement of counting-sort slot k: its particle i goes to position
+// b + rank in its cell [b, e), rank = the number of the cell's members with
+// a smaller caller index, so each cell is ordered by caller index whatever
+// the atomics did (one thread per particle, no serial per-cell sort).  The
+// position there gets the wrapped position (w = caller index bits), the
+// offsets from the cell corner (w = cell id, species in the high bits) and
+// the offsets half of the matvec record.
 template <typename T>
-__device__ __forceinline__ void scatter_elem(int64_t i, const SampleArgs<T> *args, const Geom<T> &g,
-                                             const int *cell_of, const int *slot, const int *start, V4<T> *pos_sorted,
-                                             V4<T> *loc_sorted) {
-    const T *p = args->pos + 3 * i;
-    const T x = wrap_box(p[0], g.L), y = wrap_box(p[1], g.L), z = wrap_box(p[2], g.L);
+__device__ __forceinline__ void place_elem(int64_t k, const SampleArgs<T> *args, const Geom<T> &g,
+                                           const int *__restrict__ cell_of, const int *__restrict__ start,
+                                           const int *__restrict__ perm, V4<T> *pos_sorted, V4<T> *loc_sorted,
+                                           Rec<T> *rec) {
+    const int i = perm[k];
     const int c = cell_of[i];
+    const int b = start[c], e = start[c + 1];
+    int rank = 0;
+    for (int t = b; t < e; ++t) rank += perm[t] < i;
+    const int64_t dst = b + rank;
+    const T *p = args->pos + 3 * (int64_t)i;
+    const T x = wrap_box(p[0], g.L), y = wrap_box(p[1], g.L), z = wrap_box(p[2], g.L);
     int cx, cy, cz;
     cell_xyz(c, g.nb, cx, cy, cz);
-    const int dst = start[c] + slot[i];
     V4<T> a;
     a.x = x; a.y = y; a.z = z;
-    if constexpr (sizeof(T) == 4) a.w = __int_as_float((int)i);
+    if constexpr (sizeof(T) == 4) a.w = __int_as_float(i);
     else a.w = __longlong_as_double((long long)i);
     pos_sorted[dst] = a;
     V4<T> l;
@@ -79,46 +105,16 @@ __device__ __forceinline__ void scatter_elem(int64_t i, const SampleArgs<T> *arg
     }
     if constexpr (sizeof(T) == 4) l.w = __int_as_float(cw);
     else l.w = __longlong_as_double((long long)cw);
-    loc_sorted[dst] = l;  // the per-cell sort copies the offsets into the matvec records
+    loc_sorted[dst] = l;
+    rec[dst].l = l;
 }
 
 template <typename T>
-__global__ void k_scatter(int64_t N, const SampleArgs<T> *args, Geom<T> g, const int *cell_of, const int *slot,
-                          const int *start, V4<T> *pos_sorted, V4<T> *loc_sorted) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < N) scatter_elem<T>(i, args, g, cell_of, slot, start, pos_sorted, loc_sorted);
-}
-
-template <typename T> __device__ __forceinline__ long long w_bits(T w) {
-    if constexpr (sizeof(T) == 4) return (long long)__float_as_int(w);
-    else return __double_as_longlong(w);
-}
-
-// Insertion sort of each cell's entries by caller index: makes the sorted
-// order, and every summation order downstream, independent of atomics.
-template <typename T>
-__device__ __forceinline__ void cellsort_cell(int c, const int *start, V4<T> *pos_sorted, V4<T> *loc_sorted,
-                                              Rec<T> *rec) {
-    const int b = start[c], e = start[c + 1];
-    for (int i = b + 1; i < e; ++i) {
-        const V4<T> pa = pos_sorted[i], la = loc_sorted[i];
-        const long long key = w_bits(pa.w);
-        int j = i - 1;
-        while (j >= b && w_bits(pos_sorted[j].w) > key) {
-            pos_sorted[j + 1] = pos_sorted[j];
-            loc_sorted[j + 1] = loc_sorted[j];
-            --j;
-        }
-        pos_sorted[j + 1] = pa;
-        loc_sorted[j + 1] = la;
-    }
-    for (int i = b; i < e; ++i) rec[i].l = loc_sorted[i];
-}
-
-template <typename T>
-__global__ void k_cellsort(int ncell3, const int *start, V4<T> *pos_sorted, V4<T> *loc_sorted, Rec<T> *rec) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < ncell3) cellsort_cell<T>(c, start, pos_sorted, loc_sorted, rec);
+__global__ void k_place(int64_t N, const SampleArgs<T> *args, Geom<T> g, const int *__restrict__ cell_of,
+                        const int *__restrict__ start, const int *__restrict__ perm, V4<T> *pos_sorted,
+                        V4<T> *loc_sorted, Rec<T> *rec) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < N) place_elem<T>(k, args, g, cell_of, start, perm, pos_sorted, loc_sorted, rec);
 }
 
 // One thread per sorted particle, one pass: every neighbour within r_cut over
@@ -352,14 +348,15 @@ __global__ void __launch_bounds__(1024) k_scan_batch(const BSys *__restrict__ sy
 __global__ void k_scatter_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
     PSE_BATCH_SYS(BK_SCATTER);
     for (int64_t i = lb * (int64_t)blockDim.x + threadIdx.x; i < S.N; i += stride)
-        scatter_elem<float>(i, S.d.args, S.g, S.d.cell_of, S.d.slot, S.d.cell_start, S.d.pos_sorted, S.d.loc_sorted);
+        S.d.perm[S.d.cell_start[S.d.cell_of[i]] + S.d.slot[i]] = (int)i;
 }
-__global__ void k_cellsort_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
+__global__ void k_place_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
     PSE_BATCH_SYS(BK_SORT);
-    for (int64_t c = lb * (int64_t)blockDim.x + threadIdx.x; c < S.nc3; c += stride)
-        cellsort_cell<float>((int)c, S.d.cell_start, S.d.pos_sorted, S.d.loc_sorted, S.d.rec);
+    for (int64_t k = lb * (int64_t)blockDim.x + threadIdx.x; k < S.N; k += stride)
+        place_elem<float>(k, S.d.args, S.g, S.d.cell_of, S.d.cell_start, S.d.perm, S.d.pos_sorted, S.d.loc_sorted,
+                          S.d.rec);
 }
-__global__ void __launch_bounds__(128, 8) k_nbr_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
+__global__ void __launch_bounds__(256) k_nbr_batch(const BSys *__restrict__ sys, const int *__restrict__ tab) {
     PSE_BATCH_SYS(BK_NBR);
     for (int64_t s0 = lb * (int64_t)blockDim.x; s0 < S.N; s0 += stride) {  // uniform per block
         const int64_t s = s0 + threadIdx.x;
@@ -381,7 +378,7 @@ void launch_batch_prologue_cells(const BSys *sys, int nsys, int *const *tab, con
     k_bin_batch<<<tab_blocks(nblk, BK_BIN), 256, 0, s>>>(sys, tab[BK_BIN]);
     k_scan_batch<<<nsys, 1024, 0, s>>>(sys);
     k_scatter_batch<<<tab_blocks(nblk, BK_SCATTER), 256, 0, s>>>(sys, tab[BK_SCATTER]);
-    k_cellsort_batch<<<tab_blocks(nblk, BK_SORT), 256, 0, s>>>(sys, tab[BK_SORT]);
+    k_place_batch<<<tab_blocks(nblk, BK_SORT), 256, 0, s>>>(sys, tab[BK_SORT]);
 }
 // one block per system for the float64 decisions at r_cut
 __global__ void __launch_bounds__(256) k_nbr_edges_batch(const BSys *__restrict__ sys) {
@@ -391,7 +388,7 @@ __global__ void __launch_bounds__(256) k_nbr_edges_batch(const BSys *__restrict_
 }
 
 void launch_batch_nbr(const BSys *sys, int nsys, int *const *tab, const int *nblk, cudaStream_t s) {
-    k_nbr_batch<<<tab_blocks(nblk, BK_NBR), 128, 0, s>>>(sys, tab[BK_NBR]);
+    k_nbr_batch<<<tab_blocks(nblk, BK_NBR), 256, 0, s>>>(sys, tab[BK_NBR]);
     k_nbr_edges_batch<<<nsys, 256, 0, s>>>(sys);
 }
 
@@ -484,13 +481,14 @@ void launch_bin(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d
 }
 
 template <typename T>
-void launch_scatter(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
-    k_scatter<T><<<nblk(N, 256), 256, 0, s>>>(N, args, g, d.cell_of, d.slot, d.cell_start, d.pos_sorted,
-                                              d.loc_sorted);
+void launch_scatter(int64_t N, const SampleArgs<T> *, Geom<T>, const Dev<T> &d, cudaStream_t s) {
+    k_scatter<<<nblk(N, 256), 256, 0, s>>>(N, d.cell_of, d.slot, d.cell_start, d.perm);
 }
 
-template <typename T> void launch_cellsort(int ncell3, const Dev<T> &d, cudaStream_t s) {
-    k_cellsort<T><<<nblk(ncell3, 256), 256, 0, s>>>(ncell3, d.cell_start, d.pos_sorted, d.loc_sorted, d.rec);
+template <typename T>
+void launch_place(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
+    k_place<T><<<nblk(N, 256), 256, 0, s>>>(N, args, g, d.cell_of, d.cell_start, d.perm, d.pos_sorted,
+                                            d.loc_sorted, d.rec);
 }
 
 template <typename T> void launch_nbr(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s) {
@@ -505,7 +503,7 @@ template <typename T> void launch_nbr(int64_t N, Geom<T> g, const Dev<T> &d, cud
 #define PSE_INST(T)                                                                                       \
     template void launch_bin<T>(int64_t, const SampleArgs<T> *, Geom<T>, const Dev<T> &, cudaStream_t);     \
     template void launch_scatter<T>(int64_t, const SampleArgs<T> *, Geom<T>, const Dev<T> &, cudaStream_t); \
-    template void launch_cellsort<T>(int, const Dev<T> &, cudaStream_t);                                  \
+    template void launch_place<T>(int64_t, const SampleArgs<T> *, Geom<T>, const Dev<T> &, cudaStream_t);   \
     template void launch_nbr<T>(int64_t, Geom<T>, const Dev<T> &, cudaStream_t);
 PSE_INST(float)
 PSE_INST(double)

@@ -29,6 +29,7 @@ struct NoAllocScratch {
     V4<float> table[PSE_TABLE_N];
     int cell_of[kNoAllocMaxN];
     int slot[kNoAllocMaxN];
+    int perm[kNoAllocMaxN];
     int nbr_count[kNoAllocMaxN];
     int cell_count[kNoAllocMaxCells];
     int cell_start[kNoAllocMaxCells + 1];
@@ -146,6 +147,7 @@ extern "C" pse_status pse_real_matvec_noalloc(double L, double a, double xi, dou
     d.loc_sorted = sc->loc_sorted;
     d.cell_of = sc->cell_of;
     d.slot = sc->slot;
+    d.perm = sc->perm;
     d.cell_count = sc->cell_count;
     d.cell_start = sc->cell_start;
     d.nbr_count = sc->nbr_count;
@@ -171,7 +173,7 @@ extern "C" pse_status pse_real_matvec_noalloc(double L, double a, double xi, dou
     }
     launch_bin<float>(N, d.args, g, d, s);  // clears the cell counts first
     launch_scatter<float>(N, d.args, g, d, s);
-    launch_cellsort<float>((int)nc3, d, s);
+    launch_place<float>(N, d.args, g, d, s);
     launch_nbr<float>(N, g, d, s);
     launch_matvec_caller<float>(N, d.args, g, d, s);
     // a launch that failed to start (configuration, resources) is reported

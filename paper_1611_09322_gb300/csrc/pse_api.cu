@@ -39,8 +39,9 @@ struct pse_ctx {
     int ncell3 = 0;
     cufftHandle fft = 0;
     bool fft_made = false;
-    cudaStream_t s_main = nullptr, s_wave = nullptr, s_body = nullptr;
+    cudaStream_t s_main = nullptr, s_wave = nullptr, s_body = nullptr, s_init = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};  // fork of the wave branch; its join
+    cudaEvent_t ev_init = nullptr;           // q_1 written beside the neighbour search
     cudaGraph_t graph[6] = {};            // per graph mode (GM_*)
     cudaGraphExec_t exec[6] = {};
     cudaGraphConditionalHandle cond[6] = {};
@@ -393,6 +394,8 @@ template <typename T> pse_status init_ctx(pse_ctx *c) {
     }
     CK(cudaStreamCreateWithPriority(&c->s_wave, cudaStreamNonBlocking, p_lo));
     CK(cudaStreamCreateWithPriority(&c->s_body, cudaStreamNonBlocking, p_hi));
+    CK(cudaStreamCreateWithPriority(&c->s_init, cudaStreamNonBlocking, p_hi));
+    CK(cudaEventCreateWithFlags(&c->ev_init, cudaEventDisableTiming));
     for (int i = 0; i < 2; ++i) CK(cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming));
     return PSE_OK;
 }
@@ -540,6 +543,7 @@ template <typename T> pse_status ensure(pse_ctx *c, int64_t N) {
     A(d.loc_sorted, sizeof(V4<T>) * N);
     A(d.cell_of, sizeof(int) * N);
     A(d.slot, sizeof(int) * N);
+    A(d.perm, sizeof(int) * N);
     A(d.cell_count, sizeof(int) * nc3);
     A(d.cell_start, sizeof(int) * (nc3 + 1));
     A(d.nbr_count, sizeof(int) * N);
@@ -573,7 +577,7 @@ template <typename T> void pre(pse_ctx *c, int64_t N, cudaStream_t s) {
     Dev<T> &d = dev<T>(c);
     launch_bin<T>(N, d.args, geom<T>(c), d, s);
     launch_scatter<T>(N, d.args, geom<T>(c), d, s);
-    launch_cellsort<T>(c->ncell3, d, s);
+    launch_place<T>(N, d.args, geom<T>(c), d, s);
     cudaMemsetAsync(&d.lz->overflow, 0, sizeof(int), s);
     cudaMemsetAsync(&d.lz->n_pairs, 0, sizeof(unsigned long long), s);
 }
@@ -671,12 +675,22 @@ template <typename T> pse_status capture_pre(pse_ctx *c, int mode) {
     if (!early) cudaStreamWaitEvent(c->s_wave, c->ev[0], 0);
     const pse_status wst = wave_branch<T>(c, N, c->s_wave, mode, early ? c->ev[0] : nullptr);
     cudaEventRecord(c->ev[1], c->s_wave);
+    // a plain sample's q_1 = z1 needs only the sorted order: it is drawn beside
+    // the neighbour search (which reads the offsets, not the records' q);
+    // with the preconditioner it needs the blocks, which need the list
+    const bool init_beside = mode == GM_SAMPLE && !c->pc_enabled;
+    if (init_beside) {
+        cudaStreamWaitEvent(c->s_init, c->ev[0], 0);
+        launch_lz_init<T>(N, d.args, c->params.system, d, c->s_init);
+        cudaEventRecord(c->ev_init, c->s_init);
+    }
     if (!gm_bd(mode) && !nolist_sample<T>(c, mode)) launch_nbr<T>(N, geom<T>(c), d, s);
     if (mode != GM_SAMPLE) {  // M_r F into udet (the records are overwritten by q_1 next)
         launch_gather_vec<T>(N, d.args, d, s);
         launch_matvec_sorted<T>(N, geom<T>(c), d, s);
     }
-    if (gm_noise(mode)) real_setup<T>(c, N, s);
+    if (init_beside) cudaStreamWaitEvent(s, c->ev_init, 0);
+    else if (gm_noise(mode)) real_setup<T>(c, N, s);
     return wst;
 }
 
@@ -1359,7 +1373,7 @@ void pse_destroy(pse_ctx *c) {
     if (c->sp_scratch) cudaFree(c->sp_scratch);
     free_list(c->per_n);
     free_list(c->per_ctx);
-    cudaStream_t ss[5] = {c->s_main, c->s_wave, c->s_body, c->s_copy, c->s_back};
+    cudaStream_t ss[6] = {c->s_main, c->s_wave, c->s_body, c->s_copy, c->s_back, c->s_init};
     for (cudaStream_t s : ss) if (s) cudaStreamDestroy(s);
     for (int b = 0; b < 2; ++b) {
         if (c->ev_in[b]) cudaEventDestroy(c->ev_in[b]);
@@ -1370,6 +1384,7 @@ void pse_destroy(pse_ctx *c) {
         if (c->ev_args[k]) cudaEventDestroy(c->ev_args[k]);
     if (c->args_ring) cudaFreeHost(c->args_ring);
     for (cudaEvent_t e : c->ev) if (e) cudaEventDestroy(e);
+    if (c->ev_init) cudaEventDestroy(c->ev_init);
     delete c;
 }
 
@@ -1526,7 +1541,7 @@ pse_status pse_profile_stages(pse_ctx *c, int64_t N, const float *d_pos, uint64_
     if (r == PSE_OK) r = timed(PSE_STAGE_CELLS, 1 + nscan, [&] { launch_bin<float>(N, d.args, c->gf, d, s); return PSE_OK; });
     if (r == PSE_OK) r = timed(PSE_STAGE_SORT, 2, [&] {
         launch_scatter<float>(N, d.args, c->gf, d, s);
-        launch_cellsort<float>(c->ncell3, d, s);
+        launch_place<float>(N, d.args, c->gf, d, s);
         cudaMemsetAsync(&d.lz->overflow, 0, sizeof(int), s);
         cudaMemsetAsync(&d.lz->n_pairs, 0, sizeof(unsigned long long), s);
         return PSE_OK; });
@@ -2157,8 +2172,8 @@ static pse_status batch_descriptors(pse_batch *b) {
             (d.nc3 + 255) / 256,                               // zero
             (d.N + 255) / 256,                                 // bin
             (d.N + 255) / 256,                                 // scatter
-            (d.nc3 + 255) / 256,                               // cell sort
-            (d.N + 127) / 128,                                 // neighbours
+            (d.N + 255) / 256,                                 // placement in cell order
+            (d.N + 255) / 256,                                 // neighbours
             0,                                                 // init (set below)
             (modes + 255) / 256,                               // noise
             b->p4 ? (d.N + 4 * (32 / b->p4) - 1) / (4 * (32 / b->p4))  // interpolation: 4 warps of

@@ -343,6 +343,7 @@ template <typename T> struct Dev {
     V4<T> *loc_sorted;   // offsets from the cell corner, w = cell id (int bits)
     int *cell_of;        // per caller particle
     int *slot;           // per caller particle
+    int *perm;           // counting-sort slot -> caller index
     int *cell_count;     // ncell^3
     int *cell_start;     // ncell^3 + 1
     int *nbr_count;      // N: neighbours of each sorted particle
@@ -385,7 +386,8 @@ template <typename T> void launch_bin(int64_t N, const SampleArgs<T> *args, Geom
 void launch_scan(const int *in, int *out, int64_t n, int *sums, cudaStream_t s);
 template <typename T> void launch_scatter(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d,
                                           cudaStream_t s);
-template <typename T> void launch_cellsort(int ncell3, const Dev<T> &d, cudaStream_t s);
+template <typename T>
+void launch_place(int64_t N, const SampleArgs<T> *args, Geom<T> g, const Dev<T> &d, cudaStream_t s);
 template <typename T> void launch_nbr(int64_t N, Geom<T> g, const Dev<T> &d, cudaStream_t s);
 
 inline int nbr_k(int64_t N, int64_t cap) {
