@@ -177,10 +177,11 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def _oracle_sample_times(n, xi, reps, seed0=0):
+def _oracle_sample_times(n, xi, reps, seed0=0, keep=None):
     """Wall and CPU seconds of `reps` FP64 oracle PSE samples (real Lanczos
     part + gridded wave part) of an n-particle box at the headline's density
-    and parameters; the configuration is generated outside the timing."""
+    and parameters; the configuration is generated outside the timing.  With
+    a dict `keep`, the first sample, its configuration and seeds go there."""
     import resource
     import numpy as np
     from oracle import ewald, pse
@@ -198,6 +199,8 @@ def _oracle_sample_times(n, xi, reps, seed0=0):
         r1 = resource.getrusage(resource.RUSAGE_SELF)
         cpus.append(r1.ru_utime - r0.ru_utime + r1.ru_stime - r0.ru_stime)
         js.append(j)
+        if keep is not None and r == 0:
+            keep.update(pos=pos, L=L, u=ur + uw, J=j, M=plan.M, seed=7, sample=seed0)
     return walls, cpus, js, plan.M
 
 
@@ -213,14 +216,58 @@ def _quartiles(x):
     return q[0], statistics.median(x), q[2]
 
 
-def cpu_baseline(xi=XI_TUNED, n=CPU_SAMPLE_N, reps=3, one_thread=True):
+def accuracy(first, xi):
+    """Measured errors of the CUDA path, computed in the oracle leg: (1) the
+    FP32 GPU sample of the first timed oracle sample's configuration, seeds
+    and Lanczos count against that FP64 oracle sample, element by element;
+    (2) what tol buys: the GPU sample (stop rule at tol) of N = 64 hard
+    spheres at phi = 0.1 against the exact split sample -- M_r^{1/2} z1 by
+    dense eigendecomposition of the all-image near-field mobility at the same
+    r_cut, plus the wave part summed directly over modes with the same noise
+    -- relative 2-norms (the wave part's error is the quadrature error of the
+    paper's parameter rule, several times tol)."""
+    import numpy as np
+    import torch
+    from oracle import ewald, pse
+    from paper_1611_09322_gb300 import Sampler, workloads
+    out = {}
+    if first:
+        s = Sampler(first["L"], 1.0, xi=xi, tol=TOL, grid_M=first["M"], fixed_iter=first["J"])
+        u = s.sample(torch.from_numpy(first["pos"]).cuda(), first["seed"], first["sample"]).cpu().numpy()
+        s.close()
+        ref = first["u"]
+        out["gpu_fp32_vs_fp64_oracle"] = {
+            "N": int(first["pos"].shape[0]), "J": int(first["J"]), "M": int(first["M"]),
+            "rel": float(np.linalg.norm(u - ref) / np.linalg.norm(ref)),
+            "maxrel": float(np.abs(u - ref).max() / np.abs(ref).max())}
+    N, phi, xi64, seed, sample = 64, 0.1, 0.5, 13579, 5
+    pos, L, _ = workloads.hard_spheres(N, phi, 17)
+    p64 = pos.astype(np.float64)
+    plan = ewald.plan(L, 1.0, xi64, TOL)
+    s = Sampler(L, 1.0, xi=xi64, tol=TOL)
+    _, r, w = s.sample(torch.from_numpy(pos).cuda(), seed, sample, parts=True)
+    J = s.stats()["lanczos_iters"]
+    s.close()
+    r, w = r.cpu().numpy().astype(np.float64), w.cpu().numpy().astype(np.float64)
+    lam, Q = np.linalg.eigh(ewald.mobility_real_dense(p64, L, 1.0, xi64, plan.r_cut))
+    z1 = pse.real_noise(N, seed, sample).ravel()
+    ur = (Q @ (np.sqrt(np.maximum(lam, 0.0)) * (Q.T @ z1))).reshape(N, 3)
+    uw = pse.wave_sample_direct(p64, plan, seed, sample)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))  # noqa: E731
+    out["method_vs_exact_split_sample"] = {"N": N, "phi": phi, "xi": xi64, "tol": TOL, "J": int(J),
+                                            "rel": rel(r + w, ur + uw), "rel_real": rel(r, ur),
+                                            "rel_wave": rel(w, uw)}
+    return out
+
+
+def cpu_baseline(xi=XI_TUNED, n=CPU_SAMPLE_N, reps=3, one_thread=True, keep=None):
     """The FP64 oracle as it stands, on a bounded sample of the headline
     workload: `reps` samples of an n-particle box at the same density, xi and
     tol (median and interquartile range of particle-samples/s), on the host's
     cores as the oracle uses them (`cores` = CPU time / wall time, the
     threads it actually kept busy), plus one sample in a subprocess limited
     to one thread."""
-    walls, cpus, js, M = _oracle_sample_times(n, xi, reps)
+    walls, cpus, js, M = _oracle_sample_times(n, xi, reps, keep=keep)
     rates = [n / w for w in walls]
     q1, med, q3 = _quartiles(rates)
     busy = sum(cpus) / sum(walls)
@@ -777,7 +824,12 @@ def main():
             line["variants"].update(variants_poly(dev, flush, stream, max(20, args.steps // 4)))
             line["variants"].update(variants_configs(dev, flush, stream, 10, peak))
         if not args.no_cpu_baseline and ws == 1:
-            line["cpu_baseline"] = cpu_baseline(xi)
+            first = {}
+            line["cpu_baseline"] = cpu_baseline(xi, keep=first)
+            try:
+                line["accuracy"] = accuracy(first, xi)
+            except Exception as e:  # the throughput line stands without it
+                line["accuracy"] = {"unavailable": str(e)[:200]}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
