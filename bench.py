@@ -806,7 +806,9 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-                "ms_per_step_median": statistics.median(per), "higher_is_better": True, "scaling": "weak",
+                "ms_per_step_median": statistics.median(per),
+                "ms_per_step_iqr": [round(q, 5) for q in _quartiles(per)[0::2]],
+                "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(plan, tuning), "lanczos_iters": J, "n_pairs": n_pairs,
                 "variant": "plain PSE, one system, one CUDA graph per sample",
