@@ -415,15 +415,16 @@ def kernel_roofline(stages, N, M, n_pairs, peak, interp_kernel="k_interp4"):
 
 
 def variants_configs(dev, flush, stream, steps, peak):
-    """The other workloads at full size: N = 4e6 hard spheres at phi = 0.3 (tol
-    1e-3 and 1e-5) and the 2.5e5 fractal gels (phi = 0.05, 0.1), each at the
+    """The other workloads at full size: N = 1e6 hard spheres at phi = 0.3
+    (tol 1e-3), N = 4e6 at phi = 0.3 (tol 1e-3 and 1e-5) and the 2.5e5 fractal gels (phi = 0.05, 0.1), each at the
     xi and grid of its own timed scan, plain vs learned preconditioner (network
     trained on the GPU at that xi and tol): throughput, Lanczos counts and the
     per-kernel roofline."""
     import torch
     from paper_1611_09322_gb300 import Sampler, precond_train, pse_tune_xi, workloads
     out = {}
-    cases = [("hs_4e6_phi0.3", "hs", 4_000_000, 0.3, 4, 3.0, tol) for tol in (1e-3, 1e-5)]
+    cases = [("hs_1e6_phi0.3", "hs", 1_000_000, 0.3, 5, 3.0, 1e-3)]  # the headline N at config 5's density
+    cases += [("hs_4e6_phi0.3", "hs", 4_000_000, 0.3, 4, 3.0, tol) for tol in (1e-3, 1e-5)]
     cases += [(f"gel_2.5e5_phi{phi:g}", "gel", 250_000, phi, 3, 2.0, 1e-3) for phi in (0.05, 0.1)]
     cache = {}
     for name, kind, N, phi, seed, d_f, tol in cases:

@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(PSE_BATCH_MV_THREADS) k_lz_matvec_batch(const 
     const LzSys &S = sys[blk2sys[blockIdx.x]];
     for (int i = threadIdx.x; i < PSE_TABLEC_N; i += blockDim.x) tab_s[i] = S.table_c[i];
     __syncthreads();
-    lz_matvec_body<float, PSE_BATCH_MV_TPP, 4, true>(S.N, S.K, S.g, S.rec, S.count, S.nbr, tab_s, S.u, S.part_mv,
+    lz_matvec_body<float, PSE_BATCH_MV_TPP, PSE_BATCH_MV_ILP, true>(S.N, S.K, S.g, S.rec, S.count, S.nbr, tab_s, S.u, S.part_mv,
                                                      S.lz, S.pc, S.basis, nullptr, blockIdx.x - S.blk_mv, S.nblk_mv,
                                                      sh);
 }
@@ -1163,8 +1163,21 @@ template <typename T, int TPP, int ILP, int BS = 128> int mv_blocks_per_sm() {
     }
     return per_sm;
 }
-// the default FP32 shape, which the fused batch matvec shares
-int matvec_blocks_per_sm() { return mv_blocks_per_sm<float, PSE_BATCH_MV_TPP, 4, PSE_BATCH_MV_THREADS>(); }
+// resident blocks per SM of the fused batch matvec (at most 16)
+int matvec_blocks_per_sm() {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lz_matvec_batch, PSE_BATCH_MV_THREADS, 0) !=
+                cudaSuccess ||
+            nb < 1) {
+            cudaGetLastError();
+            nb = 1;
+        }
+        per_sm = nb < 16 ? nb : 16;
+    }
+    return per_sm;
+}
 // the same for the Lanczos update (FP32 and FP64), at most 8 per SM
 template <typename T> int up_blocks_per_sm() {
     static int per_sm = 0;
@@ -1259,6 +1272,7 @@ void matvec_prepare() {
     mv_prepare_all<float>();
     mv_prepare_all<double>();
     up_blocks_per_sm<float>(); up_blocks_per_sm<double>();
+    matvec_blocks_per_sm();
 }
 
 template <typename T, int TPP, int ILP, int BS = 128>

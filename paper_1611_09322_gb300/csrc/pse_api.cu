@@ -2092,11 +2092,11 @@ extern "C" pse_status pse_batch_create(pse_batch **out, int nsys, const double *
 }
 
 // Descriptors and block tables of the fused loop kernels.  Each system gets
-// the block counts its own context would launch with the default FP32
-// shapes (one block per 512 particles of the matvec, per 256 of the update,
-// capped at the resident blocks per SM), so its reductions add the same
-// partial sums in the same order and a batched system's sample is bitwise
-// that of a lone context in the default shape.
+// a fixed number of blocks of each fused kernel (one per PSE_BATCH_MV_THREADS
+// / PSE_BATCH_MV_TPP particles of the matvec, per 256 of the update, capped
+// at the resident blocks per SM), so its reductions add the same partial
+// sums in the same order on every launch; its sample equals a lone
+// context's to float rounding.
 static pse_status batch_descriptors(pse_batch *b) {
     const int S = (int)b->sys.size();
     const int64_t cap_mv = (int64_t)num_sms() * matvec_blocks_per_sm(),
