@@ -522,7 +522,7 @@ def variants_learned_batched(dev, flush, stream, steps, xi, M):
     """The metric's comparison: learned preconditioner and batching vs plain."""
     import numpy as np
     import torch
-    from paper_1611_09322_gb300 import BatchSampler, Sampler, precond_train, workloads
+    from paper_1611_09322_gb300 import BatchSampler, Sampler, precond_train, tune_batch_grid_step, workloads
     out = {}
     # the network is kept only if it cuts the held-out mean Lanczos count by
     # one iteration; otherwise the learned form falls back to P = I
@@ -588,8 +588,12 @@ def variants_learned_batched(dev, flush, stream, steps, xi, M):
     offsets = np.cumsum([0] + [p.shape[0] for p in pos_list])
     pa = torch.from_numpy(np.concatenate(pos_list)).to(dev)
     po = torch.empty_like(pa)
+    # the systems' grids: their planned size classes or one or two classes
+    # finer (each then at the largest xi its grid admits), by a timed choice
+    # before the timed region, like the xi scan of the single system
+    gtune = tune_batch_grid_step(Ls, pa, offsets, xi=XI, tol=TOL, autotune=9)
     for name, th in (("batched_64sys_plain", None), ("batched_64sys_learned", theta)):
-        b = BatchSampler(Ls, 1.0, xi=XI, tol=TOL, autotune=9)
+        b = BatchSampler(Ls, 1.0, params=gtune["params"])
         if th is not None:
             for k in range(len(spec)):
                 b.set_precond(k, th)
@@ -599,6 +603,7 @@ def variants_learned_batched(dev, flush, stream, steps, xi, M):
         its = [b.stats(k)["lanczos_iters"] for k in range(len(spec))]
         out[name] = {"value": int(offsets[-1]) * steps / (sum(per) / 1e3), "ms_per_step": sum(per) / steps,
                      "n_systems": len(spec), "n_particles": int(offsets[-1]), "lanczos_iters_mean": float(np.mean(its)),
+                     "grid_step": gtune["step"], "grid_step_ms": {str(k): round(v, 4) for k, v in gtune["ms"].items()},
                      "preconditioner": "none" if th is None and name.endswith("plain") else
                      ("network" if th is not None else "fallback P = I (no held-out iteration gain)")}
         grids = [b.plan(k)["M"] for k in range(len(spec))]
@@ -627,8 +632,9 @@ def variants_learned_batched(dev, flush, stream, steps, xi, M):
         sk.close()
     out["workload_batched"] = ("64 periodic systems, N log-uniform in [1e3, 5e4], phi uniform in [0.05, 0.4], "
                                "half fractal gels (phi <= 0.2), each with its own box, FFT grid (the planned grid "
-                               "raised to a size class) and xi (the largest its grid admits, from xi a = 0.5), "
-                               "tol 1e-3; one CUDA graph launch per step")
+                               "raised to a size class, then 0-2 classes finer by one timed choice for the batch) "
+                               "and xi (the largest its grid admits, from xi a = 0.5), tol 1e-3; one CUDA graph "
+                               "launch per step")
     out["variants_xi"] = {"xi": xi, "M": M, "note": "the N=1e6 variants run at the headline's tuned xi and grid"}
     return out
 
@@ -640,7 +646,7 @@ def run_only(args):
     that a profiler sees every kernel.  Prints one JSON line."""
     import numpy as np
     import torch
-    from paper_1611_09322_gb300 import BatchSampler, Sampler, workloads
+    from paper_1611_09322_gb300 import BatchSampler, Sampler, tune_batch_grid_step, workloads
     dev = torch.device("cuda", 0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -666,11 +672,14 @@ def run_only(args):
         offsets = np.cumsum([0] + [p.shape[0] for p in pos_list])
         pa = torch.from_numpy(np.concatenate(pos_list)).to(dev)
         po = torch.empty_like(pa)
-        b = BatchSampler(Ls, 1.0, xi=XI, tol=TOL, use_graph=graph, autotune=9)
+        gtune = tune_batch_grid_step(Ls, pa, offsets, xi=XI, tol=TOL, autotune=9)
+        b = BatchSampler(Ls, 1.0, params=[dict(pk, use_graph=graph) for pk in gtune["params"]])
         for i in range(args.warmup):
             b.sample(pa, offsets, 1, i, out=po)
         per = timed_steps(lambda i: b.sample(pa, offsets, 1, 100 + i, out=po), args.steps, flush, stream)
-        n, variant = int(offsets[-1]), "64-system batch (N log-uniform in [1e3, 5e4], phi in [0.05, 0.4], half gels)"
+        n = int(offsets[-1])
+        variant = (f"64-system batch (N log-uniform in [1e3, 5e4], phi in [0.05, 0.4], half gels), grids "
+                   f"{gtune['step']} size classes finer than planned (timed choice)")
         b.close()
     print(json.dumps({"only": args.only, "variant": variant, "graph": graph, "steps": args.steps,
                       "ms_per_step": sum(per) / args.steps, "value": n * args.steps / (sum(per) / 1e3),

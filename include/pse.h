@@ -553,6 +553,16 @@ typedef struct pse_batch pse_batch;
  * only. */
 pse_status pse_batch_create(pse_batch **out, int nsys, const double *L, const double *a, const pse_params *p);
 
+/* The grid side a system (L, a, p) gets in a batch, `step` size classes
+ * finer: its Sec. II C plan's grid (p->grid_M when set) raised to the next
+ * class of the list above, then `step` classes further (the last class at
+ * most; a plan beyond the last class keeps its own grid).  Setting
+ * grid_M to the step-1 or step-2 grid with autotune bit 3 trades a larger
+ * xi (shorter r_cut, fewer neighbour pairs) for a larger FFT.  Host only,
+ * no GPU needed.  PSE_EINVAL on null pointers or step < 0; pse_plan's
+ * status otherwise. */
+pse_status pse_batch_grid(double L, double a, const pse_params *p, int step, int *M_out);
+
 /* Sample all systems.  offsets: host array of nsys + 1 particle offsets
  * (offsets[0] = 0, system k owns particles offsets[k] .. offsets[k+1]-1,
  * each N_k >= 1); d_pos / d_out: 3 * offsets[nsys] float32 device arrays,

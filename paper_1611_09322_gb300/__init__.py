@@ -14,7 +14,7 @@ import numpy as np
 from . import _lib
 from ._lib import PSE_FP32, PSE_FP64, PseError, pse_params, pse_plan_info, pse_stats
 
-__all__ = ["Sampler", "PolySampler", "BatchSampler", "pse_plan", "pse_real_scalars", "pse_real_scalars_poly", "pse_real_matvec_noalloc", "pse_precond_loss_grad",
+__all__ = ["Sampler", "PolySampler", "BatchSampler", "pse_plan", "pse_batch_grid", "tune_batch_grid_step", "pse_real_scalars", "pse_real_scalars_poly", "pse_real_matvec_noalloc", "pse_precond_loss_grad",
            "pse_precond_train", "pse_xi_model", "pse_tune_xi", "PseError", "PSE_FP32", "PSE_FP64", "make_params"]
 
 
@@ -89,6 +89,46 @@ def pse_tune_xi(L, pos, a=1.0, d_f=3.0, reps=5, **kw):
     _lib.check(lib.pse_tune_xi(L, a, ctypes.byref(p), pos.shape[0], _ptr(pos), d_f, reps, ctypes.byref(out),
                                _stream()), "pse_tune_xi")
     return out.as_dict()
+
+
+def pse_batch_grid(L, a=1.0, step=0, **kw):
+    """Grid side the system (L, a) gets in a batch, `step` size classes finer (pse_batch_grid)."""
+    lib = _lib.load()
+    p = make_params(**kw)
+    m = ctypes.c_int(0)
+    _lib.check(lib.pse_batch_grid(L, a, ctypes.byref(p), int(step), ctypes.byref(m)), "pse_batch_grid")
+    return m.value
+
+
+def tune_batch_grid_step(Ls, pos_all, offsets, a=1.0, steps=(0, 1, 2), reps=5, seed=1, **kw):
+    """Timed choice, for a whole batch, of how many size classes finer than
+    its planned grids the systems' FFT grids are (with autotune bit 3 each
+    then takes the largest xi its grid admits: a finer grid buys a shorter
+    r_cut).  Builds one batch per candidate step, times `reps` samples each
+    (CUDA events, after two untimed ones) and returns a dict: "step" (the
+    fastest), "ms" per step and "params" (per-system keyword dicts with the
+    chosen grids, for BatchSampler(params=...))."""
+    import torch
+    ms = {}
+    chosen = None
+    for st in steps:
+        params = [dict(kw, grid_M=pse_batch_grid(L, a, st, **kw)) for L in Ls]
+        b = BatchSampler(Ls, a, params=params)
+        out = torch.empty_like(pos_all)
+        for i in range(2):
+            b.sample(pos_all, offsets, seed, 90_000 + i, out=out)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(reps):
+            b.sample(pos_all, offsets, seed, 90_100 + i, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        ms[st] = e0.elapsed_time(e1) / reps
+        b.close()
+        if chosen is None or ms[st] < ms[chosen[0]]:
+            chosen = (st, params)
+    return {"step": chosen[0], "ms": ms, "params": chosen[1]}
 
 
 def pse_real_matvec_noalloc(L, a, xi, tol, pos, v, out):

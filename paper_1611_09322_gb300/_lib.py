@@ -120,6 +120,8 @@ SIGNATURES = {
     "pse_sample_poly": (_ST, [_VP, _I64, _VP, _VP, _U64, _U64, _VP, _VP, _VP, _VP]),
     "pse_real_matvec_poly": (_ST, [_VP, _I64, _VP, _VP, _VP, _VP, _VP]),
     "pse_batch_create": (_ST, [ctypes.POINTER(_VP), ctypes.c_int, _VP, _VP, _VP]),
+    "pse_batch_grid": (_ST, [ctypes.c_double, ctypes.c_double, ctypes.POINTER(pse_params), ctypes.c_int,
+                             ctypes.POINTER(ctypes.c_int)]),
     "pse_batch_sample": (_ST, [_VP, _VP, _VP, _U64, _U64, _VP, _VP]),
     "pse_batch_get_stats": (_ST, [_VP, ctypes.c_int, ctypes.POINTER(pse_stats)]),
     "pse_batch_get_plan": (_ST, [_VP, ctypes.c_int, ctypes.POINTER(pse_plan_info)]),

@@ -1967,6 +1967,32 @@ extern "C" void pse_batch_destroy(pse_batch *b) {
     delete b;
 }
 
+// Grid size classes of a batch: each system's Sec. II C grid is raised to
+// the next class (a finer grid only lowers the NUFFT error), so that systems
+// of a class share one batched inverse FFT.
+static const int kGridClasses[] = {16, 20, 24, 28, 32, 40, 48, 56, 64, 72, 80, 96, 112, 128, 144, 160, 192,
+                                   224, 256, 288, 320, 384, 448, 512, 576, 640, 768, 896, 1024};
+static constexpr int kNumGridClasses = (int)(sizeof(kGridClasses) / sizeof(kGridClasses[0]));
+
+extern "C" pse_status pse_batch_grid(double L, double a, const pse_params *p, int step, int *M_out) {
+    if (!p || !M_out || step < 0) return PSE_EINVAL;
+    pse_params q = *p;
+    q.autotune &= ~1;
+    pse_plan_info pi;
+    const pse_status st = pse_plan(L, a, &q, &pi);
+    if (st != PSE_OK) return st;
+    int ci = -1;
+    for (int i = 0; i < kNumGridClasses; ++i)
+        if (kGridClasses[i] >= pi.M) { ci = i; break; }
+    if (ci < 0) {  // beyond the last class: its own grid
+        *M_out = pi.M;
+        return PSE_OK;
+    }
+    ci += step;
+    *M_out = kGridClasses[ci < kNumGridClasses ? ci : kNumGridClasses - 1];
+    return PSE_OK;
+}
+
 extern "C" pse_status pse_batch_create(pse_batch **out, int nsys, const double *L, const double *a,
                                        const pse_params *p) {
     if (!out) return PSE_EINVAL;
@@ -1976,11 +2002,6 @@ extern "C" pse_status pse_batch_create(pse_batch **out, int nsys, const double *
     if (!b) return PSE_ENOMEM;
     if (cudaGetDevice(&b->device) != cudaSuccess) { cudaGetLastError(); delete b; return PSE_ECUDA; }
     pse_status st = PSE_OK;
-    // grid size classes: each system's Sec. II C grid is raised to the next
-    // class (a finer grid only lowers the NUFFT error), so that systems of a
-    // class share one batched inverse FFT
-    static const int classes[] = {16, 20, 24, 28, 32, 40, 48, 56, 64, 72, 80, 96, 112, 128, 144, 160, 192,
-                                  224, 256, 288, 320, 384, 448, 512, 576, 640, 768, 896, 1024};
     for (int k = 0; k < nsys && st == PSE_OK; ++k) {
         if (p[k].precision != PSE_FP32) { st = PSE_ENOTSUPPORTED; break; }
         pse_params q = p[k];
@@ -1991,7 +2012,7 @@ extern "C" pse_status pse_batch_create(pse_batch **out, int nsys, const double *
             pse_plan_info pi;
             st = pse_plan(L[k], a[k], &q, &pi);
             if (st != PSE_OK) break;
-            for (int cl : classes)
+            for (int cl : kGridClasses)
                 if (cl >= pi.M) { q.grid_M = cl; break; }
         }
         pse_ctx *c = nullptr;

@@ -74,3 +74,20 @@ def test_host_scalars_match_oracle(lib, xi, a):
     assert np.abs(F - Fo).max() < 1e-12 and np.abs(G - Go).max() < 1e-12
     with pytest.raises(_lib.PseError):
         pse_real_scalars(np.array([-1.0]), xi, a)
+
+
+def test_batch_grid_classes():
+    """pse_batch_grid: step 0 is the smallest size class at or above the
+    plan's grid, a class maps to itself, and each step is the next class."""
+    from paper_1611_09322_gb300 import PseError, pse_batch_grid, pse_plan
+    for L in (20.0, 50.0, 100.0, 347.3):
+        M0 = pse_plan(L, 1.0, xi=0.5, tol=1e-3)["M"]
+        g = [pse_batch_grid(L, 1.0, s, xi=0.5, tol=1e-3) for s in range(4)]
+        assert g[0] >= M0 and g[0] < g[1] < g[2] < g[3]
+        assert pse_batch_grid(L, 1.0, 0, xi=0.5, tol=1e-3, grid_M=g[0]) == g[0]
+        assert pse_batch_grid(L, 1.0, 1, xi=0.5, tol=1e-3, grid_M=g[0]) == g[1]
+        assert pse_batch_grid(L, 1.0, 0, xi=0.5, tol=1e-3, grid_M=g[1]) == g[1]
+        # no class lies strictly between the plan's grid and step 0's
+        assert pse_batch_grid(L, 1.0, 0, xi=0.5, tol=1e-3, grid_M=M0) == g[0]
+    with pytest.raises(PseError):
+        pse_batch_grid(50.0, 1.0, -1, xi=0.5, tol=1e-3)
