@@ -94,6 +94,36 @@ def test_batch_grids_are_size_classes_at_least_the_plan(torch):
     b.close()
 
 
+def test_tuned_grid_step(torch):
+    """tune_batch_grid_step times the batch at grids 0 and 1 size classes
+    finer than planned and returns per-system parameters whose grids are
+    pse_batch_grid's for the chosen step; a batch built from them samples
+    (every system converged, finite output) on exactly those grids, and a
+    finer grid gives each system a larger xi (autotune bit 3)."""
+    from paper_1611_09322_gb300 import BatchSampler, pse_batch_grid, tune_batch_grid_step
+    systems = _systems()
+    Ls = [L for _, L, _ in systems]
+    offsets = np.cumsum([0] + [p.shape[0] for p, _, _ in systems])
+    pa = torch.from_numpy(np.concatenate([p for p, _, _ in systems])).cuda()
+    r = tune_batch_grid_step(Ls, pa, offsets, steps=(0, 1), reps=2, xi=0.5, tol=1e-3, autotune=8)
+    assert r["step"] in (0, 1) and set(r["ms"]) == {0, 1} and all(v > 0 for v in r["ms"].values())
+    xis = {}
+    for st in (0, 1):
+        params = [dict(xi=0.5, tol=1e-3, autotune=8, grid_M=pse_batch_grid(L, 1.0, st, xi=0.5, tol=1e-3, autotune=8))
+                  for L in Ls]
+        if st == r["step"]:
+            assert [pk["grid_M"] for pk in params] == [pk["grid_M"] for pk in r["params"]]
+        b = BatchSampler(Ls, 1.0, params=params)
+        out = b.sample(pa, offsets, SEED, 3)
+        assert torch.isfinite(out).all()
+        for k in range(len(Ls)):
+            assert b.plan(k)["M"] == params[k]["grid_M"]
+            assert b.stats(k)["converged"] == 1
+        xis[st] = [b.plan(k)["xi"] for k in range(len(Ls))]
+        b.close()
+    assert all(x1 > x0 for x0, x1 in zip(xis[0], xis[1]))
+
+
 def test_batch_grid_fit_xi(torch):
     """autotune bit 3 in a batch: each system keeps its size-class grid and
     takes the largest xi that grid admits (checked against the host plan);
