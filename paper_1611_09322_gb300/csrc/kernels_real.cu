@@ -947,6 +947,20 @@ __global__ void k_batch_cond(LzState *const *lzs, int nsys, cudaGraphConditional
 // x_s = sum_{i=1..J} coef_i q_i[s]  (+ wave part), written in caller order.
 // On the forces path (udet != null) out = c_noise x + c_det M_r F + wave, the
 // wave part already carrying both weights.
+// Three consecutive floats of a caller-order (N, 3) array in two stores:
+// of two consecutive 4-byte aligned addresses one is 8-byte aligned, and the
+// pair starting there goes out as one float2 (the scattered output writes
+// are a third fewer).
+__device__ __forceinline__ void store3(float *p, float x, float y, float z) {
+    if ((reinterpret_cast<uintptr_t>(p) & 7) == 0) {
+        *reinterpret_cast<float2 *>(p) = make_float2(x, y);
+        p[2] = z;
+    } else {
+        p[0] = x;
+        *reinterpret_cast<float2 *>(p + 1) = make_float2(y, z);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void lz_final_body(int64_t N, const SampleArgs<T> *args, const V4<T> *pos_sorted,
                                               const V4<T> *basis, const V4<T> *uwave, const LzState *lz,
@@ -993,7 +1007,13 @@ __device__ __forceinline__ void lz_final_body(int64_t N, const SampleArgs<T> *ar
         y = cn * y + cd * m.y;
         z = cn * z + cd * m.z;
     }
-    if (args->out) { args->out[o] = x + wx; args->out[o + 1] = y + wy; args->out[o + 2] = z + wz; }
+    if (args->out) {
+        if constexpr (sizeof(T) == 4) {
+            store3(args->out + o, x + wx, y + wy, z + wz);
+        } else {
+            args->out[o] = x + wx; args->out[o + 1] = y + wy; args->out[o + 2] = z + wz;
+        }
+    }
 }
 
 template <typename T>
