@@ -260,14 +260,15 @@ def accuracy(first, xi):
     return out
 
 
-def cpu_baseline(xi=XI_TUNED, n=CPU_SAMPLE_N, reps=3, one_thread=True, keep=None):
+def cpu_baseline(xi=XI_TUNED, n=CPU_SAMPLE_N, reps=3, one_thread=True, with_accuracy=False):
     """The FP64 oracle as it stands, on a bounded sample of the headline
     workload: `reps` samples of an n-particle box at the same density, xi and
     tol (median and interquartile range of particle-samples/s), on the host's
     cores as the oracle uses them (`cores` = CPU time / wall time, the
     threads it actually kept busy), plus one sample in a subprocess limited
     to one thread."""
-    walls, cpus, js, M = _oracle_sample_times(n, xi, reps, keep=keep)
+    first = {} if with_accuracy else None
+    walls, cpus, js, M = _oracle_sample_times(n, xi, reps, keep=first)
     rates = [n / w for w in walls]
     q1, med, q3 = _quartiles(rates)
     busy = sum(cpus) / sum(walls)
@@ -287,6 +288,12 @@ def cpu_baseline(xi=XI_TUNED, n=CPU_SAMPLE_N, reps=3, one_thread=True, keep=None
                                  "cpu_time_per_wall": round(c1 / w1, 2)}
         except (subprocess.SubprocessError, ValueError, IndexError) as e:
             out["one_thread"] = {"unavailable": str(e)[:200]}
+    if with_accuracy:
+        # the oracle samples of this leg also measure the CUDA path's errors
+        try:
+            out["accuracy"] = accuracy(first, xi)
+        except Exception as e:  # the throughput line stands without it
+            out["accuracy"] = {"unavailable": str(e)[:200]}
     return out
 
 
@@ -836,12 +843,8 @@ def main():
             line["variants"].update(variants_poly(dev, flush, stream, max(20, args.steps // 4)))
             line["variants"].update(variants_configs(dev, flush, stream, 10, peak))
         if not args.no_cpu_baseline and ws == 1:
-            first = {}
-            line["cpu_baseline"] = cpu_baseline(xi, keep=first)
-            try:
-                line["accuracy"] = accuracy(first, xi)
-            except Exception as e:  # the throughput line stands without it
-                line["accuracy"] = {"unavailable": str(e)[:200]}
+            line["cpu_baseline"] = cpu_baseline(xi, with_accuracy=True)
+            line["accuracy"] = line["cpu_baseline"].pop("accuracy")
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
