@@ -253,12 +253,3 @@ def wave_covariance_grid(pos, species, species_radii, plan_):
             proj = (1.0 if p == q else 0.0) - kh[:, p] * kh[:, q]
             C[p, q] = ((phi * proj[None, :]) @ phi.conj().T).real
     return C.transpose(2, 0, 3, 1).reshape(3 * N, 3 * N)
-
-
-def pse_sample(pos, species, species_radii, L, xi, tol, seed, sample, n_iter=None, M=None, P=None):
-    """Polydisperse PSE sample: (u, u_real, u_wave, j, plan)."""
-    radii = np.asarray(species_radii, dtype=np.float64)[np.asarray(species)]
-    p = plan(L, species_radii, xi, tol, M=M, P=P)
-    ur, j, _ = real_sample(pos, radii, p, seed, sample, n_iter=n_iter)
-    uw = wave_sample_grid(pos, species, species_radii, p, seed, sample)
-    return ur + uw, ur, uw, j, p

@@ -513,14 +513,3 @@ def full_sample(pos, plan, seed, sample, n_iter=None, lanczos_tol=None, system=0
     tol = plan.tol if lanczos_tol is None else lanczos_tol
     return lanczos_sqrt(lambda v: mobility_apply(v, pos, plan, op=A), z, tol=tol, n_iter=n_iter,
                         max_iter=max_iter)
-
-
-def pse_sample(pos, L, a, xi, tol, seed, sample, n_iter=None, M=None, P=None, precond=None):
-    """Full PSE sample (N, 3) = real (Lanczos) + wave (gridded NUFFT), FP64.
-
-    Returns (u, u_real, u_wave, j_lanczos, plan).
-    """
-    plan = ewald.plan(L, a, xi, tol, M=M, P=P)
-    ur, j, _ = real_sample(pos, plan, seed, sample, n_iter=n_iter, precond=precond)
-    uw = wave_sample_grid(pos, plan, seed, sample)
-    return ur + uw, ur, uw, j, plan
