@@ -258,7 +258,3 @@ def mobility_dense(pos, L, a, xi, tol=1e-12):
     Mr = mobility_real_dense(pos, L, a, xi, rc)
     Mw = mobility_wave_dense(pos, L, a, xi, modes_sphere(kc, L))
     return Mr + Mw, Mr, Mw
-
-
-def erfc_py(x):
-    return float(erfc(x))
